@@ -1,0 +1,75 @@
+"""The seeded generators: splitmix64 and the structured families."""
+import numpy as np
+import pytest
+
+import lu_inputs as li
+
+
+def test_splitmix64_reference_values():
+    # splitmix64 started at state 0: first outputs (published test vector of the
+    # generator as used to seed xoshiro: 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4)
+    assert li.splitmix64_scalar(0, 0) == 0xE220A8397B1DCDAF
+    assert li.splitmix64_scalar(0, 1) == 0x6E789E6AA1B965F4
+    v = li.splitmix64(0, np.arange(2, dtype=np.uint64))
+    assert int(v[0]) == 0xE220A8397B1DCDAF and int(v[1]) == 0x6E789E6AA1B965F4
+
+
+def test_vector_matches_scalar():
+    seed = 20161106
+    c = np.arange(1000, dtype=np.uint64) * np.uint64(7919)
+    v = li.splitmix64(seed, c)
+    for k in (0, 1, 17, 999):
+        assert int(v[k]) == li.splitmix64_scalar(seed, int(c[k]))
+
+
+def test_torch_builder_matches_numpy():
+    torch = pytest.importorskip("torch")
+    for (m, n, seed) in ((37, 21, 3), (128, 64, 20161106)):
+        A = li.uniform(m, n, seed)
+        T = li.uniform_colmajor_torch(m, n, seed, device="cpu", ld=m + 3)
+        assert T.shape == (n, m + 3)
+        assert np.array_equal(li.from_device_colmajor(T, m), A)
+        assert float(T[:, m:].abs().sum()) == 0.0
+
+
+def test_uniform_range_and_exactness():
+    A = li.uniform(200, seed=1)
+    assert A.min() >= -1.0 and A.max() < 1.0
+    assert abs(A.mean()) < 0.02
+    # 2u - 1 is exact: scaling back gives integers
+    k = (A + 1.0) * 2.0 ** 52
+    assert np.array_equal(k, np.floor(k))
+
+
+def test_dyadic_factors_shape():
+    perm, L, U = li.dyadic_factors(50, 3)
+    assert np.array_equal(np.diag(L), np.ones(50))
+    assert np.max(np.abs(np.tril(L, -1))) <= 7 / 8
+    assert np.all(np.diag(U) != 0) and np.max(np.abs(U)) <= 8
+    assert np.array_equal(np.sort(perm), np.arange(50))
+    A, perm2, L2, U2 = li.dyadic_plu(50, 3)
+    assert np.array_equal(A[perm], L @ U)
+
+
+def test_kappa_matrix_singular_values():
+    n = 48
+    for kappa in (1e2, 1e5, 1e8):
+        A = li.kappa_matrix(n, kappa, seed=5)
+        s = np.linalg.svd(A, compute_uv=False)
+        ref = li.kappa_singular_values(n, kappa)
+        assert np.allclose(s, ref, rtol=1e-9, atol=1e-14)
+        assert s[0] / s[-1] == pytest.approx(kappa, rel=1e-6)
+
+
+def test_kappa_torch_matches_numpy():
+    torch = pytest.importorskip("torch")
+    n = 70
+    A = li.kappa_matrix(n, 1e5, seed=9, k=n)
+    T = li.kappa_matrix_torch(n, 1e5, seed=9, k=n, device="cpu", block=16)
+    assert np.allclose(li.from_device_colmajor(T, n), A, atol=1e-13)
+
+
+def test_batch_sizes_range():
+    s = li.batch_sizes(10000, 16, 256, seed=4)
+    assert s.min() == 16 and s.max() == 256
+    assert abs(s.mean() - 136) < 3
