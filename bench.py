@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 blocked LU with malleable look-ahead on one GB300, plus the
+mixed-precision time to backward error 1e-14 beside the FP64 one.
+
+A step is one pass of the hot path over one synthetic matrix: restore A
+(n = 16384, entries uniform [-1, 1), FP64, 2 GiB, larger than L2), lu_factor
+(panel, row interchanges, TRSM, trailing update, look-ahead) and lu_solve of
+b = A * ones.  The metric value is LU GFLOP/s = (2/3 n^3) / (time per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank factors its own matrix on its own GPU
+(independent replicas, no collective on the data path; "scaling": "weak") and
+the value is the sum of all ranks' flops over the slowest rank's time.
+--impl reference times the CPU oracle (plain unblocked GEPP + getrs, FP64) on
+the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LU GFLOP/s (2/3n^3) and time to 1e-14 backward error: mixed vs FP64, 1 GB300"
+N_MAIN = 16384
+SEED = 20161106 + 1000 * 2          # family 2 (blocked FP64 LU sweep), case 0
+MIXED_N = 16384
+MIXED_KAPPA = 1e5
+MIXED_REFLECTORS = 256
+SM_COUNT = 152
+FP64_PEAK_TFLOPS = 2 * 2 * SM_COUNT * 2.07e9 / 1e12   # 2 DFMA (4 flop) / clk / SM at 2070 MHz = 1.259
+
+
+def flops_lu(n):
+    return 2.0 / 3.0 * n ** 3
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower() in ("active", "0x1", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ----------------------------------------------------------------------------
+def oracle_sample(n_sample, seed):
+    import numpy as np
+
+    import lu_inputs as li
+    import oracle
+
+    A = li.uniform(n_sample, n_sample, seed)
+    b = li.ones_rhs(A)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    LU, ipiv, info = oracle.getrf(A, nthreads=threads)
+    x = oracle.getrs(LU, ipiv, b)
+    dt = time.perf_counter() - t0
+    assert info == 0 and np.max(np.abs(x - 1.0)) < 1e-8
+    return dt, threads
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n_s = args.ref_n
+    for _ in range(args.warmup):
+        oracle_sample(n_s, SEED)
+    times = []
+    threads = 1
+    for _ in range(args.steps):
+        dt, threads = oracle_sample(n_s, SEED)
+        times.append(dt)
+    t = sum(times) / len(times)
+    value = flops_lu(n_s) / t / 1e9
+    sample = f"oracle getrf+getrs (unblocked GEPP, FP64) on a uniform [-1,1) matrix of order {n_s} per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"fp64_lu_lookahead_n{N_MAIN}", "n": N_MAIN, "nrhs": 1,
+                   "sample_n": n_s, "device": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lu.build()
+    n = args.n
+    # inputs: A (FP64, column-major, 2 GiB at n = 16384) generated on the device
+    A0 = li.uniform_colmajor_torch(n, n, SEED + rank, dev, torch.float64)
+    A = torch.empty_like(A0)
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    b0 = (A0.t() @ ones).view(1, n)            # b = A * ones (column-major A0 holds A^T row-major)
+    b = torch.empty_like(b0)
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        A.copy_(A0)
+        b.copy_(b0)
+        lu.lu_factor(A, ipiv, info)
+        lu.lu_solve(A, ipiv, b)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of the last step (device residual with a library product; verification only)
+    x = b.view(-1)
+    r = b0.view(-1) - A0.t() @ x
+    eta = float(r.abs().max() / (A0.abs().sum(0).max() * x.abs().max() + b0.abs().max()))
+    assert int(info.item()) == 0 and eta < 10 * n * 2.0 ** -53, f"FP64 step failed: info={int(info.item())} eta={eta}"
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    lu.lu_update_timing(True)
+    launches0 = lu.lu_kernel_launches()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = lu.lu_kernel_launches() - launches0
+    lu.lu_update_timing(False)
+    upd_n, upd_ms, upd_flops, upd_bytes = lu.lu_update_timing_read()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ws * flops_lu(n) / (ms_per_step / 1e3) / 1e9
+
+    # end-to-end through the C ABI with host buffers (pinned), copies timed
+    hA = A0.cpu().pin_memory()
+    hb = b0.cpu().pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    hinfo = torch.zeros(1, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        A.copy_(hA, non_blocking=True)
+        b.copy_(hb, non_blocking=True)
+        lu.lu_factor(A, ipiv, info)
+        lu.lu_solve(A, ipiv, b)
+        hx.copy_(b, non_blocking=True)
+        hinfo.copy_(info, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    assert int(hinfo.item()) == 0 and float((hx - 1.0).abs().max()) < 1e-8
+    e2e = {"value": flops_lu(n) / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n + 4, "ms_per_step": e2e_ms}
+    del hA
+
+    # roofline of the dominant kernel (trailing update, FP64 DFMA)
+    achieved = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "gemm_update_simt<double>", "launches": upd_n,
+                "avg_launch_ms": upd_ms / max(1, upd_n),
+                "flops_per_launch": upd_flops / max(1, upd_n),
+                "peak_note": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"}
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f).get("gemm_update_simt<double>")
+        if tr and tr.get("valid"):
+            roofline["traffic"] = tr["bytes_per_flop"] * roofline["flops_per_launch"]
+
+    # time to backward error 1e-14: mixed precision vs FP64 on a kappa = 1e5 matrix
+    tts = None
+    if not args.skip_mixed and rank == 0:
+        tts = time_to_solution(args, dev, ms_per_step)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"fp64_lu_lookahead_n{n}", "n": n, "lda": n, "nrhs": 1, "seed": SEED,
+                   "entries": "uniform [-1,1)", "l2": "inputs larger than L2 (2 GiB FP64 matrix per step)",
+                   "parallelism": f"replicas x{ws}", "eta_fp64": eta},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "time_to_solution": tts,
+    }
+    if rank == 0 and not args.skip_cpu:
+        dt, threads = oracle_sample(args.cpu_n, SEED)
+        line["cpu_baseline"] = {"value": flops_lu(args.cpu_n) / dt / 1e9, "unit": "GFLOP/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"oracle getrf+getrs on a uniform [-1,1) matrix of order {args.cpu_n} "
+                                          f"(same generator), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def time_to_solution(args, dev, fp64_ms):
+    """Mixed-precision solve vs the FP64 factor+solve, both to eta <= 1e-14."""
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    n = args.mixed_n
+    A = li.kappa_matrix_torch(n, MIXED_KAPPA, SEED + 1, MIXED_REFLECTORS, dev)
+    xt = torch.ones(1, n, dtype=torch.float64, device=dev)   # X_true column 0 = ones
+    B = (A.t() @ xt.view(-1)).view(1, n)
+    X = torch.zeros_like(B)
+    lu.lu_solve_mixed(A, B, X)                    # warm-up
+    torch.cuda.synchronize()
+    reps = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        rep = lu.lu_solve_mixed(A, B, X)
+        torch.cuda.synchronize()
+        reps.append((time.perf_counter() - t0, rep))
+    wall, rep = min(reps, key=lambda r: r[0])
+    x = X.view(-1)
+    r = B.view(-1) - A.t() @ x
+    eta = float(r.abs().max() / (A.abs().sum(0).max() * x.abs().max() + B.abs().max()))
+    return {"n": n, "kappa": MIXED_KAPPA, "reflectors_per_side": MIXED_REFLECTORS, "nrhs": 1,
+            "mixed_ms": rep.t_total_ms, "mixed_wall_ms": wall * 1e3, "mixed_factor_ms": rep.t_factor_ms,
+            "mixed_refine_ms": rep.t_refine_ms, "mixed_rung": rep.rung, "mixed_iterations": rep.iterations,
+            "mixed_gmres_iters": rep.gmres_iters, "mixed_eta": eta, "mixed_fell_back": rep.fell_back,
+            "fp64_ms": fp64_ms if n == args.n else None,
+            "speedup_vs_fp64": (fp64_ms / rep.t_total_ms) if (n == args.n and rep.t_total_ms > 0) else None}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--mixed-n", dest="mixed_n", type=int, default=MIXED_N)
+    ap.add_argument("--cpu-n", dest="cpu_n", type=int, default=4096)
+    ap.add_argument("--ref-n", dest="ref_n", type=int, default=2048)
+    ap.add_argument("--skip-mixed", dest="skip_mixed", action="store_true")
+    ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

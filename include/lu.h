@@ -1,0 +1,225 @@
+/*
+ * lu.h -- C ABI of the GB300 LU-with-partial-pivoting library (liblu.so).
+ *
+ * The method: blocked right-looking LU factorization with partial pivoting,
+ * P A = L U (section 3 of arXiv:1611.06365, "A Case for Malleable Thread-Level
+ * Linear Algebra Libraries"), with static look-ahead (section 3.2, Figure 3,
+ * equation (2x2)) whose panel resources rejoin the trailing update once the
+ * next panel is factored (worker sharing, section 4.1).  On the GPU the panel
+ * is one thread-block cluster and the update is a tile grid on a lower
+ * priority stream; the hardware CTA scheduler hands the SMs freed by the panel
+ * to the pending update tiles.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are column-major: element (i, j) of a matrix with leading
+ *    dimension ld sits at offset i + j*ld (elements, not bytes).  ld >= max(1,n).
+ *  - All matrix, vector, pivot and info pointers are DEVICE pointers owned by
+ *    the caller, unless the argument is documented as host memory.  The
+ *    library never frees caller memory.  Internal workspace is allocated
+ *    stream-ordered (cudaMallocAsync) on the caller's stream and released
+ *    before the call returns its work to that stream.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous with respect to the host unless stated otherwise; the work
+ *    is ordered after prior work on `stream`, and later work on `stream` sees
+ *    its results.
+ *  - Pivots: int32, 1-based, LAPACK sequential-interchange meaning: at step j
+ *    row j was interchanged with row ipiv[j]-1 (ipiv[j]-1 >= j).  Ties in the
+ *    pivot search go to the smallest row index.
+ *  - Return value: 0 on success; -i when argument i (1-based) is invalid
+ *    (nothing is launched); LU_ERR_* (< -99) for runtime failures.
+ *  - Numerical singularity is not an error: *info (device int) receives 0, or
+ *    j > 0 when U(j,j) (1-based) is exactly zero for the first such j; the
+ *    factorization is completed as LAPACK's getrf does (no interchange and no
+ *    scaling for that column).
+ *  - Every device-side wait between CTAs is bounded; when a bound expires the
+ *    kernel records LU_ERR_TIMEOUT in a library status word (see
+ *    lu_last_device_status) and returns instead of hanging.
+ */
+#ifndef GB300_LU_H
+#define GB300_LU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { LU_F64 = 0, LU_F32 = 1 } lu_dtype;
+
+enum {
+    LU_OK = 0,
+    LU_ERR_CUDA = -100,        /* a CUDA runtime call failed */
+    LU_ERR_NOMEM = -101,       /* workspace allocation failed */
+    LU_ERR_TIMEOUT = -102,     /* a bounded device-side wait expired */
+    LU_ERR_UNSUPPORTED = -103  /* valid request this build cannot serve */
+};
+
+/* Trailing-update arithmetic for LU_F32 factorizations. */
+enum {
+    LU_UPDATE_NATIVE = 0,  /* same precision as the storage (FP64 / FP32 SIMT) */
+    LU_UPDATE_BF16 = 1,    /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
+    LU_UPDATE_BF16X3 = 2   /* split BF16 on tcgen05: x = hi + lo, three products
+                              hi*hi + hi*lo + lo*hi per pair, FP32 accumulate
+                              (about 16 significant bits per product) */
+};
+
+/* Tuning knobs.  Pass NULL for the built-in choice; a zero field means "auto". */
+typedef struct {
+    int nb;            /* outer panel width b_o (section 3.1 "algorithmic block size") */
+    int nb_inner;      /* inner panel width b_i (section 4.2, outer vs inner LU) */
+    int panel_ctas;    /* CTAs in the panel cluster, 1..16 (team PF size, section 3.2) */
+    int lookahead;     /* 0 (auto) or 1: static look-ahead with worker sharing;
+                          -1: plain blocked RL without look-ahead */
+    int update;        /* LU_UPDATE_* (LU_F32 only) */
+    long long spin_ns; /* bound for device-side waits in ns (0 = 2 s) */
+} lu_opts;
+
+/*
+ * lu_factor -- P A = L U of the n x n matrix A, in place.
+ *   Section 3.1, Figure 1 (right), blocked right-looking LU: per panel of b
+ *   columns, RL1 panel LU with partial pivoting, the panel's interchanges
+ *   applied to the other columns, RL2 A12 := trilu(A11)^{-1} A12, RL3
+ *   A22 := A22 - A21 A12; with look-ahead (section 3.2, Figure 3) unless
+ *   opts->lookahead == -1.
+ *   dt    LU_F64 (dA is double*) or LU_F32 (dA is float*).
+ *   n     order, n >= 0.               dA    device, n x n, leading dim lda.
+ *   lda   >= max(1, n).                d_ipiv device int[n] (output).
+ *   d_info device int (output).        opts  host pointer or NULL.
+ *   On return A holds L (strictly lower, unit diagonal implied) and U.
+ */
+int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info,
+              const lu_opts *opts, void *stream);
+
+/*
+ * lu_solve -- X := A^{-1} B with the factors from lu_factor (no transpose).
+ *   Applies the interchanges of ipiv to B in order, then L Y = P B (unit
+ *   lower) and U X = Y (upper).  Section 1 names linear systems as the use of
+ *   the factorization.
+ *   dLU   device factors (lda).  dB device n x nrhs (ldb), overwritten by X.
+ *   nrhs >= 0.  A zero U(j,j) yields Inf/NaN, as in LAPACK.
+ */
+int lu_solve(lu_dtype dt, int n, int nrhs, const void *dLU, int lda, const int *d_ipiv,
+             void *dB, int ldb, void *stream);
+
+/*
+ * lu_factor_batched -- lu_factor applied to `batch` independent matrices of
+ * possibly different orders in ONE launch (one CTA per matrix).
+ *   d_n    device int[batch], orders (0 <= n_t <= max_n).
+ *   d_A    device array of device pointers, matrix t in column-major.
+ *   d_lda  device int[batch] (lda_t >= max(1, n_t)).
+ *   d_ipiv device array of device int* (n_t entries each).
+ *   d_info device int[batch].
+ *   max_n  host int, >= every n_t; at most 1024.
+ *   Each matrix is factored with the unblocked right-looking algorithm of
+ *   section 3.1 (Figure 1, left) with partial pivoting.
+ */
+int lu_factor_batched(lu_dtype dt, int batch, const int *d_n, void *const *d_A, const int *d_lda,
+                      int *const *d_ipiv, int *d_info, int max_n, const lu_opts *opts, void *stream);
+
+/*
+ * lu_solve_batched -- lu_solve for each member of a batch (one CTA per
+ * matrix), nrhs right-hand sides each.  d_B: device array of device pointers,
+ * d_ldb device int[batch].
+ */
+int lu_solve_batched(lu_dtype dt, int batch, int nrhs, const int *d_n, const void *const *d_LU,
+                     const int *d_lda, const int *const *d_ipiv, void *const *d_B, const int *d_ldb,
+                     int max_n, void *stream);
+
+/* Options of the mixed-precision solver.  NULL selects: split-BF16 update, auto nb,
+ * 30 iterations, tol 1e-14, GMRES-IR and FP64 fallback both enabled, no
+ * fp64_factor. */
+typedef struct {
+    int update;          /* LU_UPDATE_BF16X3 (default), LU_UPDATE_BF16 or LU_UPDATE_NATIVE (FP32) */
+    int nb;              /* outer panel width for the FP32 factorization (0 = auto) */
+    int max_iter;        /* refinement iterations before declaring a stall (0 = 30) */
+    double tol;          /* target normwise backward error (0 = 1e-14) */
+    int allow_gmres;     /* 1 enables GMRES-IR when classic refinement stalls */
+    int allow_fallback;  /* 1 enables the FP64 factorization when refinement stalls */
+    int gmres_restart;   /* Krylov dimension of GMRES-IR (0 = 30) */
+    int fp64_factor;     /* 1: skip the low-precision rungs and factor in FP64 (the
+                            FP64 path measured the same way, for comparison) */
+} lu_mixed_opts;
+
+/* Result of lu_solve_mixed (host memory, filled before the call returns). */
+typedef struct {
+    int rung;            /* 0 classic IR, 1 GMRES-IR, 2 FP64 factorization fallback */
+    int iterations;      /* refinement steps taken (all rungs) */
+    int gmres_iters;     /* total inner GMRES iterations */
+    int fell_back;       /* 1 if the FP64 factorization was used */
+    int info;            /* info of the FP32 factorization (0 = nonsingular) */
+    double backward_error;  /* final max_r ||b-Ax||_inf/(||A||_inf ||x||_inf + ||b||_inf) */
+    double t_factor_ms;  /* device time of the FP32 factorization */
+    double t_refine_ms;  /* device time of refinement (and fallback) */
+    double t_total_ms;   /* device time of the whole call */
+} lu_mixed_report;
+
+/*
+ * lu_solve_mixed -- solve A X = B to FP64 backward error `tol` using an FP32
+ * LU with a BF16 tensor-core trailing update, recovered by iterative
+ * refinement with FP64 residuals; GMRES-IR and then the FP64 factorization are
+ * the fallbacks when refinement stalls.  (The precision ladder is not in the
+ * paper; the factorization it refines is the blocked look-ahead LU above.)
+ *   dA  device FP64 n x n (lda), read only.  dB device FP64 n x nrhs (ldb),
+ *   read only.  dX device FP64 n x nrhs (ldx), output.
+ *   opts host pointer or NULL.  rep host pointer (may be NULL).
+ *   Synchronizes `stream` before returning (to fill rep).
+ */
+int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
+                   double *dX, int ldx, const lu_mixed_opts *opts, lu_mixed_report *rep,
+                   void *stream);
+
+/*
+ * lu_trailing_update -- the trailing update step alone (RL3 / RU2 of the
+ * paper): C := C - A * B with C m x n FP32 column-major (ldc), A m x k and
+ * B k x n.  `update` selects LU_UPDATE_BF16 (operands rounded to BF16,
+ * tcgen05 tensor cores, FP32 accumulate), LU_UPDATE_BF16X3 (split BF16,
+ * three products) or LU_UPDATE_NATIVE (FP32 SIMT).
+ * A (lda) and B (ldb) are FP32 column-major device matrices.  Exposed so
+ * the update kernel can be tested and timed on its own.
+ */
+int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda,
+                       const float *dB, int ldb, float *dC, int ldc, void *stream);
+
+/*
+ * lu_workspace_size -- bytes of internal workspace a call allocates
+ * (routine: "factor", "solve", "mixed"); informational.
+ */
+size_t lu_workspace_size(const char *routine, int n, int nrhs, lu_dtype dt);
+
+/* Human-readable text for a return code. */
+const char *lu_status_string(int code);
+
+/*
+ * lu_last_device_status -- LU_OK or LU_ERR_TIMEOUT recorded by a bounded
+ * device wait since the last reset.  Synchronizes `stream`.  reset != 0 clears
+ * it afterwards.
+ */
+int lu_last_device_status(void *stream, int reset);
+
+/*
+ * lu_update_timing -- instrumentation of the trailing-update launches (RL3 /
+ * PF2 / RU2), used to report the update kernel against its roofline.
+ *   enable != 0: from now on every trailing-update launch is bracketed by a
+ *   pair of CUDA events recorded on the stream it is launched on; 0 stops.
+ *   Returns 0.
+ * lu_update_timing_read -- waits for the recorded events, returns the number
+ *   of timed launches, their summed device time (ms), summed algorithmic
+ *   flops (2 m n k per launch) and summed algorithmic bytes (C read and
+ *   written once, A and B read once, at their storage widths), then clears
+ *   the record.  Host pointers; any may be NULL.
+ */
+int lu_update_timing(int enable);
+int lu_update_timing_read(long long *launches, double *total_ms, double *flops, double *bytes);
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+long long lu_kernel_launches(void);
+
+/* Version string of the build (architecture and options). */
+const char *lu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LU_H */

@@ -1,0 +1,233 @@
+"""GB300-native LU factorization with partial pivoting (PA = LU) with
+look-ahead, after arXiv:1611.06365 (blocked right-looking LU, section 3;
+malleable look-ahead, section 4).
+
+This module is the Python binding of the C ABI in ``include/lu.h``: every
+function marshals torch tensors (device memory, streams) into the library's
+plain pointers and sizes and calls the entry point of the same name.  All
+arithmetic runs in the CUDA kernels of ``liblu.so``; there is no CPU path.
+
+Matrix layout: column-major.  A torch tensor ``T`` of shape (n_cols, ld) that
+is contiguous holds the column-major matrix whose column j is ``T[j, :m]``
+(``to_colmajor`` / ``from_colmajor`` convert from/to ordinary row-major
+matrices).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build_mod
+
+__all__ = [
+    "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LuError", "lib", "build",
+    "lu_factor", "lu_solve", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
+    "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status",
+    "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_kernel_launches", "to_colmajor", "from_colmajor", "MixedReport",
+]
+
+LU_F64, LU_F32 = 0, 1
+LU_UPDATE_NATIVE, LU_UPDATE_BF16, LU_UPDATE_BF16X3 = 0, 1, 2
+LU_ERR_CUDA, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED = -100, -101, -102, -103
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+class LuError(RuntimeError):
+    def __init__(self, name, code):
+        self.code = code
+        msg = _lib.lu_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{name} returned {code}: {msg}")
+
+
+class LuOpts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("nb_inner", ctypes.c_int), ("panel_ctas", ctypes.c_int),
+                ("lookahead", ctypes.c_int), ("update", ctypes.c_int), ("spin_ns", ctypes.c_longlong)]
+
+
+class MixedOpts(ctypes.Structure):
+    _fields_ = [("update", ctypes.c_int), ("nb", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("tol", ctypes.c_double), ("allow_gmres", ctypes.c_int), ("allow_fallback", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("fp64_factor", ctypes.c_int)]
+
+
+class MixedReport(ctypes.Structure):
+    _fields_ = [("rung", ctypes.c_int), ("iterations", ctypes.c_int), ("gmres_iters", ctypes.c_int),
+                ("fell_back", ctypes.c_int), ("info", ctypes.c_int), ("backward_error", ctypes.c_double),
+                ("t_factor_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile liblu.so for sm_103a (nvcc); returns its path."""
+    return _build_mod.build(force=force)
+
+
+def lib():
+    """The loaded liblu.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        path = os.path.join(_HERE, "liblu.so")
+        if not os.path.exists(path):
+            raise ImportError(f"liblu.so is not built ({path}); run paper_1611_06365_gb300.build()")
+        L = ctypes.CDLL(path)
+        vp, i, ip = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+        L.lu_factor.argtypes = [i, i, vp, i, ip, ip, ctypes.POINTER(LuOpts), vp]
+        L.lu_solve.argtypes = [i, i, i, vp, i, ip, vp, i, vp]
+        L.lu_factor_batched.argtypes = [i, i, ip, vp, ip, vp, ip, i, ctypes.POINTER(LuOpts), vp]
+        L.lu_solve_batched.argtypes = [i, i, i, ip, vp, ip, vp, vp, ip, i, vp]
+        L.lu_solve_mixed.argtypes = [i, i, vp, i, vp, i, vp, i, ctypes.POINTER(MixedOpts),
+                                     ctypes.POINTER(MixedReport), vp]
+        L.lu_trailing_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp]
+        L.lu_workspace_size.argtypes = [ctypes.c_char_p, i, i, i]
+        L.lu_workspace_size.restype = ctypes.c_size_t
+        L.lu_status_string.argtypes = [i]
+        L.lu_status_string.restype = ctypes.c_char_p
+        L.lu_last_device_status.argtypes = [vp, i]
+        L.lu_version.restype = ctypes.c_char_p
+        L.lu_update_timing.argtypes = [i]
+        L.lu_update_timing.restype = i
+        L.lu_update_timing_read.argtypes = [ctypes.POINTER(ctypes.c_longlong)] + [ctypes.POINTER(ctypes.c_double)] * 3
+        L.lu_update_timing_read.restype = i
+        L.lu_kernel_launches.restype = ctypes.c_longlong
+        for f in ("lu_factor", "lu_solve", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
+                  "lu_trailing_update", "lu_last_device_status"):
+            getattr(L, f).restype = i
+        _lib = L
+    return _lib
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return LU_F64
+    if t.dtype == torch.float32:
+        return LU_F32
+    raise TypeError(f"unsupported dtype {t.dtype}: float64 or float32")
+
+
+def _check(name, rc):
+    if rc != 0:
+        raise LuError(name, rc)
+    return rc
+
+
+def _cm_dims(A, n=None):
+    """(n, ld) of a column-major tensor of shape (n_cols, ld)."""
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("column-major matrix expected: a (n_cols, ld) tensor with unit inner stride")
+    return (A.shape[0] if n is None else n), A.stride(0)
+
+
+def lu_factor(A, ipiv, info, n=None, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0,
+              update=LU_UPDATE_NATIVE, spin_ns=0, stream=None):
+    """P A = L U in place (see include/lu.h).  A: column-major (n, lda) tensor."""
+    n, lda = _cm_dims(A, n)
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns)
+    return _check("lu_factor", lib().lu_factor(_dtype_code(A), n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
+                                                ctypes.byref(o), _stream(stream)))
+
+
+def lu_solve(LU, ipiv, B, n=None, nrhs=None, *, stream=None):
+    """B := A^{-1} B with the factors of lu_factor.  B: column-major (nrhs, ldb)."""
+    n, lda = _cm_dims(LU, n)
+    nrhs = B.shape[0] if nrhs is None else nrhs
+    ldb = B.stride(0) if B.dim() == 2 else B.shape[0]
+    return _check("lu_solve", lib().lu_solve(_dtype_code(LU), n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B), ldb,
+                                              _stream(stream)))
+
+
+def lu_factor_batched(dtype_code, ns, A_ptrs, ldas, ipiv_ptrs, infos, max_n, *, stream=None):
+    """Batched factorization; all arguments are device tensors (pointer arrays as int64)."""
+    return _check("lu_factor_batched", lib().lu_factor_batched(dtype_code, ns.shape[0], _ptr(ns), _ptr(A_ptrs), _ptr(ldas),
+                                                                _ptr(ipiv_ptrs), _ptr(infos), max_n, None,
+                                                                _stream(stream)))
+
+
+def lu_solve_batched(dtype_code, nrhs, ns, LU_ptrs, ldas, ipiv_ptrs, B_ptrs, ldbs, max_n, *, stream=None):
+    return _check("lu_solve_batched", lib().lu_solve_batched(dtype_code, ns.shape[0], nrhs, _ptr(ns), _ptr(LU_ptrs),
+                                                              _ptr(ldas), _ptr(ipiv_ptrs), _ptr(B_ptrs), _ptr(ldbs),
+                                                              max_n, _stream(stream)))
+
+
+def lu_solve_mixed(A, B, X, n=None, *, update=LU_UPDATE_BF16X3, nb=0, max_iter=0, tol=0.0, allow_gmres=1,
+                   allow_fallback=1, gmres_restart=0, fp64_factor=0, stream=None):
+    """Mixed-precision solve A X = B (FP64 in/out).  Returns a MixedReport."""
+    n, lda = _cm_dims(A, n)
+    nrhs = B.shape[0]
+    o = MixedOpts(update, nb, max_iter, tol, allow_gmres, allow_fallback, gmres_restart, fp64_factor)
+    rep = MixedReport()
+    _check("lu_solve_mixed", lib().lu_solve_mixed(n, nrhs, _ptr(A), lda, _ptr(B), B.stride(0), _ptr(X), X.stride(0),
+                                                  ctypes.byref(o), ctypes.byref(rep), _stream(stream)))
+    return rep
+
+
+def lu_trailing_update(update, A, B, C, m, n, k, *, stream=None):
+    """C := C - A B (FP32 column-major tensors: A (k, lda), B (n, ldb), C (n, ldc))."""
+    return _check("lu_trailing_update", lib().lu_trailing_update(update, m, n, k, _ptr(A), A.stride(0), _ptr(B),
+                                                                  B.stride(0), _ptr(C), C.stride(0), _stream(stream)))
+
+
+def lu_workspace_size(routine: str, n: int, nrhs: int, dtype_code: int) -> int:
+    return lib().lu_workspace_size(routine.encode(), n, nrhs, dtype_code)
+
+
+def lu_status_string(code: int) -> str:
+    return lib().lu_status_string(code).decode()
+
+
+def lu_last_device_status(stream=None, reset=False) -> int:
+    return lib().lu_last_device_status(_stream(stream), int(bool(reset)))
+
+
+def lu_update_timing(enable: bool) -> int:
+    return lib().lu_update_timing(int(bool(enable)))
+
+
+def lu_update_timing_read():
+    """(launches, total_ms, flops, bytes) of the timed trailing-update launches."""
+    n = ctypes.c_longlong()
+    ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check("lu_update_timing_read", lib().lu_update_timing_read(ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                                                 ctypes.byref(by)))
+    return n.value, ms.value, fl.value, by.value
+
+
+def lu_kernel_launches() -> int:
+    return lib().lu_kernel_launches()
+
+
+def lu_version() -> str:
+    return lib().lu_version().decode()
+
+
+def to_colmajor(M, ld=None):
+    """Row-major (m, n) torch matrix -> column-major (n, ld) tensor (copy)."""
+    import torch
+    m, n = M.shape
+    ld = m if ld is None else ld
+    T = torch.zeros((n, ld), dtype=M.dtype, device=M.device)
+    T[:, :m] = M.t()
+    return T
+
+
+def from_colmajor(T, m=None):
+    """Inverse of to_colmajor: column-major (n, ld) tensor -> row-major (m, n) matrix."""
+    m = T.shape[1] if m is None else m
+    return T[:, :m].t().contiguous()

@@ -1,0 +1,637 @@
+// C ABI of liblu (declared in include/lu.h) and the host-side scheduler of the
+// blocked right-looking LU with look-ahead.
+//
+// Schedule (section 3.2, Figure 3; section 4.1 for worker sharing).  Two
+// streams per device: P (highest priority) carries the panel branch T_PF and
+// U (lowest priority) the remainder branch T_RU.  For outer iteration k
+// (panel k already factored on P, its interchanges in row map k):
+//
+//   U:  wait panel(k) | interchanges on the columns left of panel k |
+//       RU1: interchanges + TRSM on the columns right of strip k+1 |
+//       RU2: update of those columns
+//   P:  wait RU2(k-1) | PF1: interchanges + TRSM on strip k+1 |
+//       PF2: update of strip k+1 | PF3: factor panel k+1 (cluster kernel)
+//
+// No kernel waits on another kernel: the branches are ordered with CUDA
+// events only.  Worker sharing comes from the GPU's CTA scheduler: RU2 is a
+// grid with many more tiles than SMs, so when the panel cluster exits its SMs
+// are handed the RU2 tiles still queued -- the GPU counterpart of the paper's
+// malleable BLAS, where PF threads join RU2 at the next Loop-4 boundary.
+//
+// An outer panel wider than what one cluster holds in shared memory is
+// factored by the inner/outer scheme of section 4.2 (Figure 6): inner panels
+// of width b_i on the cluster, each followed by its interchanges, TRSM and
+// update restricted to the outer panel.
+#include "common.cuh"
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+namespace lu {
+// panel.cu
+template <typename T>
+cudaError_t launch_panel(T *P, int lda, int m, int W, int *ipiv, int row_base, int *info, int max_ctas, size_t smem_cap,
+                         cudaStream_t s);
+int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap);
+// swap_trsm.cu
+cudaError_t launch_pivot_map(const int *ipiv, int kb, int b, int *map, int *perm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c_begin, int c_end, int do_trsm,
+                             __nv_bfloat16 *stage, int ldst, int stage_c0, int stage_k, int split, cudaStream_t s);
+// gemm_simt.cu
+template <typename T>
+cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s);
+// gemm_tc.cu
+cudaError_t make_stage_maps(CUtensorMap *mapA, const __nv_bfloat16 *stageA, int rowsA, CUtensorMap *mapB,
+                            const __nv_bfloat16 *stageB, int colsB, int kinner, int lds);
+int tc_box_rows();
+int tc_box_cols();
+cudaError_t make_stage_map(CUtensorMap *map, const __nv_bfloat16 *base, int kpad, int outer, int lds, int box_outer);
+cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
+                           int b_col0, float *C, int ldc, int *status, long long bound_ns, cudaStream_t s);
+cudaError_t launch_stage_rows(int rows, int k, int kpad, const float *L, int ld, __nv_bfloat16 *stage, int lds, int split,
+                              cudaStream_t s);
+cudaError_t launch_stage_cols(int k, int kpad, int cols, const float *B, int ld, __nv_bfloat16 *stage, int lds, int split,
+                              cudaStream_t s);
+int tc_kpad(int k);
+int tc_max_k();
+// solve.cu
+cudaError_t launch_ipiv_to_perm(const int *ipiv, int n, int *perm, cudaStream_t s);
+template <typename TI, typename TO>
+cudaError_t launch_gather_rows(int n, int nrhs, const int *perm, const TI *B, int ldb, TO *X, int ldx, cudaStream_t s);
+template <typename T>
+cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status, long long bound_ns,
+                             int sms, cudaStream_t s);
+size_t trsv_workspace_ints(int n);
+cudaError_t launch_iota(int *v, int n, cudaStream_t s);
+// batched.cu
+template <typename T>
+cudaError_t launch_getrf_batched(int batch, const int *ns, T *const *As, const int *ldas, int *const *ipivs, int *infos,
+                                 int max_n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_getrs_batched(int batch, int nrhs, const int *ns, const T *const *LUs, const int *ldas,
+                                 const int *const *ipivs, T *const *Bs, const int *ldbs, int max_n, cudaStream_t s);
+// mixed.cu
+cudaError_t launch_cast_rowsum(int n, const double *A, int lda, float *A32, int lda32, double *rowsum, cudaStream_t s);
+size_t residual_workspace_doubles(int n, int nrhs);
+cudaError_t launch_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B, int ldb,
+                            double *R, int ldr, double *part, unsigned long long *rmax, cudaStream_t s);
+cudaError_t launch_absmax(int n, int nrhs, const double *V, int ldv, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_vecmax(int n, const double *v, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_to_f32_scaled(int n, int nrhs, const double *R, int ldr, const unsigned long long *rmax, float *R32,
+                                 int ldr32, cudaStream_t s);
+cudaError_t launch_axpy_scaled(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax, double *X, int ldx,
+                               cudaStream_t s);
+}  // namespace lu
+
+using namespace lu;
+
+// ---------------------------------------------------------------------------
+// per-device state
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kMaxDev = 64;
+constexpr size_t kPanelSmemCap = 200 * 1024;
+
+struct DevState {
+    bool init = false;
+    cudaStream_t P = nullptr, U = nullptr;
+    cudaEvent_t evP[2] = {nullptr, nullptr}, evU[2] = {nullptr, nullptr};
+    cudaEvent_t evIn = nullptr, evOutP = nullptr, evOutU = nullptr;
+    int *status = nullptr;   // device status word
+    int sms = 0;
+};
+
+DevState g_dev[kMaxDev];
+std::mutex g_mu;
+std::recursive_mutex g_enqueue_mu;   // the per-device streams/events serve one enqueue at a time
+char g_last_err[512];
+
+cudaError_t dev_state(DevState **out) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= kMaxDev) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &st = g_dev[d];
+    if (!st.init) {
+        int lo = 0, hi = 0;
+        if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithPriority(&st.P, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithPriority(&st.U, cudaStreamNonBlocking, lo)) != cudaSuccess) return e;
+        for (int i = 0; i < 2; ++i) {
+            if ((e = cudaEventCreateWithFlags(&st.evP[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&st.evU[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventCreateWithFlags(&st.evIn, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&st.evOutP, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&st.evOutU, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&st.status, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMemset(st.status, 0, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, d)) != cudaSuccess) return e;
+        st.init = true;
+    }
+    *out = &st;
+    return cudaSuccess;
+}
+
+// stream-ordered workspace that is released on the caller's stream
+struct Workspace {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Workspace(cudaStream_t st) : s(st) {}
+    template <typename T>
+    cudaError_t get(T **p, size_t count) {
+        void *v = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMallocAsync(&v, count * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(v);
+        *p = static_cast<T *>(v);
+        return cudaSuccess;
+    }
+    ~Workspace() {
+        for (void *v : ptrs) cudaFreeAsync(v, s);
+    }
+};
+
+}  // namespace
+
+static std::atomic<long long> g_launches{0};
+void lu_count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// trailing-update instrumentation (lu_update_timing)
+namespace {
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<TimedLaunch> g_timed;
+
+bool timing_on() {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    return g_timing;
+}
+}  // namespace
+
+void lu_note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+    if (getenv("LU_DEBUG")) fprintf(stderr, "liblu: %s\n", g_last_err);
+}
+
+int *lu_device_status_ptr() {
+    DevState *st = nullptr;
+    if (dev_state(&st) != cudaSuccess) return nullptr;
+    return st->status;
+}
+
+long long lu_spin_bound_ns(const lu_opts *o) {
+    if (o && o->spin_ns > 0) return o->spin_ns;
+    return 2000000000LL;
+}
+
+// ---------------------------------------------------------------------------
+// blocked right-looking LU with look-ahead
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Plan {
+    int bo = 0;       // outer panel width
+    int bi = 0;       // inner panel width (cluster capacity)
+    bool tc = false;  // BF16 tensor-core update
+    int nprod = 1;    // 1: BF16, 3: split BF16
+    bool lookahead = true;
+    int panel_ctas = 16;
+    long long bound = 2000000000LL;
+};
+
+template <typename T>
+Plan make_plan(int n, const lu_opts *o) {
+    Plan p;
+    const int wfit = std::max(1, panel_width_that_fits(std::max(n, 1), sizeof(T), kPanelSmemCap, 64));
+    const bool tc = (sizeof(T) == 4) && o && (o->update == LU_UPDATE_BF16 || o->update == LU_UPDATE_BF16X3);
+    p.tc = tc;
+    p.nprod = (o && o->update == LU_UPDATE_BF16X3) ? 3 : 1;
+    if (tc) {
+        p.bo = (o && o->nb > 0) ? o->nb : (n >= 8192 ? 256 : (n >= 2048 ? 128 : 64));
+        p.bo = std::min(p.bo, tc_max_k());
+        p.bi = (o && o->nb_inner > 0) ? std::min(o->nb_inner, wfit) : std::min(32, wfit);
+    } else {
+        p.bo = (o && o->nb > 0) ? o->nb : wfit;
+        p.bi = (o && o->nb_inner > 0) ? std::min(o->nb_inner, wfit) : std::min(p.bo, wfit);
+    }
+    p.bi = std::max(1, std::min(p.bi, p.bo));
+    p.lookahead = !(o && o->lookahead < 0);
+    p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : 16;
+    p.bound = lu_spin_bound_ns(o);
+    return p;
+}
+
+template <typename T>
+struct FactorCtx {
+    int n;
+    T *A;
+    int lda;
+    int *ipiv;
+    int *info;
+    int *perm;            // optional
+    Plan pl;
+    DevState *st;
+    int *maps[3];         // 2 outer (parity) + 1 inner
+    __nv_bfloat16 *stA[2] = {nullptr, nullptr};
+    __nv_bfloat16 *stB = nullptr;
+    int kpad = 0;
+    int kinner = 0;   // staged elements per row/column (kpad, or 2 kpad when split)
+    CUtensorMap mapA[2], mapB;
+};
+
+template <typename T>
+cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s);
+
+// C[rows r0.., cols c0..c1) -= L(rows r0.., cols kb..kb+w) * U(rows kb..kb+w, cols c0..c1)
+template <typename T>
+cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s) {
+    const int r0 = kb + w;
+    const int m = c.n - r0, nn = c1 - c0;
+    if (m <= 0 || nn <= 0) return cudaSuccess;
+    if (!timing_on()) return update_launch<T>(c, k_par, kb, w, c0, c1, s);
+    TimedLaunch t;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&t.a)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&t.b)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(t.a, s)) != cudaSuccess) return e;
+    if ((e = update_launch<T>(c, k_par, kb, w, c0, c1, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(t.b, s)) != cudaSuccess) return e;
+    const int k = c.pl.tc ? c.kpad : w;
+    const double opw = c.pl.tc ? 2.0 : (double)sizeof(T);
+    t.flops = 2.0 * m * nn * (double)w;
+    t.bytes = 2.0 * m * nn * sizeof(T) + (double)m * k * opw + (double)k * nn * opw;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timed.push_back(t);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s) {
+    const int r0 = kb + w;
+    const int m = c.n - r0, nn = c1 - c0;
+    if constexpr (sizeof(T) == 4) {
+        if (c.pl.tc)
+            return launch_gemm_tc(c.pl.nprod, m, nn, c.kpad, c.mapA[k_par], 0, c.mapB, c0 - r0,
+                                  reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda, c.st->status, c.pl.bound, s);
+    }
+    return launch_gemm_simt<T>(m, nn, w, c.A + r0 + (size_t)kb * c.lda, c.lda, c.A + kb + (size_t)c0 * c.lda, c.lda,
+                               c.A + r0 + (size_t)c0 * c.lda, c.lda, s);
+}
+
+template <typename T>
+cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, int c1, int do_trsm, cudaStream_t s) {
+    __nv_bfloat16 *stage = (do_trsm && c.pl.tc) ? c.stB : nullptr;
+    return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, stage, c.kinner, kb + w, c.kpad, c.pl.nprod == 3, s);
+}
+
+// Factor outer panel at column kb (width w) on stream s; leaves row map in maps[par].
+template <typename T>
+cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s) {
+    const int n = c.n, lda = c.lda;
+    cudaError_t e;
+    for (int ib = 0; ib < w; ib += c.pl.bi) {
+        const int wi = std::min(c.pl.bi, w - ib);
+        const int col = kb + ib;
+        e = launch_panel<T>(c.A + col + (size_t)col * lda, lda, n - col, wi, c.ipiv + col, col, c.info, c.pl.panel_ctas,
+                            kPanelSmemCap, s);
+        if (e != cudaSuccess) return e;
+        if (wi < w) {
+            int *mi = c.maps[2];
+            if ((e = launch_pivot_map(c.ipiv, col, wi, mi, nullptr, s)) != cudaSuccess) return e;
+            if (ib > 0 && (e = launch_swap_trsm<T>(c.A, lda, col, wi, mi, kb, col, 0, nullptr, 0, 0, 0, 0, s)) != cudaSuccess)
+                return e;
+            if (ib + wi < w) {
+                if ((e = launch_swap_trsm<T>(c.A, lda, col, wi, mi, col + wi, kb + w, 1, nullptr, 0, 0, 0, 0, s)) != cudaSuccess)
+                    return e;
+                const int r0 = col + wi;
+                if ((e = launch_gemm_simt<T>(n - r0, kb + w - r0, wi, c.A + r0 + (size_t)col * lda, lda,
+                                             c.A + col + (size_t)r0 * lda, lda, c.A + r0 + (size_t)r0 * lda, lda, s)) !=
+                    cudaSuccess)
+                    return e;
+            }
+        }
+    }
+    if ((e = launch_pivot_map(c.ipiv, kb, w, c.maps[par], c.perm, s)) != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4) {
+        if (c.pl.tc && kb + w < n) {
+            e = launch_stage_rows(n - kb - w, w, c.kpad, reinterpret_cast<const float *>(c.A) + (kb + w) + (size_t)kb * lda, lda,
+                                  c.stA[par], c.kinner, c.pl.nprod == 3, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+int factor_impl(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Plan &pl, cudaStream_t caller) {
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
+    LU_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), caller));
+    if (n == 0) return LU_OK;
+    std::lock_guard<std::recursive_mutex> lk(g_enqueue_mu);
+    Workspace ws(caller);
+    FactorCtx<T> c;
+    c.n = n; c.A = A; c.lda = lda; c.ipiv = ipiv; c.info = info; c.perm = perm; c.pl = pl; c.st = st;
+    const int bo = pl.bo;
+    for (int i = 0; i < 3; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
+    if (perm) LU_CUDA_TRY(launch_iota(perm, n, caller));
+    if (pl.tc) {
+        c.kpad = tc_kpad(bo);
+        c.kinner = c.kpad * (pl.nprod == 3 ? 2 : 1);
+        for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.stA[i], (size_t)n * c.kinner));
+        LU_CUDA_TRY(ws.get(&c.stB, (size_t)n * c.kinner));
+        for (int i = 0; i < 2; ++i) LU_CUDA_TRY(make_stage_map(&c.mapA[i], c.stA[i], c.kinner, n, c.kinner, tc_box_rows()));
+        LU_CUDA_TRY(make_stage_map(&c.mapB, c.stB, c.kinner, n, c.kinner, tc_box_cols()));
+    }
+    cudaStream_t P = st->P, U = st->U;
+    LU_CUDA_TRY(cudaEventRecord(st->evIn, caller));
+    LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evIn, 0));
+    LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evIn, 0));
+
+    const int nblk = (n + bo - 1) / bo;
+    // prologue: panel 0
+    LU_CUDA_TRY(factor_outer_panel<T>(c, 0, std::min(bo, n), 0, P));
+    LU_CUDA_TRY(cudaEventRecord(st->evP[0], P));
+    for (int k = 0; k < nblk; ++k) {
+        const int kb = k * bo, w = std::min(bo, n - kb), par = k & 1;
+        const int cn0 = kb + w, wn = std::min(bo, n - cn0);
+        const int *map = c.maps[par];
+        // ---- T_RU on U -------------------------------------------------------
+        LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evP[par], 0));
+        if (kb > 0) LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, 0, kb, 0, U));
+        const int rest0 = pl.lookahead ? cn0 + wn : cn0;
+        if (rest0 < n) {
+            LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, rest0, n, 1, U));
+            LU_CUDA_TRY(update<T>(c, par, kb, w, rest0, n, U));
+        }
+        LU_CUDA_TRY(cudaEventRecord(st->evU[par], U));
+        // ---- T_PF on P: next panel --------------------------------------------
+        if (wn > 0) {
+            if (pl.lookahead) {
+                if (k > 0) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par ^ 1], 0));
+                LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P));
+                LU_CUDA_TRY(update<T>(c, par, kb, w, cn0, cn0 + wn, P));
+            } else {
+                LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par], 0));
+            }
+            LU_CUDA_TRY(factor_outer_panel<T>(c, cn0, wn, par ^ 1, P));
+            LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
+        }
+    }
+    LU_CUDA_TRY(cudaEventRecord(st->evOutP, P));
+    LU_CUDA_TRY(cudaEventRecord(st->evOutU, U));
+    LU_CUDA_TRY(cudaStreamWaitEvent(caller, st->evOutP, 0));
+    LU_CUDA_TRY(cudaStreamWaitEvent(caller, st->evOutU, 0));
+    LU_CUDA_TRY(cudaGetLastError());
+    return LU_OK;
+}
+
+template <typename T>
+int solve_impl(int n, int nrhs, const T *LU, int lda, const int *ipiv, const int *perm_opt, T *B, int ldb, long long bound,
+               cudaStream_t s) {
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
+    if (n == 0 || nrhs == 0) return LU_OK;
+    Workspace ws(s);
+    int *perm = const_cast<int *>(perm_opt);
+    if (!perm) {
+        LU_CUDA_TRY(ws.get(&perm, n));
+        LU_CUDA_TRY(launch_ipiv_to_perm(ipiv, n, perm, s));
+    }
+    T *X = nullptr;
+    LU_CUDA_TRY(ws.get(&X, (size_t)n * nrhs));
+    LU_CUDA_TRY((launch_gather_rows<T, T>(n, nrhs, perm, B, ldb, X, n, s)));
+    int *tws = nullptr;
+    LU_CUDA_TRY(ws.get(&tws, trsv_workspace_ints(n)));
+    LU_CUDA_TRY(launch_trsv_pair<T>(LU, lda, n, nrhs, X, n, tws, st->status, bound, st->sms, s));
+    LU_CUDA_TRY(cudaMemcpy2DAsync(B, sizeof(T) * ldb, X, sizeof(T) * n, sizeof(T) * n, nrhs, cudaMemcpyDeviceToDevice, s));
+    return LU_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info, const lu_opts *opts, void *stream) {
+    if (dt != LU_F64 && dt != LU_F32) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && !dA) return -3;
+    if (lda < std::max(1, n)) return -4;
+    if (n > 0 && !d_ipiv) return -5;
+    if (!d_info) return -6;
+    if (opts && (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 ||
+                 (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3)))
+        return -7;
+    if (opts && opts->update != LU_UPDATE_NATIVE && dt != LU_F32) return -7;
+    if (opts && opts->update != LU_UPDATE_NATIVE && opts->nb > tc_max_k()) return -7;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dt == LU_F64) {
+        Plan p = make_plan<double>(n, opts);
+        return factor_impl<double>(n, static_cast<double *>(dA), lda, d_ipiv, d_info, nullptr, p, s);
+    }
+    Plan p = make_plan<float>(n, opts);
+    return factor_impl<float>(n, static_cast<float *>(dA), lda, d_ipiv, d_info, nullptr, p, s);
+}
+
+int lu_solve(lu_dtype dt, int n, int nrhs, const void *dLU, int lda, const int *d_ipiv, void *dB, int ldb, void *stream) {
+    if (dt != LU_F64 && dt != LU_F32) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (n > 0 && !dLU) return -4;
+    if (lda < std::max(1, n)) return -5;
+    if (n > 0 && !d_ipiv) return -6;
+    if (n > 0 && nrhs > 0 && !dB) return -7;
+    if (ldb < std::max(1, n)) return -8;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dt == LU_F64)
+        return solve_impl<double>(n, nrhs, static_cast<const double *>(dLU), lda, d_ipiv, nullptr, static_cast<double *>(dB),
+                                  ldb, lu_spin_bound_ns(nullptr), s);
+    return solve_impl<float>(n, nrhs, static_cast<const float *>(dLU), lda, d_ipiv, nullptr, static_cast<float *>(dB), ldb,
+                             lu_spin_bound_ns(nullptr), s);
+}
+
+int lu_factor_batched(lu_dtype dt, int batch, const int *d_n, void *const *d_A, const int *d_lda, int *const *d_ipiv,
+                      int *d_info, int max_n, const lu_opts *opts, void *stream) {
+    (void)opts;
+    if (dt != LU_F64 && dt != LU_F32) return -1;
+    if (batch < 0) return -2;
+    if (batch > 0 && !d_n) return -3;
+    if (batch > 0 && !d_A) return -4;
+    if (batch > 0 && !d_lda) return -5;
+    if (batch > 0 && !d_ipiv) return -6;
+    if (batch > 0 && !d_info) return -7;
+    if (max_n < 0 || max_n > 1024) return -8;
+    if (batch > 2147483647 / 2) return -2;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dt == LU_F64)
+        LU_CUDA_TRY(launch_getrf_batched<double>(batch, d_n, reinterpret_cast<double *const *>(d_A), d_lda, d_ipiv, d_info, max_n, s));
+    else
+        LU_CUDA_TRY(launch_getrf_batched<float>(batch, d_n, reinterpret_cast<float *const *>(d_A), d_lda, d_ipiv, d_info, max_n, s));
+    return LU_OK;
+}
+
+int lu_solve_batched(lu_dtype dt, int batch, int nrhs, const int *d_n, const void *const *d_LU, const int *d_lda,
+                     const int *const *d_ipiv, void *const *d_B, const int *d_ldb, int max_n, void *stream) {
+    if (dt != LU_F64 && dt != LU_F32) return -1;
+    if (batch < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (batch > 0 && !d_n) return -4;
+    if (batch > 0 && !d_LU) return -5;
+    if (batch > 0 && !d_lda) return -6;
+    if (batch > 0 && !d_ipiv) return -7;
+    if (batch > 0 && !d_B) return -8;
+    if (batch > 0 && !d_ldb) return -9;
+    if (max_n < 0 || max_n > 1024) return -10;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dt == LU_F64)
+        LU_CUDA_TRY(launch_getrs_batched<double>(batch, nrhs, d_n, reinterpret_cast<const double *const *>(d_LU), d_lda, d_ipiv,
+                                                 reinterpret_cast<double *const *>(d_B), d_ldb, max_n, s));
+    else
+        LU_CUDA_TRY(launch_getrs_batched<float>(batch, nrhs, d_n, reinterpret_cast<const float *const *>(d_LU), d_lda, d_ipiv,
+                                                reinterpret_cast<float *const *>(d_B), d_ldb, max_n, s));
+    return LU_OK;
+}
+
+int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda, const float *dB, int ldb, float *dC,
+                       int ldc, void *stream) {
+    if (update != LU_UPDATE_NATIVE && update != LU_UPDATE_BF16 && update != LU_UPDATE_BF16X3) return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (k < 0 || (update != LU_UPDATE_NATIVE && k > tc_max_k())) return -4;
+    if (m > 0 && k > 0 && !dA) return -5;
+    if (lda < std::max(1, m)) return -6;
+    if (n > 0 && k > 0 && !dB) return -7;
+    if (ldb < std::max(1, k)) return -8;
+    if (m > 0 && n > 0 && !dC) return -9;
+    if (ldc < std::max(1, m)) return -10;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (m == 0 || n == 0 || k == 0) return LU_OK;
+    if (update == LU_UPDATE_NATIVE) {
+        LU_CUDA_TRY(launch_gemm_simt<float>(m, n, k, dA, lda, dB, ldb, dC, ldc, s));
+        return LU_OK;
+    }
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
+    Workspace ws(s);
+    const int kpad = tc_kpad(k);
+    const int split = update == LU_UPDATE_BF16X3;
+    const int kinner = kpad * (split ? 2 : 1);
+    __nv_bfloat16 *sa = nullptr, *sb = nullptr;
+    LU_CUDA_TRY(ws.get(&sa, (size_t)m * kinner));
+    LU_CUDA_TRY(ws.get(&sb, (size_t)n * kinner));
+    LU_CUDA_TRY(launch_stage_rows(m, k, kpad, dA, lda, sa, kinner, split, s));
+    LU_CUDA_TRY(launch_stage_cols(k, kpad, n, dB, ldb, sb, kinner, split, s));
+    CUtensorMap ma, mb;
+    LU_CUDA_TRY(make_stage_maps(&ma, sa, m, &mb, sb, n, kinner, kinner));
+    LU_CUDA_TRY(launch_gemm_tc(split ? 3 : 1, m, n, kpad, ma, 0, mb, 0, dC, ldc, st->status, lu_spin_bound_ns(nullptr), s));
+    return LU_OK;
+}
+
+size_t lu_workspace_size(const char *routine, int n, int nrhs, lu_dtype dt) {
+    if (!routine || n < 0 || nrhs < 0) return 0;
+    const size_t N = (size_t)n, elem = dt == LU_F64 ? 8 : 4;
+    if (!strcmp(routine, "factor")) return 3 * (1 + 4 * 256) * sizeof(int) + (dt == LU_F32 ? 3 * N * 512 * 2 : 0);
+    if (!strcmp(routine, "solve")) return N * sizeof(int) + N * nrhs * elem + trsv_workspace_ints(n) * sizeof(int);
+    if (!strcmp(routine, "mixed"))
+        return N * N * 4 + N * sizeof(int) * 2 + 3 * N * 512 * 2 + residual_workspace_doubles(n, nrhs) * 8 +
+               N * nrhs * (8 * 2 + 4 * 2) + N * 8;
+    return 0;
+}
+
+const char *lu_status_string(int code) {
+    switch (code) {
+        case LU_OK: return "success";
+        case LU_ERR_CUDA: return "CUDA runtime error";
+        case LU_ERR_NOMEM: return "workspace allocation failed";
+        case LU_ERR_TIMEOUT: return "a bounded device-side wait expired";
+        case LU_ERR_UNSUPPORTED: return "unsupported request";
+        default: break;
+    }
+    if (code < 0 && code > -100) return "invalid argument (return value -i names argument i)";
+    return "unknown status";
+}
+
+int lu_last_device_status(void *stream, int reset) {
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    LU_CUDA_TRY(cudaMemcpyAsync(&v, st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaStreamSynchronize(s));
+    if (reset) LU_CUDA_TRY(cudaMemsetAsync(st->status, 0, sizeof(int), s));
+    return v;
+}
+
+int lu_update_timing(int enable) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timing = enable != 0;
+    return LU_OK;
+}
+
+int lu_update_timing_read(long long *launches, double *total_ms, double *flops, double *bytes) {
+    std::vector<TimedLaunch> v;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        v.swap(g_timed);
+    }
+    double ms = 0.0, fl = 0.0, by = 0.0;
+    int rc = LU_OK;
+    for (auto &t : v) {
+        float e = 0.f;
+        cudaError_t st = cudaEventSynchronize(t.b);
+        if (st == cudaSuccess) st = cudaEventElapsedTime(&e, t.a, t.b);
+        if (st != cudaSuccess) rc = LU_ERR_CUDA;
+        ms += e;
+        fl += t.flops;
+        by += t.bytes;
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    if (launches) *launches = (long long)v.size();
+    if (total_ms) *total_ms = ms;
+    if (flops) *flops = fl;
+    if (bytes) *bytes = by;
+    return rc;
+}
+
+long long lu_kernel_launches(void) { return g_launches.load(); }
+
+const char *lu_version(void) { return "liblu 0.1 (sm_103a; cluster panel, tcgen05 BF16 update, FP64 DFMA update)"; }
+
+}  // extern "C"
+
+// internal entry points used by the mixed-precision driver (mixed_api.cu)
+namespace lu {
+int factor_f32_internal(int n, float *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s) {
+    Plan p = make_plan<float>(n, o);
+    return factor_impl<float>(n, A, lda, ipiv, info, perm, p, s);
+}
+int factor_f64_internal(int n, double *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s) {
+    Plan p = make_plan<double>(n, o);
+    return factor_impl<double>(n, A, lda, ipiv, info, perm, p, s);
+}
+int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s) {
+    return solve_impl<float>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s);
+}
+int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s) {
+    return solve_impl<double>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s);
+}
+}  // namespace lu

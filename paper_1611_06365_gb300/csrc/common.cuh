@@ -1,0 +1,72 @@
+// Shared device/host helpers of liblu (CUDA path only).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include "../../include/lu.h"
+
+#define LU_CUDA_TRY(expr)                                                       \
+    do {                                                                        \
+        cudaError_t _e = (expr);                                                \
+        if (_e != cudaSuccess) {                                                \
+            lu_note_cuda_error(_e, #expr, __FILE__, __LINE__);                  \
+            return LU_ERR_CUDA;                                                 \
+        }                                                                       \
+    } while (0)
+
+void lu_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Library-wide device status word (LU_OK or LU_ERR_TIMEOUT), one per device.
+int *lu_device_status_ptr();
+// Counts kernel launches of this library (reported by lu_kernel_launches).
+void lu_count_launch(int k = 1);
+// Default bound for device-side waits, in globaltimer nanoseconds.
+long long lu_spin_bound_ns(const lu_opts *o);
+
+__device__ __forceinline__ unsigned long long lu_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int lu_ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void lu_st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded spin until *flag >= target.  Returns false (and records
+// LU_ERR_TIMEOUT in *status) when `bound_ns` of globaltimer time has passed.
+__device__ __forceinline__ bool lu_wait_flag(const int *flag, int target, int *status, long long bound_ns) {
+    if (lu_ld_acquire(flag) >= target) return true;
+    unsigned long long t0 = lu_globaltimer();
+    unsigned int spins = 0;
+    while (lu_ld_acquire(flag) < target) {
+        if (((++spins) & 63u) == 0u) {
+            if ((long long)(lu_globaltimer() - t0) > bound_ns) {
+                atomicExch(status, (int)LU_ERR_TIMEOUT);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+    return true;
+}
+
+template <typename T> struct lu_abs_t;
+template <> struct lu_abs_t<double> { __device__ static double f(double x) { return fabs(x); } };
+template <> struct lu_abs_t<float>  { __device__ static float f(float x) { return fabsf(x); } };
+template <typename T> __device__ __forceinline__ T lu_abs(T x) { return lu_abs_t<T>::f(x); }
+
+// (|v|, row) maximum with the smallest row winning ties.  NaN magnitudes never
+// win (comparisons with NaN are false), an invalid candidate has mag = -1.
+template <typename T>
+__device__ __forceinline__ bool lu_better(T mag_a, int idx_a, T mag_b, int idx_b) {
+    return (mag_a > mag_b) || (mag_a == mag_b && idx_a < idx_b);
+}
+
+static inline int lu_ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

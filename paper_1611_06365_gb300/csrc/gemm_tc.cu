@@ -1,0 +1,424 @@
+// Trailing update RL3 / PF2 / RU2 (section 3.1, Figure 1 right; section 3.2,
+// Figure 3) on the 5th-generation tensor cores: C := C - A * B with C in FP32
+// and the operands A = L21 and B = U12 rounded to BF16.
+//
+// Per CTA one 128 x 64 tile of C and the whole K (<= 256):
+//   * thread 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle) of
+//     the K-major BF16 operand tiles, one mbarrier per 64-wide K chunk;
+//   * thread 0 issues tcgen05.mma (kind::f16, M=128, N=64, K=16 per
+//     instruction) as soon as each chunk lands, accumulating in TMEM;
+//   * meanwhile all 128 threads prefetch their row of the C tile into
+//     registers (column-major C: a warp reads 128 contiguous bytes per column);
+//   * after tcgen05.commit signals the accumulator, each warp reads its 32
+//     TMEM lanes (tcgen05.ld 32x32b) and writes C - acc.
+// Two CTAs fit on an SM (about 100 KB of shared memory each), so one CTA's
+// epilogue (the HBM-bound part: C read and write in FP32) overlaps the other's
+// loads and MMAs.  Every mbarrier wait is bounded; on expiry the kernel records
+// LU_ERR_TIMEOUT, waits once more (bounded) for its own copies, frees its TMEM
+// and returns.
+//
+// Operand staging (BF16, K contiguous, K padded to a multiple of 64 with zeros):
+//   A: row-major, element (i, k) at stageA[i * lds + k]  (the panel's L21)
+//   B: column-major, element (k, j) at stageB[j * lds + k]  (U12 by columns)
+#include "common.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+namespace lu {
+
+constexpr int kTcBM = 128;
+constexpr int kTcBN = 128;
+constexpr int kTcBK = 64;            // one 128-byte swizzle span of BF16
+constexpr int kTcMaxK = 256;
+constexpr int kTcThreads = 192;      // 6 warps: TMA, MMA, 4 x epilogue
+constexpr int kTcChunkA = kTcBM * kTcBK * 2;   // 16 KB
+constexpr int kTcChunkB = kTcBN * kTcBK * 2;   // 16 KB
+constexpr size_t kTcSmem = 1024 + (size_t)6 * (kTcChunkA + kTcChunkB) + 256;   // 6 x1 stages = 3 x3 stages
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on phase `parity` of an mbarrier
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long bound_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = lu_globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((long long)(lu_globaltimer() - t0) > bound_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
+// atoms of 1024 bytes stacked along M/N (stride byte offset 1024).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                       // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
+    d |= (uint64_t)1 << 46;                       // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                       // swizzle: 128 B
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D=F32, A=B=BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Persistent, warp-specialized tile loop (one CTA per SM):
+//   warp 0  TMA producer: K chunks of the A and B tiles into a ring of
+//           shared-memory stages (full/empty mbarrier pair per stage);
+//   warp 1  MMA issuer: NPROD products per chunk into one of two TMEM
+//           accumulators (128 lanes x kTcBN columns each), tcgen05.commit
+//           frees the stage and, after the last chunk, hands the
+//           accumulator to the epilogue;
+//   warps 2-5  epilogue: prefetch the C tile row of each thread while the
+//           MMAs run, then C := C - acc from TMEM (tcgen05.ld), and release
+//           the accumulator so the MMAs of the tile after next can start.
+// NPROD = 1: C -= A_hi B_hi (plain BF16 operands).
+// NPROD = 3: split BF16, x = x_hi + x_lo with x_hi = bf16(x),
+//            x_lo = bf16(x - x_hi): C -= A_hi B_hi + A_hi B_lo + A_lo B_hi,
+//            about 16 significant bits per product instead of 8.
+template <int NPROD>
+__global__ void __launch_bounds__(kTcThreads, 1)
+gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, int a_row0,
+               const __grid_constant__ CUtensorMap mapB, int b_col0, float *__restrict__ C, int ldc,
+               int *__restrict__ status, long long bound_ns) {
+    constexpr int NSPLIT = NPROD == 1 ? 1 : 2;
+    constexpr uint32_t kStageBytes = (uint32_t)NSPLIT * (kTcChunkA + kTcChunkB);
+    constexpr int kStages = NPROD == 1 ? 6 : 3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = smem_raw + (base - raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + (size_t)kStages * kStageBytes);
+    // bars: full[kStages], empty[kStages], acc_full[2], acc_empty[2]
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * kStages;
+    const uint32_t accf0 = empty0 + 8u * kStages, acce0 = accf0 + 16u;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nk = K / kTcBK;                       // K is a multiple of kTcBK
+    const int kpad_off = K;                         // lo halves start at x = K
+    const int mt = (m + kTcBM - 1) / kTcBM, ntl = (n + kTcBN - 1) / kTcBN;
+    const int ntiles = mt * ntl;
+
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) { mbar_init(full0 + 8u * i, 1); mbar_init(empty0 + 8u * i, 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(accf0 + 8u * i, 1); mbar_init(acce0 + 8u * i, 128); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * kTcBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const int tm = (t % mt) * kTcBM, tn = (t / mt) * kTcBN;
+                for (int kc = 0; kc < nk; ++kc) {
+                    if (!mbar_wait_bounded(empty0 + 8u * s, ph ^ 1u, bound_ns)) { *abort_flag = 1; break; }
+                    const uint32_t st = base + (uint32_t)s * kStageBytes;
+                    const uint32_t fb = full0 + 8u * s;
+                    mbar_expect_tx(fb, kStageBytes);
+                    tma_load_2d(st, &mapA, kc * kTcBK, a_row0 + tm, fb);
+                    tma_load_2d(st + NSPLIT * kTcChunkA, &mapB, kc * kTcBK, b_col0 + tn, fb);
+                    if (NSPLIT == 2) {
+                        tma_load_2d(st + kTcChunkA, &mapA, kpad_off + kc * kTcBK, a_row0 + tm, fb);
+                        tma_load_2d(st + 2 * kTcChunkA + kTcChunkB, &mapB, kpad_off + kc * kTcBK, b_col0 + tn, fb);
+                    }
+                    if (++s == kStages) { s = 0; ph ^= 1u; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_bf16(kTcBM, kTcBN);
+            int s = 0;
+            uint32_t ph = 0;
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++it) {
+                const int a = it & 1;
+                const uint32_t aph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait_bounded(acce0 + 8u * a, aph ^ 1u, bound_ns)) { *abort_flag = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(a * kTcBN);
+                for (int kc = 0; kc < nk; ++kc) {
+                    if (!mbar_wait_bounded(full0 + 8u * s, ph, bound_ns)) { *abort_flag = 1; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t st = base + (uint32_t)s * kStageBytes;
+                    const uint32_t sAh = st, sAl = st + kTcChunkA;
+                    const uint32_t sBh = st + NSPLIT * kTcChunkA, sBl = sBh + kTcChunkB;
+#pragma unroll
+                    for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                        const uint32_t first = (kc | kk) == 0 ? 0u : 1u;
+                        umma_bf16(acc, umma_desc_sw128(sAh + kk * 32), umma_desc_sw128(sBh + kk * 32), idesc, first);
+                        if (NPROD == 3) {
+                            umma_bf16(acc, umma_desc_sw128(sAh + kk * 32), umma_desc_sw128(sBl + kk * 32), idesc, 1u);
+                            umma_bf16(acc, umma_desc_sw128(sAl + kk * 32), umma_desc_sw128(sBh + kk * 32), idesc, 1u);
+                        }
+                    }
+                    umma_commit(empty0 + 8u * s);            // stage free once these MMAs are done
+                    if (++s == kStages) { s = 0; ph ^= 1u; }
+                }
+                if (*abort_flag) break;
+                umma_commit(accf0 + 8u * a);                 // accumulator ready
+            }
+        }
+    } else {
+        // epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        const int q = warp & 3;
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int tm = (t % mt) * kTcBM, tn = (t / mt) * kTcBN;
+            const int a = it & 1;
+            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            const int row = tm + q * 32 + lane;
+            float cold[kTcBN];
+#pragma unroll
+            for (int c = 0; c < kTcBN; ++c) {
+                const int col = tn + c;
+                cold[c] = (row < m && col < n) ? C[(size_t)row + (size_t)col * ldc] : 0.f;
+            }
+            if (*abort_flag || !mbar_wait_bounded(accf0 + 8u * a, aph, bound_ns)) { *abort_flag = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)(a * kTcBN) + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+            for (int h = 0; h < kTcBN / 32; ++h) {
+                float v[32];
+                tmem_ld32(acc + (uint32_t)(h * 32), v);
+                if (row < m) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        const int col = tn + h * 32 + c;
+                        if (col < n) C[(size_t)row + (size_t)col * ldc] = cold[h * 32 + c] - v[c];
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8u * a) : "memory");
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && *abort_flag) {
+        atomicExch(status, (int)LU_ERR_TIMEOUT);
+        // give copies in flight one bounded chance to land before shared memory is released
+        for (int i = 0; i < kStages; ++i) mbar_wait_bounded(full0 + 8u * i, 0, bound_ns / 4);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcBN) : "memory");
+    }
+}
+
+// ---- operand staging -------------------------------------------------------
+
+// L21 (rows x k, FP32 column-major, ld) -> BF16 row-major stage[i * lds + kk],
+// zero for kk in [k, kpad); with split, the low part x - bf16(x) rounded to
+// BF16 goes to stage[i * lds + kpad + kk].  Tiles of 32 x 32 transposed through
+// shared memory.
+__global__ void stage_rows_bf16(int rows, int k, int kpad, const float *__restrict__ L, int ld,
+                                __nv_bfloat16 *__restrict__ stage, int lds, int split) {
+    __shared__ float t[32][33];
+    const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int i = i0 + tx, kk = k0 + yy;
+        t[yy][tx] = (i < rows && kk < k) ? L[(size_t)i + (size_t)kk * ld] : 0.f;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int i = i0 + yy, kk = k0 + tx;
+        if (i < rows && kk < kpad) {
+            const float x = t[tx][yy];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            stage[(size_t)i * lds + kk] = hi;
+            if (split) stage[(size_t)i * lds + kpad + kk] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        }
+    }
+}
+
+// B (k x cols, FP32 column-major, ld) -> BF16 stage[j * lds + kk], zero pad.
+__global__ void stage_cols_bf16(int k, int kpad, int cols, const float *__restrict__ B, int ld,
+                                __nv_bfloat16 *__restrict__ stage, int lds, int split) {
+    const size_t total = (size_t)cols * kpad;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(e % kpad), j = (int)(e / kpad);
+        const float x = kk < k ? B[(size_t)kk + (size_t)j * ld] : 0.f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        stage[(size_t)j * lds + kk] = hi;
+        if (split) stage[(size_t)j * lds + kpad + kk] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
+// ---- host side ---------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static cudaError_t get_encoder() {
+    if (g_encode) return cudaSuccess;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return cudaSuccess;
+}
+
+// 2-D BF16 map over a K-major staging buffer: inner dimension kpad (elements),
+// outer dimension `outer` rows/columns, leading dimension lds elements.
+cudaError_t make_stage_map(CUtensorMap *map, const __nv_bfloat16 *base, int kpad, int outer, int lds, int box_outer) {
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)(outer > 0 ? outer : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)lds * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// kinner: elements per staged row/column (kpad, or 2 kpad with split)
+cudaError_t make_stage_maps(CUtensorMap *mapA, const __nv_bfloat16 *stageA, int rowsA, CUtensorMap *mapB,
+                            const __nv_bfloat16 *stageB, int colsB, int kinner, int lds) {
+    cudaError_t e = make_stage_map(mapA, stageA, kinner, rowsA, lds, kTcBM);
+    if (e != cudaSuccess) return e;
+    return make_stage_map(mapB, stageB, kinner, colsB, lds, kTcBN);
+}
+
+int tc_box_rows() { return kTcBM; }
+int tc_box_cols() { return kTcBN; }
+
+// C[m x n] -= A[a_row0 + (0..m), 0..K) * B[0..K, b_col0 + (0..n)] through the maps
+// (nprod = 1: BF16 operands; nprod = 3: split BF16, staging holds hi | lo).
+cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
+                           int b_col0, float *C, int ldc, int *status, long long bound_ns, cudaStream_t s) {
+    if (m <= 0 || n <= 0 || K <= 0) return cudaSuccess;
+    if (K > kTcMaxK || K % kTcBK != 0 || (nprod != 1 && nprod != 3)) return cudaErrorInvalidValue;
+    static int sms = 0;
+    static bool attr[2] = {false, false};
+    if (!sms) {
+        int d = 0;
+        cudaGetDevice(&d);
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        if (e != cudaSuccess) return e;
+    }
+    const int ntiles = lu_ceil_div(m, kTcBM) * lu_ceil_div(n, kTcBN);
+    const int grid = ntiles < sms ? ntiles : sms;
+    if (nprod == 1) {
+        if (!attr[0]) {
+            cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+            if (e != cudaSuccess) return e;
+            attr[0] = true;
+        }
+        gemm_update_tc<1><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, C, ldc, status, bound_ns);
+    } else {
+        if (!attr[1]) {
+            cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+            if (e != cudaSuccess) return e;
+            attr[1] = true;
+        }
+        gemm_update_tc<3><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, C, ldc, status, bound_ns);
+    }
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_rows(int rows, int k, int kpad, const float *L, int ld, __nv_bfloat16 *stage, int lds, int split,
+                              cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    dim3 grid(lu_ceil_div(rows, 32), lu_ceil_div(kpad, 32));
+    stage_rows_bf16<<<grid, 256, 0, s>>>(rows, k, kpad, L, ld, stage, lds, split);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_cols(int k, int kpad, int cols, const float *B, int ld, __nv_bfloat16 *stage, int lds, int split,
+                              cudaStream_t s) {
+    if (cols <= 0) return cudaSuccess;
+    size_t total = (size_t)cols * kpad;
+    int grid = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    stage_cols_bf16<<<grid, 256, 0, s>>>(k, kpad, cols, B, ld, stage, lds, split);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+int tc_kpad(int k) { return ((k + kTcBK - 1) / kTcBK) * kTcBK; }
+int tc_max_k() { return kTcMaxK; }
+
+}  // namespace lu

@@ -1,0 +1,252 @@
+// lu_solve_mixed: FP32 LU with a (split-)BF16 tensor-core trailing update, recovered
+// to FP64 accuracy by iterative refinement (not part of the paper: it refines
+// the paper's blocked look-ahead factorization computed in lower precision).
+//
+// Ladder, in order, each rung entered only when the previous one stalls:
+//   0  classic refinement: x += U^{-1} L^{-1} P r with r = b - A x in FP64;
+//   1  GMRES-IR (Carson and Higham, SIAM J. Sci. Comput. 39(6), 2017), here
+//      in its flexible form: the correction equation A d = r is solved by
+//      FGMRES (Saad, SIAM J. Sci. Comput. 14(2), 1993) with the FP32 factors
+//      as right preconditioner and FP64 products with A, so that rounding in
+//      the FP32 preconditioner solve does not limit the attainable accuracy;
+//   2  the FP64 factorization of this library, then classic refinement.
+// Convergence: normwise backward error
+//   eta = max_q ||b_q - A x_q||_inf / (||A||_inf ||x_q||_inf + ||b_q||_inf)
+// at most `tol`.  Stall: eta has not halved over the last two steps, or
+// max_iter steps were taken on the rung.
+#include "common.cuh"
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace lu {
+int factor_f32_internal(int n, float *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s);
+int factor_f64_internal(int n, double *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s);
+int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s);
+int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s);
+cudaError_t launch_cast_rowsum(int n, const double *A, int lda, float *A32, int lda32, double *rowsum, cudaStream_t s);
+size_t residual_workspace_doubles(int n, int nrhs);
+cudaError_t launch_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B, int ldb,
+                            double *R, int ldr, double *part, unsigned long long *rmax, cudaStream_t s);
+cudaError_t launch_absmax(int n, int nrhs, const double *V, int ldv, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_vecmax(int n, const double *v, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_to_f32_scaled(int n, int nrhs, const double *R, int ldr, const unsigned long long *rmax, float *R32,
+                                 int ldr32, cudaStream_t s);
+cudaError_t launch_axpy_scaled(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax, double *X, int ldx,
+                               cudaStream_t s);
+cudaError_t launch_axpy_f64(int n, int nrhs, const double *D, int ldd, double *X, int ldx, cudaStream_t s);
+int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb, double *X, int ldx, const float *LU32,
+             int ld32, const int *perm, double anorm, const double *bnorm, double tol, int max_outer, int restart,
+             int *iters_out, int *inner_out, double *eta_out, cudaStream_t s);
+}  // namespace lu
+
+using namespace lu;
+
+namespace {
+
+struct Buf {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Buf(cudaStream_t st) : s(st) {}
+    template <typename T>
+    cudaError_t get(T **p, size_t count) {
+        void *v = nullptr;
+        cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(count, 1) * sizeof(T), s);
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(v);
+        *p = static_cast<T *>(v);
+        return cudaSuccess;
+    }
+    ~Buf() {
+        for (void *v : ptrs) cudaFreeAsync(v, s);
+    }
+};
+
+double bits_to_double(unsigned long long b) {
+    double d;
+    memcpy(&d, &b, sizeof(d));
+    return d;
+}
+
+}  // namespace
+
+// eta for each column from device norms (synchronizes s)
+static int eta_now(int nrhs, const unsigned long long *d_rmax, const unsigned long long *d_xmax, double anorm,
+                   const std::vector<double> &bnorm, double *eta, cudaStream_t s) {
+    std::vector<unsigned long long> h(2 * (size_t)nrhs);
+    LU_CUDA_TRY(cudaMemcpyAsync(h.data(), d_rmax, sizeof(unsigned long long) * nrhs, cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaMemcpyAsync(h.data() + nrhs, d_xmax, sizeof(unsigned long long) * nrhs, cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    for (int q = 0; q < nrhs; ++q) {
+        const double r = bits_to_double(h[q]), x = bits_to_double(h[nrhs + q]);
+        const double den = anorm * x + bnorm[q];
+        double e = den > 0.0 ? r / den : (r > 0.0 ? INFINITY : 0.0);
+        if (std::isnan(e)) e = INFINITY;
+        worst = std::max(worst, e);
+    }
+    *eta = worst;
+    return LU_OK;
+}
+
+extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb, double *dX, int ldx,
+                              const lu_mixed_opts *opts, lu_mixed_report *rep, void *stream) {
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (n > 0 && !dA) return -3;
+    if (lda < std::max(1, n)) return -4;
+    if (n > 0 && nrhs > 0 && !dB) return -5;
+    if (ldb < std::max(1, n)) return -6;
+    if (n > 0 && nrhs > 0 && !dX) return -7;
+    if (ldx < std::max(1, n)) return -8;
+    if (opts && (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3))
+        return -9;
+    if (opts && (opts->nb < 0 || opts->max_iter < 0 || opts->tol < 0 || opts->gmres_restart < 0)) return -9;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lu_mixed_report r = {};
+    const int update = opts ? opts->update : LU_UPDATE_BF16X3;
+    const int max_iter = (opts && opts->max_iter > 0) ? opts->max_iter : 30;
+    const double tol = (opts && opts->tol > 0) ? opts->tol : 1e-14;
+    const bool allow_gmres = opts ? opts->allow_gmres != 0 : true;
+    const bool allow_fb = opts ? opts->allow_fallback != 0 : true;
+    const int restart = (opts && opts->gmres_restart > 0) ? opts->gmres_restart : 30;
+    const bool fp64_only = opts && opts->fp64_factor != 0;
+    if (n == 0 || nrhs == 0) {
+        if (rep) *rep = r;
+        return LU_OK;
+    }
+    cudaEvent_t e0, e1, e2;
+    LU_CUDA_TRY(cudaEventCreate(&e0));
+    LU_CUDA_TRY(cudaEventCreate(&e1));
+    LU_CUDA_TRY(cudaEventCreate(&e2));
+    LU_CUDA_TRY(cudaEventRecord(e0, s));
+
+    Buf ws(s);
+    const int ld32 = (n + 31) & ~31;
+    float *A32 = nullptr, *R32 = nullptr;
+    int *ipiv = nullptr, *perm = nullptr, *info = nullptr;
+    double *rowsum = nullptr, *R = nullptr, *part = nullptr;
+    unsigned long long *norms = nullptr;   // [0] anorm, [1..nrhs] rmax, [1+nrhs..] xmax, [1+2nrhs..] bmax
+    LU_CUDA_TRY(ws.get(&A32, (size_t)ld32 * n));
+    LU_CUDA_TRY(ws.get(&R32, (size_t)n * nrhs));
+    LU_CUDA_TRY(ws.get(&ipiv, n));
+    LU_CUDA_TRY(ws.get(&perm, n));
+    LU_CUDA_TRY(ws.get(&info, 1));
+    LU_CUDA_TRY(ws.get(&rowsum, n));
+    LU_CUDA_TRY(ws.get(&R, (size_t)n * nrhs));
+    LU_CUDA_TRY(ws.get(&part, residual_workspace_doubles(n, nrhs)));
+    LU_CUDA_TRY(ws.get(&norms, 1 + 3 * (size_t)nrhs));
+    unsigned long long *d_anorm = norms, *d_rmax = norms + 1, *d_xmax = norms + 1 + nrhs, *d_bmax = norms + 1 + 2 * nrhs;
+
+    // ||A||_inf and ||b||_inf
+    LU_CUDA_TRY(launch_cast_rowsum(n, dA, lda, A32, ld32, rowsum, s));
+    LU_CUDA_TRY(launch_vecmax(n, rowsum, d_anorm, s));
+    LU_CUDA_TRY(launch_absmax(n, nrhs, dB, ldb, d_bmax, s));
+    // FP32 factorization
+    lu_opts fo = {};
+    fo.update = update;
+    fo.nb = opts ? opts->nb : 0;
+    int rc = LU_OK;
+    if (!fp64_only) {
+        rc = factor_f32_internal(n, A32, ld32, ipiv, info, perm, &fo, s);
+        if (rc != LU_OK) return rc;
+    } else {
+        LU_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+    }
+    LU_CUDA_TRY(cudaEventRecord(e1, s));
+    std::vector<unsigned long long> hn(1 + 3 * (size_t)nrhs);
+    int hinfo = 0;
+    LU_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(unsigned long long) * hn.size(), cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaStreamSynchronize(s));
+    r.info = hinfo;
+    const double anorm = bits_to_double(hn[0]);
+    std::vector<double> bnorm(nrhs);
+    for (int q = 0; q < nrhs; ++q) bnorm[q] = bits_to_double(hn[1 + 2 * nrhs + q]);
+
+    // rung 0: classic refinement from x = 0, r = b
+    LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
+    LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
+                                  cudaMemcpyDeviceToDevice, s));
+    LU_CUDA_TRY(cudaMemcpyAsync(d_rmax, d_bmax, sizeof(unsigned long long) * nrhs, cudaMemcpyDeviceToDevice, s));
+    double eta = 1.0;
+    std::vector<double> hist;
+    bool done = false;
+    if (hinfo == 0 && !fp64_only) {
+        for (int it = 0; it < max_iter; ++it) {
+            LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
+            rc = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
+            if (rc != LU_OK) return rc;
+            LU_CUDA_TRY(launch_axpy_scaled(n, nrhs, R32, n, d_rmax, dX, ldx, s));
+            LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
+            LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
+            rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+            if (rc != LU_OK) return rc;
+            r.iterations++;
+            hist.push_back(eta);
+            if (eta <= tol) { done = true; break; }
+            const size_t h = hist.size();
+            if (h >= 3 && !(hist[h - 1] <= 0.5 * hist[h - 3])) break;   // stalled
+        }
+    }
+    // rung 1: GMRES-IR with the FP32 factors as preconditioner
+    if (!done && hinfo == 0 && allow_gmres && !fp64_only) {
+        r.rung = 1;
+        int outer = 0, inner = 0;
+        rc = gmres_ir(n, nrhs, dA, lda, dB, ldb, dX, ldx, A32, ld32, perm, anorm, bnorm.data(), tol, max_iter, restart, &outer,
+                      &inner, &eta, s);
+        if (rc != LU_OK) return rc;
+        r.iterations += outer;
+        r.gmres_iters += inner;
+        done = eta <= tol;
+    }
+    // rung 2: FP64 factorization
+    if (!done && (allow_fb || fp64_only)) {
+        r.rung = 2;
+        r.fell_back = fp64_only ? 0 : 1;
+        double *A64 = nullptr;
+        int *ipiv64 = nullptr, *perm64 = nullptr, *info64 = nullptr;
+        LU_CUDA_TRY(ws.get(&A64, (size_t)n * n));
+        LU_CUDA_TRY(ws.get(&ipiv64, n));
+        LU_CUDA_TRY(ws.get(&perm64, n));
+        LU_CUDA_TRY(ws.get(&info64, 1));
+        LU_CUDA_TRY(cudaMemcpy2DAsync(A64, sizeof(double) * n, dA, sizeof(double) * lda, sizeof(double) * n, n,
+                                      cudaMemcpyDeviceToDevice, s));
+        rc = factor_f64_internal(n, A64, n, ipiv64, info64, perm64, nullptr, s);
+        if (rc != LU_OK) return rc;
+        LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
+        LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
+                                      cudaMemcpyDeviceToDevice, s));
+        double *D = nullptr;
+        LU_CUDA_TRY(ws.get(&D, (size_t)n * nrhs));
+        for (int it = 0; it < 5; ++it) {
+            LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
+            rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
+            if (rc != LU_OK) return rc;
+            LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));   // X += D
+            LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
+            LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
+            rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+            if (rc != LU_OK) return rc;
+            r.iterations++;
+            if (eta <= tol) break;
+        }
+        done = eta <= tol;
+    }
+    LU_CUDA_TRY(cudaEventRecord(e2, s));
+    LU_CUDA_TRY(cudaEventSynchronize(e2));
+    float t01 = 0, t12 = 0;
+    cudaEventElapsedTime(&t01, e0, e1);
+    cudaEventElapsedTime(&t12, e1, e2);
+    r.t_factor_ms = t01;
+    r.t_refine_ms = t12;
+    r.t_total_ms = (double)t01 + t12;
+    r.backward_error = eta;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (rep) *rep = r;
+    return LU_OK;
+}

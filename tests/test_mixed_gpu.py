@@ -1,0 +1,126 @@
+"""Mixed-precision solve (FP32 factors with a BF16 tensor-core update, FP64
+refinement) and the BF16 trailing-update kernel on its own."""
+import numpy as np
+import pytest
+
+import lu_inputs as li
+from tests.gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).float().bfloat16().double().numpy()
+
+
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 256), (1000, 77, 100), (5, 3, 16), (700, 900, 192)])
+def test_trailing_update_bf16_vs_fp32_reference(m, n, k, split):
+    """C - A B with A, B rounded to BF16 (split: x = hi + lo, products
+    hi*hi + hi*lo + lo*hi): every product of two BF16 values is exact in
+    FP32, so the only difference from an exact sum of the same products is
+    FP32 accumulation: |err| <= k' eps32 sum |a||b| + eps32 |C - AB|,
+    k' the number of products summed."""
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    A = li.uniform(m, k, seed=1 + m)
+    B = li.uniform(k, n, seed=2 + n)
+    C = li.uniform(m, n, seed=3 + k)
+    dA = li.to_device_colmajor(A, dev(), torch.float32)
+    dB = li.to_device_colmajor(B, dev(), torch.float32)
+    dC = li.to_device_colmajor(C, dev(), torch.float32)
+    mode = lu.LU_UPDATE_BF16X3 if split else lu.LU_UPDATE_BF16
+    lu.lu_trailing_update(mode, dA, dB, dC, m, n, k)
+    torch.cuda.synchronize()
+    got = li.from_device_colmajor(dC, m)
+    A32 = A.astype(np.float32).astype(np.float64)
+    B32 = B.astype(np.float32).astype(np.float64)
+    C32 = C.astype(np.float32).astype(np.float64)
+    Ah, Bh = _bf16(A32), _bf16(B32)
+    if split:
+        Al = _bf16((A32 - Ah).astype(np.float32).astype(np.float64))
+        Bl = _bf16((B32 - Bh).astype(np.float32).astype(np.float64))
+        prod = Ah @ Bh + Ah @ Bl + Al @ Bh
+        mag = np.abs(Ah) @ np.abs(Bh) + np.abs(Ah) @ np.abs(Bl) + np.abs(Al) @ np.abs(Bh)
+        kk = 3 * k
+        # the split really is more accurate than one BF16 product
+        assert np.max(np.abs(prod - A32 @ B32)) < 2.0 ** -14 * np.max(np.abs(A32) @ np.abs(B32))
+    else:
+        prod, mag, kk = Ah @ Bh, np.abs(Ah) @ np.abs(Bh), k
+    ref = C32 - prod
+    bound = kk * 2.0 ** -23 * mag + 2.0 ** -23 * np.abs(ref) + 1e-30
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+def test_trailing_update_native_fp32():
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    m, n, k = 257, 129, 48
+    A, B, C = li.uniform(m, k, seed=4), li.uniform(k, n, seed=5), li.uniform(m, n, seed=6)
+    dA, dB, dC = (li.to_device_colmajor(X, dev(), torch.float32) for X in (A, B, C))
+    lu.lu_trailing_update(lu.LU_UPDATE_NATIVE, dA, dB, dC, m, n, k)
+    torch.cuda.synchronize()
+    ref = C.astype(np.float32).astype(float) - A.astype(np.float32).astype(float) @ B.astype(np.float32).astype(float)
+    assert np.max(np.abs(li.from_device_colmajor(dC, m) - ref)) <= k * 2.0 ** -22 * 2
+
+
+def _mixed(A, B, **kw):
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    n, nrhs = B.shape
+    dA = li.to_device_colmajor(A, dev())
+    dB = li.to_device_colmajor(B, dev())
+    dX = torch.zeros_like(dB)
+    rep = lu.lu_solve_mixed(dA, dB, dX, n, **kw)
+    torch.cuda.synchronize()
+    return li.from_device_colmajor(dX, n), rep
+
+
+@pytest.mark.parametrize("nrhs", [1, 8])
+def test_mixed_uniform_reaches_1e14(oracle_mod, nrhs):
+    n = 1500
+    A = li.uniform(n, n, seed=li.BASE_SEED + 2000)
+    B = li.uniform(n, nrhs, seed=li.BASE_SEED + 2001)
+    X, rep = _mixed(A, B)
+    eta = oracle_mod.backward_error(A, X, B)
+    assert eta <= 1e-14 and rep.backward_error <= 1e-14
+    assert rep.fell_back == 0
+    Xo = oracle_mod.getrs(*oracle_mod.getrf(A, nthreads=oracle_mod.default_threads())[:2], B)
+    assert np.max(np.abs(X - Xo)) / np.max(np.abs(Xo)) <= 1e-9
+
+
+@pytest.mark.parametrize("kappa,rung_max", [(1e2, 0), (1e5, 1), (1e8, 2)])
+def test_mixed_kappa_ladder(oracle_mod, kappa, rung_max):
+    n = 600
+    A = li.kappa_matrix(n, kappa, seed=li.BASE_SEED + 2100, k=n)
+    xt = li.uniform(n, 1, seed=9)
+    xt[:, 0] = 1.0
+    B = A @ xt
+    X, rep = _mixed(A, B)
+    eta = oracle_mod.backward_error(A, X, B)
+    assert eta <= 1e-14, (rep.as_dict(), eta)
+    assert rep.rung <= rung_max
+    # forward error within kappa * eta (with a safety factor)
+    assert np.max(np.abs(X - xt)) / np.max(np.abs(xt)) <= 100 * kappa * max(eta, 1e-16)
+
+
+def test_mixed_kappa_1e12_falls_back(oracle_mod):
+    n = 400
+    A = li.kappa_matrix(n, 1e12, seed=li.BASE_SEED + 2200, k=n)
+    B = A @ np.ones((n, 1))
+    X, rep = _mixed(A, B)
+    assert oracle_mod.backward_error(A, X, B) <= 1e-14
+    assert rep.rung in (1, 2)
+
+
+def test_mixed_forced_fallback_path(oracle_mod):
+    n = 300
+    A = li.uniform(n, n, seed=5)
+    B = li.uniform(n, 2, seed=6)
+    X, rep = _mixed(A, B, max_iter=1, allow_gmres=0, tol=1e-300)
+    assert rep.fell_back == 1 and rep.rung == 2
+    assert oracle_mod.backward_error(A, X, B) <= 1e-15

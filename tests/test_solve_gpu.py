@@ -1,0 +1,126 @@
+"""Parity of lu_solve (and the batched entry points) with the oracle."""
+import numpy as np
+import pytest
+
+import lu_inputs as li
+from tests.gpu_util import EPS64, dev, factor_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (65, 3), (512, 1), (700, 17)])
+def test_solve_f64_matches_oracle(oracle_mod, n, nrhs):
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    A = li.uniform(n, n, seed=30 + n)
+    B = li.uniform(n, nrhs, seed=31 + n)
+    LU, ipiv, info, dA, dpiv = factor_gpu(A, "f64")
+    dB = li.to_device_colmajor(B, dev())
+    lu.lu_solve(dA, dpiv, dB, n)
+    torch.cuda.synchronize()
+    X = li.from_device_colmajor(dB, n)
+    LUo, pivo, _ = oracle_mod.getrf(A)
+    Xo = oracle_mod.getrs(LUo, pivo, B)
+    assert np.max(np.abs(X - Xo)) <= 1e3 * n * EPS64 * max(1.0, np.max(np.abs(Xo)))
+    assert oracle_mod.backward_error(A, X, B) <= 10 * n * EPS64
+
+
+def test_solve_dyadic_exact():
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    n = 300
+    A, perm, L, U = li.dyadic_plu(n, seed=3)
+    x = ((li.splitmix64(6, np.arange(n, dtype=np.uint64)) % np.uint64(9)).astype(np.int64) - 4).astype(float)
+    b = A @ x
+    LU, ipiv, info, dA, dpiv = factor_gpu(A, "f64")
+    dB = torch.from_numpy(b).to(dev()).view(1, n).clone()
+    lu.lu_solve(dA, dpiv, dB, n)
+    torch.cuda.synchronize()
+    assert np.array_equal(dB.view(-1).cpu().numpy(), x)
+
+
+def test_c1_factor_and_solve_ones(oracle_mod):
+    """n = 512 workload: b = A * ones; the solution is ones to rounding."""
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    A = li.uniform(512, 512, seed=li.BASE_SEED + 1000)
+    b = li.ones_rhs(A)
+    LU, ipiv, info, dA, dpiv = factor_gpu(A, "f64")
+    dB = torch.from_numpy(b).to(dev()).view(1, 512).clone()
+    lu.lu_solve(dA, dpiv, dB, 512)
+    torch.cuda.synchronize()
+    x = dB.view(-1).cpu().numpy()
+    xo = oracle_mod.getrs(*oracle_mod.getrf(A)[:2], b)
+    assert np.max(np.abs(x - xo)) < 1e-11
+    assert oracle_mod.backward_error(A, x, b) <= 10 * 512 * EPS64
+
+
+def _batch_buffers(mats, dtype):
+    import torch
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    devA = [li.to_device_colmajor(a, dev(), dtype=tdt) for a in mats]
+    piv = [torch.zeros(max(1, a.shape[0]), dtype=torch.int32, device=dev()) for a in mats]
+    ns = torch.tensor([a.shape[0] for a in mats], dtype=torch.int32, device=dev())
+    ptrA = torch.tensor([t.data_ptr() for t in devA], dtype=torch.int64, device=dev())
+    ptrP = torch.tensor([t.data_ptr() for t in piv], dtype=torch.int64, device=dev())
+    lds = ns.clone().clamp(min=1)
+    info = torch.zeros(len(mats), dtype=torch.int32, device=dev())
+    return devA, piv, ns, ptrA, ptrP, lds, info
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_matches_oracle(oracle_mod, dtype):
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    sizes = li.batch_sizes(60, 16, 256, seed=li.BASE_SEED + 3000)
+    sizes[:3] = [256, 16, 1]
+    mats = li.batch_matrices(sizes, seed=li.BASE_SEED + 3001)
+    rhs = [li.ones_rhs(a) for a in mats]
+    devA, piv, ns, ptrA, ptrP, lds, info = _batch_buffers(mats, dtype)
+    code = lu.LU_F64 if dtype == "f64" else lu.LU_F32
+    lu.lu_factor_batched(code, ns, ptrA, lds, ptrP, info, 256)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    devB = [torch.from_numpy(b).to(dev(), tdt).view(1, -1).clone() for b in rhs]
+    ptrB = torch.tensor([t.data_ptr() for t in devB], dtype=torch.int64, device=dev())
+    lu.lu_solve_batched(code, 1, ns, ptrA, lds, ptrP, ptrB, lds, 256)
+    torch.cuda.synchronize()
+    LUs, pivs, infos, xs = oracle_mod.getrf_getrs_batched(mats, rhs)
+    assert np.array_equal(info.cpu().numpy(), infos)
+    for t, A in enumerate(mats):
+        n = A.shape[0]
+        gp = piv[t].cpu().numpy()[:n]
+        if t % 2 == 1:
+            assert np.array_equal(gp, np.arange(1, n + 1))
+        if dtype == "f64":
+            assert np.array_equal(gp, pivs[t]), t
+            LU = li.from_device_colmajor(devA[t], n)
+            assert np.max(np.abs(LU - LUs[t])) <= 10 * n * EPS64 * max(1.0, np.max(np.abs(LUs[t])))
+            assert np.max(np.abs(devB[t].view(-1).cpu().numpy() - xs[t])) <= 1e-9
+        else:
+            LU = li.from_device_colmajor(devA[t], n)
+            r, a = oracle_mod.lu_residual_fro(A.astype(np.float32).astype(np.float64), LU, gp)
+            assert r / a <= 10 * n * 1.2e-7
+            assert np.max(np.abs(devB[t].view(-1).cpu().numpy() - 1.0)) <= 1e-2
+
+
+def test_batched_dyadic_exact():
+    import paper_1611_06365_gb300 as lu
+    import torch
+    mats, perms = [], []
+    for i, n in enumerate([16, 33, 100, 256, 200]):
+        A, perm, L, U = li.dyadic_plu(n, seed=70 + i)
+        mats.append(A)
+        perms.append((perm, L, U))
+    devA, piv, ns, ptrA, ptrP, lds, info = _batch_buffers(mats, "f64")
+    lu.lu_factor_batched(lu.LU_F64, ns, ptrA, lds, ptrP, info, 256)
+    torch.cuda.synchronize()
+    from tests.gpu_util import expected_ipiv
+    for t, (perm, L, U) in enumerate(perms):
+        n = L.shape[0]
+        LU = li.from_device_colmajor(devA[t], n)
+        assert np.array_equal(piv[t].cpu().numpy()[:n], expected_ipiv(perm))
+        assert np.array_equal(np.triu(LU), U) and np.array_equal(np.tril(LU, -1) + np.eye(n), L)
