@@ -52,7 +52,8 @@ enum {
     LU_ERR_CUDA = -100,        /* a CUDA runtime call failed */
     LU_ERR_NOMEM = -101,       /* workspace allocation failed */
     LU_ERR_TIMEOUT = -102,     /* a bounded device-side wait expired */
-    LU_ERR_UNSUPPORTED = -103  /* valid request this build cannot serve */
+    LU_ERR_UNSUPPORTED = -103, /* valid request this build cannot serve */
+    LU_ERR_SCRATCH = -104      /* request larger than the fixed scratch of lu_solve_noalloc */
 };
 
 /* Trailing-update arithmetic for LU_F32 factorizations. */
@@ -101,6 +102,27 @@ int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info,
  */
 int lu_solve(lu_dtype dt, int n, int nrhs, const void *dLU, int lda, const int *d_ipiv,
              void *dB, int ldb, void *stream);
+
+/*
+ * lu_solve_noalloc -- lu_solve that allocates no memory.  (No counterpart in
+ * the paper: it exists for callers that cannot allocate device memory during
+ * a solve, e.g. an application whose framework has reserved the device
+ * memory for its own pool, so any cudaMalloc would fail, or a latency-critical
+ * loop that cannot afford an allocation that may wait for the device.)
+ *   Arguments as lu_solve; d_status (device int, may be NULL) receives
+ *   LU_OK, or LU_ERR_TIMEOUT if a bounded wait of the substitution expired.
+ *   Workspace comes from one fixed array in device memory of
+ *   lu_solve_noalloc_capacity() bytes (4 MiB) that every GPU loading the
+ *   library keeps until exit.  A request needs about
+ *   4 n + elem * n * nrhs + 8 ceil(n/64) bytes plus alignment (elem = 8 for
+ *   LU_F64, 4 for LU_F32); a larger one returns LU_ERR_SCRATCH and launches
+ *   nothing.  The first call on a device looks up the array's device address
+ *   (make it before any stream capture).  All calls share the array: calls
+ *   whose work overlaps on the GPU race and must be serialized by the caller.
+ */
+int lu_solve_noalloc(lu_dtype dt, int n, int nrhs, const void *dLU, int lda, const int *d_ipiv,
+                     void *dB, int ldb, int *d_status, void *stream);
+size_t lu_solve_noalloc_capacity(void);
 
 /*
  * lu_factor_batched -- lu_factor applied to `batch` independent matrices of

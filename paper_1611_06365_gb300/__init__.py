@@ -21,7 +21,7 @@ from . import build as _build_mod
 
 __all__ = [
     "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LuError", "lib", "build",
-    "lu_factor", "lu_solve", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
+    "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status",
     "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_kernel_launches", "to_colmajor", "from_colmajor", "MixedReport",
 ]
@@ -29,6 +29,7 @@ __all__ = [
 LU_F64, LU_F32 = 0, 1
 LU_UPDATE_NATIVE, LU_UPDATE_BF16, LU_UPDATE_BF16X3 = 0, 1, 2
 LU_ERR_CUDA, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED = -100, -101, -102, -103
+LU_ERR_SCRATCH = -104
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -88,6 +89,9 @@ def lib():
         L.lu_status_string.restype = ctypes.c_char_p
         L.lu_last_device_status.argtypes = [vp, i]
         L.lu_version.restype = ctypes.c_char_p
+        L.lu_solve_noalloc.argtypes = [i, i, i, vp, i, ip, vp, i, ip, vp]
+        L.lu_solve_noalloc.restype = i
+        L.lu_solve_noalloc_capacity.restype = ctypes.c_size_t
         L.lu_update_timing.argtypes = [i]
         L.lu_update_timing.restype = i
         L.lu_update_timing_read.argtypes = [ctypes.POINTER(ctypes.c_longlong)] + [ctypes.POINTER(ctypes.c_double)] * 3
@@ -151,6 +155,22 @@ def lu_solve(LU, ipiv, B, n=None, nrhs=None, *, stream=None):
     ldb = B.stride(0) if B.dim() == 2 else B.shape[0]
     return _check("lu_solve", lib().lu_solve(_dtype_code(LU), n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B), ldb,
                                               _stream(stream)))
+
+
+def lu_solve_noalloc(LU, ipiv, B, n=None, nrhs=None, *, status=None, stream=None):
+    """lu_solve without any memory allocation: the workspace is a fixed array of
+    lu_solve_noalloc_capacity() bytes in device memory.  For callers that may
+    not allocate during a solve (device memory reserved by another pool,
+    latency-critical loops).  Calls that overlap on the GPU must not share it."""
+    n, lda = _cm_dims(LU, n)
+    nrhs = B.shape[0] if nrhs is None else nrhs
+    ldb = B.stride(0) if B.dim() == 2 else B.shape[0]
+    return _check("lu_solve_noalloc", lib().lu_solve_noalloc(_dtype_code(LU), n, nrhs, _ptr(LU), lda, _ptr(ipiv),
+                                                              _ptr(B), ldb, _ptr(status), _stream(stream)))
+
+
+def lu_solve_noalloc_capacity() -> int:
+    return lib().lu_solve_noalloc_capacity()
 
 
 def lu_factor_batched(dtype_code, ns, A_ptrs, ldas, ipiv_ptrs, infos, max_n, *, stream=None):

@@ -563,6 +563,7 @@ const char *lu_status_string(int code) {
         case LU_ERR_NOMEM: return "workspace allocation failed";
         case LU_ERR_TIMEOUT: return "a bounded device-side wait expired";
         case LU_ERR_UNSUPPORTED: return "unsupported request";
+        case LU_ERR_SCRATCH: return "request exceeds the fixed scratch of the no-allocation entry point";
         default: break;
     }
     if (code < 0 && code > -100) return "invalid argument (return value -i names argument i)";
