@@ -114,7 +114,7 @@ int lu_solve(lu_dtype dt, int n, int nrhs, const void *dLU, int lda, const int *
  *   Workspace comes from one fixed array in device memory of
  *   lu_solve_noalloc_capacity() bytes (4 MiB) that every GPU loading the
  *   library keeps until exit.  A request needs about
- *   4 n + elem * n * nrhs + 8 ceil(n/64) bytes plus alignment (elem = 8 for
+ *   4 n + elem * n * nrhs + 256 ceil(n/64) bytes plus alignment (elem = 8 for
  *   LU_F64, 4 for LU_F32); a larger one returns LU_ERR_SCRATCH and launches
  *   nothing.  The first call on a device looks up the array's device address
  *   (make it before any stream capture).  All calls share the array: calls

@@ -36,11 +36,11 @@
 namespace lu {
 // panel.cu
 template <typename T>
-cudaError_t launch_panel(T *P, int lda, int m, int W, int *ipiv, int row_base, int *info, int max_ctas, size_t smem_cap,
-                         cudaStream_t s);
-int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap);
+cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
+                               int *perm, __nv_bfloat16 *stage, int lds, int kpad, int split, int max_ctas,
+                               size_t smem_cap, cudaStream_t s);
+int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo);
 // swap_trsm.cu
-cudaError_t launch_pivot_map(const int *ipiv, int kb, int b, int *map, int *perm, cudaStream_t s);
 template <typename T>
 cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c_begin, int c_end, int do_trsm,
                              __nv_bfloat16 *stage, int ldst, int stage_c0, int stage_k, int split, cudaStream_t s);
@@ -54,13 +54,14 @@ int tc_box_rows();
 int tc_box_cols();
 cudaError_t make_stage_map(CUtensorMap *map, const __nv_bfloat16 *base, int kpad, int outer, int lds, int box_outer);
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
-                           int b_col0, float *C, int ldc, int *status, long long bound_ns, cudaStream_t s);
+                           int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s);
 cudaError_t launch_stage_rows(int rows, int k, int kpad, const float *L, int ld, __nv_bfloat16 *stage, int lds, int split,
                               cudaStream_t s);
 cudaError_t launch_stage_cols(int k, int kpad, int cols, const float *B, int ld, __nv_bfloat16 *stage, int lds, int split,
                               cudaStream_t s);
 int tc_kpad(int k);
 int tc_max_k();
+bool tc_c_aligned(const float *C, int ldc);
 // solve.cu
 cudaError_t launch_ipiv_to_perm(const int *ipiv, int n, int *perm, cudaStream_t s);
 template <typename TI, typename TO>
@@ -104,7 +105,7 @@ struct DevState {
     bool init = false;
     cudaStream_t P = nullptr, U = nullptr;
     cudaEvent_t evP[2] = {nullptr, nullptr}, evU[2] = {nullptr, nullptr};
-    cudaEvent_t evIn = nullptr, evOutP = nullptr, evOutU = nullptr;
+    cudaEvent_t evIn = nullptr, evOutP = nullptr, evOutU = nullptr, evPF2 = nullptr;
     int *status = nullptr;   // device status word
     int sms = 0;
 };
@@ -133,6 +134,7 @@ cudaError_t dev_state(DevState **out) {
         if ((e = cudaEventCreateWithFlags(&st.evIn, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&st.evOutP, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&st.evOutU, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&st.evPF2, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&st.status, sizeof(int))) != cudaSuccess) return e;
         if ((e = cudaMemset(st.status, 0, sizeof(int))) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, d)) != cudaSuccess) return e;
@@ -217,18 +219,24 @@ struct Plan {
 template <typename T>
 Plan make_plan(int n, const lu_opts *o) {
     Plan p;
-    const int wfit = std::max(1, panel_width_that_fits(std::max(n, 1), sizeof(T), kPanelSmemCap, 64));
     const bool tc = (sizeof(T) == 4) && o && (o->update == LU_UPDATE_BF16 || o->update == LU_UPDATE_BF16X3);
     p.tc = tc;
     p.nprod = (o && o->update == LU_UPDATE_BF16X3) ? 3 : 1;
     if (tc) {
         p.bo = (o && o->nb > 0) ? o->nb : (n >= 8192 ? 256 : (n >= 2048 ? 128 : 64));
         p.bo = std::min(p.bo, tc_max_k());
-        p.bi = (o && o->nb_inner > 0) ? std::min(o->nb_inner, wfit) : std::min(32, wfit);
+    } else if (sizeof(T) == 4) {
+        p.bo = (o && o->nb > 0) ? o->nb : 128;
     } else {
-        p.bo = (o && o->nb > 0) ? o->nb : wfit;
-        p.bi = (o && o->nb_inner > 0) ? std::min(o->nb_inner, wfit) : std::min(p.bo, wfit);
+        // FP64: the update is DFMA-bound for any b >= 8, so the panel width is
+        // the inner width the cluster holds (up to 32)
+        p.bo = (o && o->nb > 0) ? o->nb : 0;
     }
+    const int bo_fit = std::min(std::max(p.bo, 1), 256);
+    const int wfit = std::max(1, panel_width_that_fits(std::max(n, 1), sizeof(T), kPanelSmemCap, 64, p.bo > 0 ? bo_fit : 0));
+    if (p.bo == 0) p.bo = std::min(32, wfit);
+    p.bo = std::min(p.bo, 256);
+    p.bi = (o && o->nb_inner > 0) ? std::min(o->nb_inner, wfit) : std::min(32, wfit);
     p.bi = std::max(1, std::min(p.bi, p.bo));
     p.lookahead = !(o && o->lookahead < 0);
     p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : 16;
@@ -246,12 +254,13 @@ struct FactorCtx {
     int *perm;            // optional
     Plan pl;
     DevState *st;
-    int *maps[3];         // 2 outer (parity) + 1 inner
+    int *maps[2];         // row maps of panels k (parity)
     __nv_bfloat16 *stA[2] = {nullptr, nullptr};
     __nv_bfloat16 *stB = nullptr;
     int kpad = 0;
     int kinner = 0;   // staged elements per row/column (kpad, or 2 kpad when split)
     CUtensorMap mapA[2], mapB;
+    int *tile_ctr = nullptr;   // [0]: panel-branch updates, [1]: remainder-branch updates
 };
 
 template <typename T>
@@ -287,7 +296,8 @@ cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int
     if constexpr (sizeof(T) == 4) {
         if (c.pl.tc)
             return launch_gemm_tc(c.pl.nprod, m, nn, c.kpad, c.mapA[k_par], 0, c.mapB, c0 - r0,
-                                  reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda, c.st->status, c.pl.bound, s);
+                                  reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda,
+                                  c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status, c.pl.bound, s);
     }
     return launch_gemm_simt<T>(m, nn, w, c.A + r0 + (size_t)kb * c.lda, c.lda, c.A + kb + (size_t)c0 * c.lda, c.lda,
                                c.A + r0 + (size_t)c0 * c.lda, c.lda, s);
@@ -299,56 +309,50 @@ cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, in
     return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, stage, c.kinner, kb + w, c.kpad, c.pl.nprod == 3, s);
 }
 
-// Factor outer panel at column kb (width w) on stream s; leaves row map in maps[par].
+// Factor outer panel at column kb (width w) on stream s: one cluster launch
+// that also leaves the row map in maps[par], updates perm and stages L21.
 template <typename T>
 cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s) {
-    const int n = c.n, lda = c.lda;
-    cudaError_t e;
-    for (int ib = 0; ib < w; ib += c.pl.bi) {
-        const int wi = std::min(c.pl.bi, w - ib);
-        const int col = kb + ib;
-        e = launch_panel<T>(c.A + col + (size_t)col * lda, lda, n - col, wi, c.ipiv + col, col, c.info, c.pl.panel_ctas,
-                            kPanelSmemCap, s);
-        if (e != cudaSuccess) return e;
-        if (wi < w) {
-            int *mi = c.maps[2];
-            if ((e = launch_pivot_map(c.ipiv, col, wi, mi, nullptr, s)) != cudaSuccess) return e;
-            if (ib > 0 && (e = launch_swap_trsm<T>(c.A, lda, col, wi, mi, kb, col, 0, nullptr, 0, 0, 0, 0, s)) != cudaSuccess)
-                return e;
-            if (ib + wi < w) {
-                if ((e = launch_swap_trsm<T>(c.A, lda, col, wi, mi, col + wi, kb + w, 1, nullptr, 0, 0, 0, 0, s)) != cudaSuccess)
-                    return e;
-                const int r0 = col + wi;
-                if ((e = launch_gemm_simt<T>(n - r0, kb + w - r0, wi, c.A + r0 + (size_t)col * lda, lda,
-                                             c.A + col + (size_t)r0 * lda, lda, c.A + r0 + (size_t)r0 * lda, lda, s)) !=
-                    cudaSuccess)
-                    return e;
-            }
-        }
-    }
-    if ((e = launch_pivot_map(c.ipiv, kb, w, c.maps[par], c.perm, s)) != cudaSuccess) return e;
-    if constexpr (sizeof(T) == 4) {
-        if (c.pl.tc && kb + w < n) {
-            e = launch_stage_rows(n - kb - w, w, c.kpad, reinterpret_cast<const float *>(c.A) + (kb + w) + (size_t)kb * lda, lda,
-                                  c.stA[par], c.kinner, c.pl.nprod == 3, s);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    return cudaSuccess;
+    __nv_bfloat16 *stage = (c.pl.tc && kb + w < c.n) ? c.stA[par] : nullptr;
+    return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, std::min(c.pl.bi, w), c.ipiv + kb, kb,
+                                 c.info, c.maps[par], c.perm, stage, c.kinner, c.kpad, c.pl.nprod == 3, c.pl.panel_ctas,
+                                 kPanelSmemCap, s);
 }
 
 template <typename T>
+int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Plan &pl, cudaStream_t caller);
+
+template <typename T>
 int factor_impl(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Plan &pl, cudaStream_t caller) {
-    DevState *st = nullptr;
-    LU_CUDA_TRY(dev_state(&st));
     LU_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), caller));
     if (n == 0) return LU_OK;
+    if (pl.tc && !(((uintptr_t)A % 16 == 0) && lda % 4 == 0)) {
+        // the tensor-core update moves C with TMA (16-byte aligned columns):
+        // factor an aligned copy and copy the factors back
+        Workspace ws(caller);
+        const int ld2 = (n + 3) & ~3;
+        T *A2 = nullptr;
+        LU_CUDA_TRY(ws.get(&A2, (size_t)ld2 * n));
+        LU_CUDA_TRY(cudaMemcpy2DAsync(A2, sizeof(T) * ld2, A, sizeof(T) * lda, sizeof(T) * n, n, cudaMemcpyDeviceToDevice, caller));
+        int rc = factor_core<T>(n, A2, ld2, ipiv, info, perm, pl, caller);
+        if (rc != LU_OK) return rc;
+        LU_CUDA_TRY(cudaMemcpy2DAsync(A, sizeof(T) * lda, A2, sizeof(T) * ld2, sizeof(T) * n, n, cudaMemcpyDeviceToDevice, caller));
+        return LU_OK;
+    }
+    return factor_core<T>(n, A, lda, ipiv, info, perm, pl, caller);
+}
+
+template <typename T>
+int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Plan &pl, cudaStream_t caller) {
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
     std::lock_guard<std::recursive_mutex> lk(g_enqueue_mu);
     Workspace ws(caller);
     FactorCtx<T> c;
     c.n = n; c.A = A; c.lda = lda; c.ipiv = ipiv; c.info = info; c.perm = perm; c.pl = pl; c.st = st;
     const int bo = pl.bo;
-    for (int i = 0; i < 3; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
+    for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
+    LU_CUDA_TRY(ws.get(&c.tile_ctr, 2));
     if (perm) LU_CUDA_TRY(launch_iota(perm, n, caller));
     if (pl.tc) {
         c.kpad = tc_kpad(bo);
@@ -371,24 +375,29 @@ int factor_impl(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
         const int kb = k * bo, w = std::min(bo, n - kb), par = k & 1;
         const int cn0 = kb + w, wn = std::min(bo, n - cn0);
         const int *map = c.maps[par];
-        // ---- T_RU on U -------------------------------------------------------
+        const int rest0 = pl.lookahead ? cn0 + wn : cn0;
+        // ---- T_RU on U, first part: interchanges left of panel k, RU1 ------------
         LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evP[par], 0));
         if (kb > 0) LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, 0, kb, 0, U));
-        const int rest0 = pl.lookahead ? cn0 + wn : cn0;
-        if (rest0 < n) {
-            LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, rest0, n, 1, U));
-            LU_CUDA_TRY(update<T>(c, par, kb, w, rest0, n, U));
+        if (rest0 < n) LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, rest0, n, 1, U));
+        // ---- T_PF on P: PF1, PF2 on strip k+1, then PF3 = panel k+1 ------------------
+        if (wn > 0 && pl.lookahead) {
+            if (k > 0) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par ^ 1], 0));
+            LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P));
+            LU_CUDA_TRY(update<T>(c, par, kb, w, cn0, cn0 + wn, P));
+            // RU2 starts after PF2: when both become ready the panel (higher
+            // priority) is dispatched first, and RU2's queued CTAs fill the
+            // rest of the GPU and later the SMs the panel cluster frees
+            LU_CUDA_TRY(cudaEventRecord(st->evPF2, P));
+            LU_CUDA_TRY(factor_outer_panel<T>(c, cn0, wn, par ^ 1, P));
+            LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
+            LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evPF2, 0));
         }
+        // ---- T_RU on U, second part: RU2 ----------------------------------------------
+        if (rest0 < n) LU_CUDA_TRY(update<T>(c, par, kb, w, rest0, n, U));
         LU_CUDA_TRY(cudaEventRecord(st->evU[par], U));
-        // ---- T_PF on P: next panel --------------------------------------------
-        if (wn > 0) {
-            if (pl.lookahead) {
-                if (k > 0) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par ^ 1], 0));
-                LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P));
-                LU_CUDA_TRY(update<T>(c, par, kb, w, cn0, cn0 + wn, P));
-            } else {
-                LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par], 0));
-            }
+        if (wn > 0 && !pl.lookahead) {
+            LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par], 0));
             LU_CUDA_TRY(factor_outer_panel<T>(c, cn0, wn, par ^ 1, P));
             LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
         }
@@ -540,8 +549,22 @@ int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda
     LU_CUDA_TRY(launch_stage_rows(m, k, kpad, dA, lda, sa, kinner, split, s));
     LU_CUDA_TRY(launch_stage_cols(k, kpad, n, dB, ldb, sb, kinner, split, s));
     CUtensorMap ma, mb;
+    int *ctr = nullptr;
+    LU_CUDA_TRY(ws.get(&ctr, 1));
     LU_CUDA_TRY(make_stage_maps(&ma, sa, m, &mb, sb, n, kinner, kinner));
-    LU_CUDA_TRY(launch_gemm_tc(split ? 3 : 1, m, n, kpad, ma, 0, mb, 0, dC, ldc, st->status, lu_spin_bound_ns(nullptr), s));
+    if (tc_c_aligned(dC, ldc)) {
+        LU_CUDA_TRY(launch_gemm_tc(split ? 3 : 1, m, n, kpad, ma, 0, mb, 0, dC, ldc, ctr, st->status, lu_spin_bound_ns(nullptr), s));
+    } else {
+        // the kernel moves C with TMA (16-byte aligned rows): work on an aligned copy
+        const int ldt = (m + 3) & ~3;
+        float *ct = nullptr;
+        LU_CUDA_TRY(ws.get(&ct, (size_t)ldt * n));
+        LU_CUDA_TRY(cudaMemcpy2DAsync(ct, sizeof(float) * ldt, dC, sizeof(float) * ldc, sizeof(float) * m, n,
+                                      cudaMemcpyDeviceToDevice, s));
+        LU_CUDA_TRY(launch_gemm_tc(split ? 3 : 1, m, n, kpad, ma, 0, mb, 0, ct, ldt, ctr, st->status, lu_spin_bound_ns(nullptr), s));
+        LU_CUDA_TRY(cudaMemcpy2DAsync(dC, sizeof(float) * ldc, ct, sizeof(float) * ldt, sizeof(float) * m, n,
+                                      cudaMemcpyDeviceToDevice, s));
+    }
     return LU_OK;
 }
 

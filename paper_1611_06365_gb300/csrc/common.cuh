@@ -39,21 +39,32 @@ __device__ __forceinline__ void lu_st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Bounded spin until *flag >= target.  Returns false (and records
-// LU_ERR_TIMEOUT in *status) when `bound_ns` of globaltimer time has passed.
+__device__ __forceinline__ int lu_ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded spin until *flag >= target: relaxed polls, then one acquire fence
+// (an acquire on every poll would be needlessly expensive).  Returns false
+// (and records LU_ERR_TIMEOUT in *status) when `bound_ns` of globaltimer time
+// has passed.
 __device__ __forceinline__ bool lu_wait_flag(const int *flag, int target, int *status, long long bound_ns) {
-    if (lu_ld_acquire(flag) >= target) return true;
-    unsigned long long t0 = lu_globaltimer();
-    unsigned int spins = 0;
-    while (lu_ld_acquire(flag) < target) {
-        if (((++spins) & 63u) == 0u) {
-            if ((long long)(lu_globaltimer() - t0) > bound_ns) {
-                atomicExch(status, (int)LU_ERR_TIMEOUT);
-                return false;
+    if (lu_ld_relaxed(flag) < target) {
+        const unsigned long long t0 = lu_globaltimer();
+        unsigned int spins = 0;
+        while (lu_ld_relaxed(flag) < target) {
+            // back off: many pollers on one line would slow its writer down
+            __nanosleep(spins < 8 ? 32 : 256);
+            if (((++spins) & 7u) == 0u) {
+                if ((long long)(lu_globaltimer() - t0) > bound_ns) {
+                    atomicExch(status, (int)LU_ERR_TIMEOUT);
+                    return false;
+                }
             }
-            __nanosleep(64);
         }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     return true;
 }
 

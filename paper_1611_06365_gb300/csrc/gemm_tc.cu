@@ -1,25 +1,28 @@
 // Trailing update RL3 / PF2 / RU2 (section 3.1, Figure 1 right; section 3.2,
 // Figure 3) on the 5th-generation tensor cores: C := C - A * B with C in FP32
-// and the operands A = L21 and B = U12 rounded to BF16.
+// and the operands A = L21 and B = U12 rounded to BF16 (or split into two
+// BF16 halves, three products).
 //
-// Per CTA one 128 x 64 tile of C and the whole K (<= 256):
-//   * thread 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle) of
-//     the K-major BF16 operand tiles, one mbarrier per 64-wide K chunk;
-//   * thread 0 issues tcgen05.mma (kind::f16, M=128, N=64, K=16 per
-//     instruction) as soon as each chunk lands, accumulating in TMEM;
-//   * meanwhile all 128 threads prefetch their row of the C tile into
-//     registers (column-major C: a warp reads 128 contiguous bytes per column);
-//   * after tcgen05.commit signals the accumulator, each warp reads its 32
-//     TMEM lanes (tcgen05.ld 32x32b) and writes C - acc.
-// Two CTAs fit on an SM (about 100 KB of shared memory each), so one CTA's
-// epilogue (the HBM-bound part: C read and write in FP32) overlaps the other's
-// loads and MMAs.  Every mbarrier wait is bounded; on expiry the kernel records
-// LU_ERR_TIMEOUT, waits once more (bounded) for its own copies, frees its TMEM
-// and returns.
+// Persistent, warp-specialized kernel, one CTA per SM, 128 x 128 tiles of C
+// taken from a global atomic tile queue; all data movement through TMA:
+//   warp 0   producer: tile index from the queue; the tile's C block (FP32,
+//            128 rows x 128 columns, four 128 x 32 boxes) into the C buffer
+//            once the previous tile's store has drained it; the K chunks of
+//            the A and B tiles (128-byte swizzle) into a ring of stages;
+//   warp 1   MMA issuer: tcgen05.mma kind::f16 (M=128, N=128, K=16) into one
+//            of two TMEM accumulators; tcgen05.commit frees stages and hands
+//            the accumulator to the epilogue;
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator, C := C - acc in shared
+//            memory, then a TMA store of each 128 x 32 box.
+// So the HBM traffic of the update -- C read and written once in FP32 -- is
+// carried by TMA and overlaps the MMAs of the same and the next tile.  Every
+// mbarrier wait is bounded; on expiry the kernel records LU_ERR_TIMEOUT, waits
+// once more (bounded) for its own copies, frees its TMEM and returns.
 //
 // Operand staging (BF16, K contiguous, K padded to a multiple of 64 with zeros):
 //   A: row-major, element (i, k) at stageA[i * lds + k]  (the panel's L21)
 //   B: column-major, element (k, j) at stageB[j * lds + k]  (U12 by columns)
+// With the split, the low halves follow at k + kpad.
 #include "common.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -34,7 +37,9 @@ constexpr int kTcMaxK = 256;
 constexpr int kTcThreads = 192;      // 6 warps: TMA, MMA, 4 x epilogue
 constexpr int kTcChunkA = kTcBM * kTcBK * 2;   // 16 KB
 constexpr int kTcChunkB = kTcBN * kTcBK * 2;   // 16 KB
-constexpr size_t kTcSmem = 1024 + (size_t)6 * (kTcChunkA + kTcChunkB) + 256;   // 6 x1 stages = 3 x3 stages
+constexpr int kTcCBox = 32;                    // columns per C box
+constexpr int kTcCBytes = kTcBM * kTcBN * 4;   // 64 KB C buffer
+constexpr size_t kTcSmem = 1024 + (size_t)4 * (kTcChunkA + kTcChunkB) + kTcCBytes + 256;   // 4 x1 or 2 x3 stages
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -75,6 +80,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
 }
 
 // UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
@@ -123,38 +135,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Persistent, warp-specialized tile loop (one CTA per SM):
-//   warp 0  TMA producer: K chunks of the A and B tiles into a ring of
-//           shared-memory stages (full/empty mbarrier pair per stage);
-//   warp 1  MMA issuer: NPROD products per chunk into one of two TMEM
-//           accumulators (128 lanes x kTcBN columns each), tcgen05.commit
-//           frees the stage and, after the last chunk, hands the
-//           accumulator to the epilogue;
-//   warps 2-5  epilogue: prefetch the C tile row of each thread while the
-//           MMAs run, then C := C - acc from TMEM (tcgen05.ld), and release
-//           the accumulator so the MMAs of the tile after next can start.
-// NPROD = 1: C -= A_hi B_hi (plain BF16 operands).
-// NPROD = 3: split BF16, x = x_hi + x_lo with x_hi = bf16(x),
-//            x_lo = bf16(x - x_hi): C -= A_hi B_hi + A_hi B_lo + A_lo B_hi,
-//            about 16 significant bits per product instead of 8.
 template <int NPROD>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, int a_row0,
-               const __grid_constant__ CUtensorMap mapB, int b_col0, float *__restrict__ C, int ldc,
-               int *__restrict__ status, long long bound_ns) {
+               const __grid_constant__ CUtensorMap mapB, int b_col0, const __grid_constant__ CUtensorMap mapC,
+               int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns) {
     constexpr int NSPLIT = NPROD == 1 ? 1 : 2;
     constexpr uint32_t kStageBytes = (uint32_t)NSPLIT * (kTcChunkA + kTcChunkB);
-    constexpr int kStages = NPROD == 1 ? 6 : 3;
+    constexpr int kStages = NPROD == 1 ? 4 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (base - raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + (size_t)kStages * kStageBytes);
-    // bars: full[kStages], empty[kStages], acc_full[2], acc_empty[2]
+    const uint32_t sC = base + (uint32_t)kStages * kStageBytes;          // C buffer, 4 boxes [32 cols][128 rows]
+    float *Cs = reinterpret_cast<float *>(gbase + (size_t)kStages * kStageBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + (size_t)kStages * kStageBytes + kTcCBytes);
+    // bars: full[kStages], empty[kStages], acc_full[2], acc_empty[2], tile_full[2], c_full, c_empty
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8u * kStages;
-    const uint32_t accf0 = empty0 + 8u * kStages, acce0 = accf0 + 16u;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
+    const uint32_t accf0 = empty0 + 8u * kStages, acce0 = accf0 + 16u, tilef0 = acce0 + 16u;
+    const uint32_t cfull = tilef0 + 16u, cempty = cfull + 8u;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *stage_tile = reinterpret_cast<volatile int *>(tmem_slot + 2);        // [kStages]
+    volatile int *acc_tile = reinterpret_cast<volatile int *>(tmem_slot + 2 + kStages);  // [2]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nk = K / kTcBK;                       // K is a multiple of kTcBK
@@ -164,7 +167,13 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) { mbar_init(full0 + 8u * i, 1); mbar_init(empty0 + 8u * i, 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(accf0 + 8u * i, 1); mbar_init(acce0 + 8u * i, 128); }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(accf0 + 8u * i, 1);
+            mbar_init(acce0 + 8u * i, 128);
+            mbar_init(tilef0 + 8u * i, 1);
+        }
+        mbar_init(cfull, 1);
+        mbar_init(cempty, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -183,22 +192,43 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
     if (warp == 0) {
         if (lane == 0) {
             int s = 0;
-            uint32_t ph = 0;
-            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-                const int tm = (t % mt) * kTcBM, tn = (t / mt) * kTcBN;
-                for (int kc = 0; kc < nk; ++kc) {
-                    if (!mbar_wait_bounded(empty0 + 8u * s, ph ^ 1u, bound_ns)) { *abort_flag = 1; break; }
+            uint32_t ph = 0, cph = 0;
+            for (;;) {
+                int t = atomicAdd(tile_ctr, 1);
+                if (t >= ntiles || *abort_flag) t = -1;
+                const int tm = t >= 0 ? (t % mt) * kTcBM : 0, tn = t >= 0 ? (t / mt) * kTcBN : 0;
+                bool ok = true;
+                const int chunks = t >= 0 ? nk : 1;
+                for (int kc = 0; kc < chunks && ok; ++kc) {
+                    if (!mbar_wait_bounded(empty0 + 8u * s, ph ^ 1u, bound_ns)) { *abort_flag = 1; ok = false; break; }
                     const uint32_t st = base + (uint32_t)s * kStageBytes;
                     const uint32_t fb = full0 + 8u * s;
-                    mbar_expect_tx(fb, kStageBytes);
-                    tma_load_2d(st, &mapA, kc * kTcBK, a_row0 + tm, fb);
-                    tma_load_2d(st + NSPLIT * kTcChunkA, &mapB, kc * kTcBK, b_col0 + tn, fb);
-                    if (NSPLIT == 2) {
-                        tma_load_2d(st + kTcChunkA, &mapA, kpad_off + kc * kTcBK, a_row0 + tm, fb);
-                        tma_load_2d(st + 2 * kTcChunkA + kTcChunkB, &mapB, kpad_off + kc * kTcBK, b_col0 + tn, fb);
+                    stage_tile[s] = t;
+                    if (t < 0) {
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
+                    } else {
+                        mbar_expect_tx(fb, kStageBytes);
+                        tma_load_2d(st, &mapA, kc * kTcBK, a_row0 + tm, fb);
+                        tma_load_2d(st + NSPLIT * kTcChunkA, &mapB, kc * kTcBK, b_col0 + tn, fb);
+                        if (NSPLIT == 2) {
+                            tma_load_2d(st + kTcChunkA, &mapA, kpad_off + kc * kTcBK, a_row0 + tm, fb);
+                            tma_load_2d(st + 2 * kTcChunkA + kTcChunkB, &mapB, kpad_off + kc * kTcBK, b_col0 + tn, fb);
+                        }
                     }
                     if (++s == kStages) { s = 0; ph ^= 1u; }
                 }
+                // the tile's C block, once the previous tile's store has left the buffer
+                if (t >= 0 && ok) {
+                    if (!mbar_wait_bounded(cempty, cph ^ 1u, bound_ns)) { *abort_flag = 1; ok = false; }
+                    else {
+                        mbar_expect_tx(cfull, (uint32_t)kTcCBytes);
+#pragma unroll
+                        for (int b = 0; b < kTcBN / kTcCBox; ++b)
+                            tma_load_2d(sC + (uint32_t)b * (kTcBM * kTcCBox * 4), &mapC, tm, tn + b * kTcCBox, cfull);
+                        cph ^= 1u;
+                    }
+                }
+                if (t < 0 || !ok) break;
             }
         }
     } else if (warp == 1) {
@@ -206,15 +236,30 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
             const uint32_t idesc = umma_idesc_bf16(kTcBM, kTcBN);
             int s = 0;
             uint32_t ph = 0;
-            int it = 0;
-            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++it) {
+            for (int it = 0;; ++it) {
                 const int a = it & 1;
                 const uint32_t aph = (uint32_t)((it >> 1) & 1);
-                if (!mbar_wait_bounded(acce0 + 8u * a, aph ^ 1u, bound_ns)) { *abort_flag = 1; break; }
+                // the accumulator must be free before its tile index is replaced
+                bool stop = false;
+                if (!mbar_wait_bounded(acce0 + 8u * a, aph ^ 1u, bound_ns)) { *abort_flag = 1; stop = true; }
+                if (*abort_flag) stop = true;
+                int t = -1;
+                if (!stop) {
+                    if (!mbar_wait_bounded(full0 + 8u * s, ph, bound_ns)) { *abort_flag = 1; stop = true; }
+                    else t = stage_tile[s];
+                }
+                if (stop || t < 0) {
+                    acc_tile[a] = -1;
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tilef0 + 8u * a) : "memory");
+                    break;
+                }
+                acc_tile[a] = t;
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tilef0 + 8u * a) : "memory");
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t acc = tmem + (uint32_t)(a * kTcBN);
+                bool ok = true;
                 for (int kc = 0; kc < nk; ++kc) {
-                    if (!mbar_wait_bounded(full0 + 8u * s, ph, bound_ns)) { *abort_flag = 1; break; }
+                    if (kc > 0 && !mbar_wait_bounded(full0 + 8u * s, ph, bound_ns)) { *abort_flag = 1; ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t st = base + (uint32_t)s * kStageBytes;
                     const uint32_t sAh = st, sAl = st + kTcChunkA;
@@ -231,49 +276,63 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
                     umma_commit(empty0 + 8u * s);            // stage free once these MMAs are done
                     if (++s == kStages) { s = 0; ph ^= 1u; }
                 }
-                if (*abort_flag) break;
+                if (!ok) {
+                    // the epilogue of this tile is already waiting: release it without data
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(accf0 + 8u * a) : "memory");
+                    break;
+                }
                 umma_commit(accf0 + 8u * a);                 // accumulator ready
             }
         }
     } else {
-        // epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        // epilogue: warps 2..5 own TMEM lane quarters (warp % 4); thread = tile row
         const int q = warp & 3;
-        int it = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-            const int tm = (t % mt) * kTcBM, tn = (t / mt) * kTcBN;
+        const int r = q * 32 + lane;
+        const bool leader = (tid == 64);
+        uint32_t cph = 0;
+        for (int it = 0;; ++it) {
             const int a = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
-            const int row = tm + q * 32 + lane;
-            float cold[kTcBN];
-#pragma unroll
-            for (int c = 0; c < kTcBN; ++c) {
-                const int col = tn + c;
-                cold[c] = (row < m && col < n) ? C[(size_t)row + (size_t)col * ldc] : 0.f;
-            }
-            if (*abort_flag || !mbar_wait_bounded(accf0 + 8u * a, aph, bound_ns)) { *abort_flag = 1; break; }
+            if (!mbar_wait_bounded(tilef0 + 8u * a, aph, bound_ns)) { *abort_flag = 1; break; }
+            const int t = acc_tile[a];
+            if (t < 0) break;
+            const int tm = (t % mt) * kTcBM, tn = (t / mt) * kTcBN;
+            bool ok = mbar_wait_bounded(cfull, cph, bound_ns) && mbar_wait_bounded(accf0 + 8u * a, aph, bound_ns);
+            cph ^= 1u;
+            if (!ok || *abort_flag) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = tmem + (uint32_t)(a * kTcBN) + ((uint32_t)(q * 32) << 16);
 #pragma unroll
             for (int h = 0; h < kTcBN / 32; ++h) {
                 float v[32];
                 tmem_ld32(acc + (uint32_t)(h * 32), v);
-                if (row < m) {
+                float *box = Cs + (size_t)h * (kTcBM * kTcCBox);   // box h: [32 cols][128 rows]
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const int col = tn + h * 32 + c;
-                        if (col < n) C[(size_t)row + (size_t)col * ldc] = cold[h * 32 + c] - v[c];
-                    }
-                }
+                for (int c = 0; c < 32; ++c) box[c * kTcBM + r] -= v[c];
             }
+            // accumulator read: the MMAs of the tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8u * a) : "memory");
+            // results visible to the async proxy, then one thread stores the boxes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (leader) {
+#pragma unroll
+                for (int b = 0; b < kTcBN / kTcCBox; ++b)
+                    tma_store_2d(&mapC, tm, tn + b * kTcCBox, sC + (uint32_t)b * (kTcBM * kTcCBox * 4));
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(cempty) : "memory");
+            }
         }
+        if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0 && *abort_flag) {
         atomicExch(status, (int)LU_ERR_TIMEOUT);
         // give copies in flight one bounded chance to land before shared memory is released
         for (int i = 0; i < kStages; ++i) mbar_wait_bounded(full0 + 8u * i, 0, bound_ns / 4);
+        mbar_wait_bounded(cfull, 0, bound_ns / 4);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -364,12 +423,34 @@ cudaError_t make_stage_maps(CUtensorMap *mapA, const __nv_bfloat16 *stageA, int 
 int tc_box_rows() { return kTcBM; }
 int tc_box_cols() { return kTcBN; }
 
+// 2-D FP32 map over the m x n column-major block at C (leading dimension ldc):
+// x = row (contiguous), y = column; boxes of 128 rows x 32 columns.  TMA needs
+// C 16-byte aligned and ldc a multiple of 4 (checked by the caller).
+static cudaError_t make_c_map(CUtensorMap *map, float *C, int m, int n, int ldc) {
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)ldc * 4};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBM, (cuuint32_t)kTcCBox};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+bool tc_c_aligned(const float *C, int ldc) { return ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0); }
+
 // C[m x n] -= A[a_row0 + (0..m), 0..K) * B[0..K, b_col0 + (0..n)] through the maps
 // (nprod = 1: BF16 operands; nprod = 3: split BF16, staging holds hi | lo).
+// C must be 16-byte aligned with ldc a multiple of 4 (tc_c_aligned).
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
-                           int b_col0, float *C, int ldc, int *status, long long bound_ns, cudaStream_t s) {
+                           int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s) {
     if (m <= 0 || n <= 0 || K <= 0) return cudaSuccess;
     if (K > kTcMaxK || K % kTcBK != 0 || (nprod != 1 && nprod != 3)) return cudaErrorInvalidValue;
+    if (!tc_c_aligned(C, ldc)) return cudaErrorInvalidValue;
+    CUtensorMap mapC;
+    cudaError_t ec = make_c_map(&mapC, C, m, n, ldc);
+    if (ec != cudaSuccess) return ec;
     static int sms = 0;
     static bool attr[2] = {false, false};
     if (!sms) {
@@ -380,20 +461,24 @@ cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &ma
     }
     const int ntiles = lu_ceil_div(m, kTcBM) * lu_ceil_div(n, kTcBN);
     const int grid = ntiles < sms ? ntiles : sms;
+    cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
+    if (ez != cudaSuccess) return ez;
     if (nprod == 1) {
         if (!attr[0]) {
             cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
             if (e != cudaSuccess) return e;
             attr[0] = true;
         }
-        gemm_update_tc<1><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, C, ldc, status, bound_ns);
+        gemm_update_tc<1><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
+                                                            bound_ns);
     } else {
         if (!attr[1]) {
             cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
             if (e != cudaSuccess) return e;
             attr[1] = true;
         }
-        gemm_update_tc<3><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, C, ldc, status, bound_ns);
+        gemm_update_tc<3><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
+                                                            bound_ns);
     }
     lu_count_launch();
     return cudaGetLastError();

@@ -5,12 +5,12 @@
 //   interchanges at a time with the same row-map construction as the
 //   factorization's interchange kernel.
 // * gather_rows: X = B[perm, :].
-// * trsv_blocks: blocked substitution by row blocks of 64.  A persistent grid
-//   takes row blocks in order from an atomic ticket; the CTA of block I reads
-//   the off-diagonal blocks of its rows as the solutions of earlier blocks
-//   are published (flag per block, release/acquire), then solves its diagonal
-//   block and publishes.  A CTA only waits for blocks handed out before its
-//   own, which belong to CTAs already running, so the chain always advances;
+// * trsv_blocks: blocked substitution by row blocks of 64.  Warps take row
+//   blocks in order from an atomic ticket; the warp of block I accumulates the
+//   off-diagonal products of its rows as the solutions of earlier blocks are
+//   published (flag per block, release/acquire), then solves its diagonal
+//   block and publishes.  A warp only waits for blocks handed out before its
+//   own, which belong to warps already running, so the chain always advances;
 //   every wait is bounded and records LU_ERR_TIMEOUT on expiry.
 #include "common.cuh"
 #include <algorithm>
@@ -18,9 +18,10 @@
 namespace lu {
 
 constexpr int kTB = 64;           // row block
-constexpr int kTThreads = 256;
 constexpr int kMaxRhs = 16;       // right-hand sides per pass
 constexpr int kHash = 1024;
+constexpr int kFlagPad = 32;      // one flag per 128-byte line
+constexpr int kTWarps = 2;        // warps per CTA
 
 __global__ void ipiv_to_perm_kernel(const int *__restrict__ ipiv, int n, int *__restrict__ perm) {
     __shared__ int keys[kHash], slot_of[kHash];
@@ -72,96 +73,148 @@ __global__ void gather_rows_kernel(int n, int nrhs, const int *__restrict__ perm
 
 // LOWER: unit lower forward substitution (blocks taken top-down);
 // !LOWER: upper backward substitution (blocks taken bottom-up).
-template <typename T, bool LOWER>
-__global__ void __launch_bounds__(kTThreads)
+// One warp per 64-row block (two rows per lane), no CTA-wide barriers: a warp
+// takes its block from the ticket, stages its diagonal block and the
+// off-diagonal block of its last dependency in shared memory while earlier
+// blocks are still being solved, accumulates the products of the earlier
+// published blocks straight from global memory (32 columns of loads in
+// flight), and so keeps only a shared-memory product, the diagonal solve
+// (shuffles) and the publication on the block-to-block chain.  NQ is the
+// number of right-hand sides handled per pass (a compile-time bound, so the
+// per-lane arrays stay in registers).
+template <typename T, bool LOWER, int NQ>
+__global__ void __launch_bounds__(32 * kTWarps)
 trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ X, int ldx, int *__restrict__ ticket,
             int *__restrict__ flags, int *__restrict__ status, long long bound_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*Ld)[kTB + 1] = reinterpret_cast<T (*)[kTB + 1]>(smem_raw);                       // diagonal block [r][c]
-    T (*yJ)[kMaxRhs] = reinterpret_cast<T (*)[kMaxRhs]>(smem_raw + sizeof(T) * kTB * (kTB + 1));
-    T (*part)[kTB][kMaxRhs] = reinterpret_cast<T (*)[kTB][kMaxRhs]>(smem_raw + sizeof(T) * (kTB * (kTB + 1) + kTB * kMaxRhs));
-    T (*xb)[kMaxRhs] = reinterpret_cast<T (*)[kMaxRhs]>(smem_raw + sizeof(T) * (kTB * (kTB + 1) + 5 * kTB * kMaxRhs));
-    __shared__ int tk_s, abort_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *Dg = reinterpret_cast<T *>(smem_raw) + (size_t)warp * 2 * kTB * kTB;   // diagonal block [c][r]
+    T *Lp = Dg + (size_t)kTB * kTB;                                            // last dependency block [c][r]
     const int nblk = (n + kTB - 1) / kTB;
-    const int r = threadIdx.x & (kTB - 1), g = threadIdx.x >> 6;
     for (;;) {
-        if (threadIdx.x == 0) { tk_s = atomicAdd(ticket, 1); abort_s = 0; }
-        __syncthreads();
-        const int t = tk_s;
+        int t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= nblk) break;
         const int I = LOWER ? t : nblk - 1 - t;
         const int r0 = I * kTB, rows = min(kTB, n - r0);
-        T acc[kMaxRhs];
+        const bool has0 = lane < rows, has1 = lane + 32 < rows;
+        const int ndep = LOWER ? I : nblk - 1 - I;
+        const int Jlast = LOWER ? I - 1 : I + 1;
+        const int clast = Jlast * kTB, ncl = ndep > 0 ? min(kTB, n - clast) : 0;
+        // stage the diagonal block and the last dependency's block (matrix data only)
+        for (int blk = 0; blk < 2; ++blk) {
+            const int cbase = blk == 0 ? r0 : clast, ncol = blk == 0 ? rows : ncl;
+            T *dst = blk == 0 ? Dg : Lp;
+            for (int cb = 0; cb < ncol; cb += 16) {
+                T a[16], b[16];
 #pragma unroll
-        for (int q = 0; q < kMaxRhs; ++q) acc[q] = T(0);
-        // off-diagonal blocks, in the order their solutions appear
-        for (int s = 0; s < (LOWER ? I : nblk - 1 - I); ++s) {
+                for (int u = 0; u < 16; ++u) {
+                    const int c = cb + u;
+                    a[u] = (has0 && c < ncol) ? LU[(size_t)(r0 + lane) + (size_t)(cbase + c) * lda] : T(0);
+                    b[u] = (has1 && c < ncol) ? LU[(size_t)(r0 + lane + 32) + (size_t)(cbase + c) * lda] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    dst[(cb + u) * kTB + lane] = a[u];
+                    dst[(cb + u) * kTB + lane + 32] = b[u];
+                }
+            }
+        }
+        T acc0[NQ], acc1[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) { acc0[q] = T(0); acc1[q] = T(0); }
+        bool ok = true;
+        for (int s = 0; s < ndep; ++s) {
             const int J = LOWER ? s : nblk - 1 - s;
             const int c0 = J * kTB, cols = min(kTB, n - c0);
-            if (threadIdx.x == 0) {
-                if (!lu_wait_flag(&flags[J], 1, status, bound_ns)) abort_s = 1;
-                __threadfence();
+            int w = 1;
+            if (lane == 0) w = lu_wait_flag(&flags[(size_t)J * kFlagPad], 1, status, bound_ns) ? 1 : 0;
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (!w) { ok = false; break; }
+            T y0[NQ], y1[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                y0[q] = (q < nrhs && lane < cols) ? __ldcg(&X[(size_t)(c0 + lane) + (size_t)q * ldx]) : T(0);
+                y1[q] = (q < nrhs && lane + 32 < cols) ? __ldcg(&X[(size_t)(c0 + lane + 32) + (size_t)q * ldx]) : T(0);
             }
-            __syncthreads();
-            if (abort_s) return;
-            for (int e = threadIdx.x; e < cols * nrhs; e += kTThreads) {
-                const int c = e % cols, q = e / cols;
-                yJ[c][q] = __ldcg(&X[(size_t)(c0 + c) + (size_t)q * ldx]);
-            }
-            __syncthreads();
-            if (r < rows) {
-                for (int c = g; c < cols; c += 4) {
-                    const T l = LU[(size_t)(r0 + r) + (size_t)(c0 + c) * lda];
-                    for (int q = 0; q < nrhs; ++q) acc[q] = fma(-l, yJ[c][q], acc[q]);
-                }
-            }
-            __syncthreads();
-        }
-        for (int q = 0; q < nrhs; ++q) part[g][r][q] = acc[q];
-        // diagonal block into shared memory
-        for (int e = threadIdx.x; e < kTB * kTB; e += kTThreads) {
-            const int rr = e & (kTB - 1), cc = e >> 6;
-            Ld[rr][cc] = (rr < rows && cc < rows) ? LU[(size_t)(r0 + rr) + (size_t)(r0 + cc) * lda] : T(0);
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < rows * nrhs; e += kTThreads) {
-            const int rr = e % rows, q = e / rows;
-            xb[rr][q] = X[(size_t)(r0 + rr) + (size_t)q * ldx] + part[0][rr][q] + part[1][rr][q] + part[2][rr][q] +
-                        part[3][rr][q];
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            for (int q = 0; q < nrhs; ++q) {
-                if (LOWER) {
-                    for (int jj = 0; jj < rows; ++jj) {
-                        __syncwarp();
-                        const T y = xb[jj][q];
-                        for (int rr = lane; rr < rows; rr += 32)
-                            if (rr > jj) xb[rr][q] = fma(-Ld[rr][jj], y, xb[rr][q]);
-                    }
-                } else {
-                    for (int jj = rows - 1; jj >= 0; --jj) {
-                        __syncwarp();
-                        if (lane == 0) xb[jj][q] = xb[jj][q] / Ld[jj][jj];
-                        __syncwarp();
-                        const T y = xb[jj][q];
-                        for (int rr = lane; rr < jj; rr += 32) xb[rr][q] = fma(-Ld[rr][jj], y, xb[rr][q]);
-                    }
-                }
+            if (J == Jlast) {
                 __syncwarp();
+#pragma unroll 8
+                for (int c = 0; c < cols; ++c) {
+                    const T l0 = Lp[c * kTB + lane], l1 = Lp[c * kTB + lane + 32];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const T yv = __shfl_sync(0xffffffffu, c < 32 ? y0[q] : y1[q], c & 31);
+                        acc0[q] = fma(-l0, yv, acc0[q]);
+                        acc1[q] = fma(-l1, yv, acc1[q]);
+                    }
+                }
+            } else {
+                const T *col = LU + (size_t)c0 * lda + r0;
+                for (int cb = 0; cb < cols; cb += 32) {
+                    T la[32], lb[32];
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const int c = cb + u;
+                        la[u] = (has0 && c < cols) ? col[(size_t)c * lda + lane] : T(0);
+                        lb[u] = (has1 && c < cols) ? col[(size_t)c * lda + lane + 32] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            const T yv = __shfl_sync(0xffffffffu, cb == 0 ? y0[q] : y1[q], u);
+                            acc0[q] = fma(-la[u], yv, acc0[q]);
+                            acc1[q] = fma(-lb[u], yv, acc1[q]);
+                        }
+                    }
+                }
             }
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < rows * nrhs; e += kTThreads) {
-            const int rr = e % rows, q = e / rows;
-            X[(size_t)(r0 + rr) + (size_t)q * ldx] = xb[rr][q];
+        if (!ok) return;
+        // x = b + products, then the diagonal solve (two rows per lane)
+        T x0[NQ], x1[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            x0[q] = (q < nrhs && has0) ? X[(size_t)(r0 + lane) + (size_t)q * ldx] + acc0[q] : T(0);
+            x1[q] = (q < nrhs && has1) ? X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] + acc1[q] : T(0);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            lu_st_release(&flags[I], 1);
+        __syncwarp();
+        if (LOWER) {
+            for (int jj = 0; jj < rows; ++jj) {
+                const T l0 = Dg[jj * kTB + lane], l1 = Dg[jj * kTB + lane + 32];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const T y = __shfl_sync(0xffffffffu, jj < 32 ? x0[q] : x1[q], jj & 31);
+                    if (lane > jj) x0[q] = fma(-l0, y, x0[q]);
+                    if (lane + 32 > jj) x1[q] = fma(-l1, y, x1[q]);
+                }
+            }
+        } else {
+            for (int jj = rows - 1; jj >= 0; --jj) {
+                const T d = Dg[jj * kTB + jj];
+                const T l0 = Dg[jj * kTB + lane], l1 = Dg[jj * kTB + lane + 32];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    if (jj < 32 && lane == jj) x0[q] = x0[q] / d;
+                    if (jj >= 32 && lane + 32 == jj) x1[q] = x1[q] / d;
+                    const T y = __shfl_sync(0xffffffffu, jj < 32 ? x0[q] : x1[q], jj & 31);
+                    if (lane < jj) x0[q] = fma(-l0, y, x0[q]);
+                    if (lane + 32 < jj) x1[q] = fma(-l1, y, x1[q]);
+                }
+            }
         }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (q < nrhs) {
+                if (has0) X[(size_t)(r0 + lane) + (size_t)q * ldx] = x0[q];
+                if (has1) X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] = x1[q];
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) lu_st_release(&flags[(size_t)I * kFlagPad], 1);
     }
 }
 
@@ -182,32 +235,47 @@ cudaError_t launch_gather_rows(int n, int nrhs, const int *perm, const TI *B, in
     return cudaGetLastError();
 }
 
-// Workspace: ints [2 + 2*nblk] (two tickets, two flag arrays), zeroed here.
+// two tickets, then two flag arrays with one flag per 128-byte line
+size_t trsv_workspace_ints(int n) { return (size_t)kFlagPad * (1 + 2 * ((n + kTB - 1) / kTB)); }
+
+template <typename T, int NQ>
+static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, int n, int nq, T *X, int ldx, int *ws, int nblk,
+                                  int *status, long long bound_ns, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(trsv_blocks<T, true, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(trsv_blocks<T, false, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    trsv_blocks<T, true, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws, ws + kFlagPad, status, bound_ns);
+    lu_count_launch();
+    trsv_blocks<T, false, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws + 1,
+                                                               ws + kFlagPad + (size_t)nblk * kFlagPad, status, bound_ns);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+// Workspace: trsv_workspace_ints(n) ints, zeroed here before each pass.
 template <typename T>
 cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status,
                              long long bound_ns, int sms, cudaStream_t s) {
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     const int nblk = (n + kTB - 1) / kTB;
-    cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int) * (size_t)(2 + 2 * nblk), s);
-    if (e != cudaSuccess) return e;
-    const int grid = std::min(nblk, 2 * sms);
-    const size_t smem = sizeof(T) * (kTB * (kTB + 1) + 6 * kTB * kMaxRhs);
-    e = cudaFuncSetAttribute(trsv_blocks<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(trsv_blocks<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    const size_t wsn = trsv_workspace_ints(n);
+    const int grid = std::min((nblk + kTWarps - 1) / kTWarps, 8 * sms);
+    const size_t smem = sizeof(T) * (size_t)kTWarps * 2 * kTB * kTB;
+    cudaError_t e = cudaSuccess;
     for (int q0 = 0; q0 < nrhs; q0 += kMaxRhs) {
         const int nq = std::min(kMaxRhs, nrhs - q0);
-        if (q0 > 0) {
-            e = cudaMemsetAsync(ws, 0, sizeof(int) * (size_t)(2 + 2 * nblk), s);
-            if (e != cudaSuccess) return e;
-        }
-        trsv_blocks<T, true><<<grid, kTThreads, smem, s>>>(LU, lda, n, nq, X + (size_t)q0 * ldx, ldx, ws, ws + 2, status, bound_ns);
-        lu_count_launch();
-        trsv_blocks<T, false><<<grid, kTThreads, smem, s>>>(LU, lda, n, nq, X + (size_t)q0 * ldx, ldx, ws + 1, ws + 2 + nblk, status, bound_ns);
-        lu_count_launch();
+        e = cudaMemsetAsync(ws, 0, sizeof(int) * wsn, s);
+        if (e != cudaSuccess) return e;
+        T *Xq = X + (size_t)q0 * ldx;
+        if (nq == 1) e = launch_trsv_nq<T, 1>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
+        else if (nq <= 2) e = launch_trsv_nq<T, 2>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
+        else if (nq <= 4) e = launch_trsv_nq<T, 4>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
+        else if (nq <= 8) e = launch_trsv_nq<T, 8>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
+        else e = launch_trsv_nq<T, 16>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 __global__ void iota_kernel(int *v, int n) {
@@ -221,7 +289,6 @@ cudaError_t launch_iota(int *v, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-size_t trsv_workspace_ints(int n) { return (size_t)(2 + 2 * ((n + kTB - 1) / kTB)); }
 
 template cudaError_t launch_gather_rows<double, double>(int, int, const int *, const double *, int, double *, int, cudaStream_t);
 template cudaError_t launch_gather_rows<float, float>(int, int, const int *, const float *, int, float *, int, cudaStream_t);

@@ -2,10 +2,10 @@
 // solve RL2 / PF1 / RU1: A12 := trilu(A11)^{-1} A12 (section 3.1, Figure 1
 // right; section 3.2, Figure 3).
 //
-// The b interchanges of a panel are first turned into one row map (kernel
-// build_pivot_map): the set S of rows they touch (the b panel rows plus every
-// distinct target row) and, for each row of S, the row whose old content it
-// receives.  Applying the interchanges in order equals one gather/scatter over
+// The b interchanges of a panel are first turned into one row map (built at
+// the end of the panel kernel): the set S of rows they touch (the b panel rows
+// plus every distinct target row) and, for each row of S, the row whose old
+// content it receives.  Applying the interchanges in order equals one gather/scatter over
 // S, so every column strip can then be processed independently and in
 // parallel -- the paper notes the permutation is embarrassingly parallel
 // (section 3.1) and spreads it over all threads (section 3.2).
@@ -14,65 +14,13 @@
 
 namespace lu {
 
-constexpr int kMapHash = 4096;      // open-addressing table (> 4 x 2 x 512)
 constexpr int kSwapThreads = 256;
 constexpr int kStrip = 32;          // columns per CTA
+constexpr int kVS = kStrip + 1;      // row stride of the strip buffer (bank-conflict padding)
 constexpr int kTrsmBlk = 32;        // diagonal block of the blocked TRSM
 
-// map layout in global memory: [0] = count, [1 .. 1+2b) rows, [1+2b .. 1+4b) src
-__global__ void build_pivot_map(const int *__restrict__ ipiv, int kb, int b, int *__restrict__ map,
-                                int *__restrict__ perm) {
-    __shared__ int keys[kMapHash];
-    __shared__ int slot_of[kMapHash];
-    extern __shared__ int dyn[];
-    int *rows = dyn;            // [2b]
-    int *cont = dyn + 2 * b;    // [2b]
-    __shared__ int cnt_s;
-    for (int i = threadIdx.x; i < kMapHash; i += blockDim.x) keys[i] = -1;
-    for (int t = threadIdx.x; t < b; t += blockDim.x) { rows[t] = kb + t; cont[t] = kb + t; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int cnt = b;
-        for (int j = 0; j < b; ++j) {
-            const int r = kb + j;
-            const int p = ipiv[kb + j] - 1;
-            if (p == r) continue;
-            int ip;
-            if (p < kb + b) {
-                ip = p - kb;
-            } else {
-                unsigned h = ((unsigned)p * 2654435761u) & (kMapHash - 1);
-                while (keys[h] != -1 && keys[h] != p) h = (h + 1) & (kMapHash - 1);
-                if (keys[h] == -1) {
-                    keys[h] = p;
-                    slot_of[h] = cnt;
-                    rows[cnt] = p;
-                    cont[cnt] = p;
-                    ++cnt;
-                }
-                ip = slot_of[h];
-            }
-            int t = cont[j];
-            cont[j] = cont[ip];
-            cont[ip] = t;
-        }
-        cnt_s = cnt;
-        map[0] = cnt;
-    }
-    __syncthreads();
-    const int cnt = cnt_s;
-    for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-        map[1 + s] = rows[s];
-        map[1 + 2 * b + s] = cont[s];
-    }
-    if (perm) {
-        // the row permutation P as a vector: P A row j = A row perm[j]
-        int *old = cont + 2 * b;   // [2b] scratch after rows/cont
-        for (int s = threadIdx.x; s < cnt; s += blockDim.x) old[s] = perm[cont[s]];
-        __syncthreads();
-        for (int s = threadIdx.x; s < cnt; s += blockDim.x) perm[rows[s]] = old[s];
-    }
-}
+// map layout in global memory (written by the panel kernel): [0] = count,
+// [1 .. 1+2b) rows, [1+2b .. 1+4b) src
 
 template <typename T> __device__ __forceinline__ __nv_bfloat16 to_bf16(T v) { return __float2bfloat16_rn((float)v); }
 
@@ -90,8 +38,8 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
     int *rows = reinterpret_cast<int *>(smem_raw);              // [2b]
     int *src = rows + 2 * b;                                     // [2b]
     T *V = reinterpret_cast<T *>(smem_raw + (((size_t)4 * b * sizeof(int) + 15) & ~(size_t)15));
-    // V: [2b][kStrip], rows of S by strip column (X = first b rows)
-    T *Lblk = V + (size_t)2 * b * kStrip;                       // [kTrsmBlk][b] column slab of L11
+    // V: [2b][kVS], rows of S by strip column (X = first b rows)
+    T *Lblk = V + (size_t)2 * b * kVS;                          // [kTrsmBlk][b] column slab of L11
 
     const int c0 = c_begin + blockIdx.x * kStrip;
     const int ncol = min(kStrip, c_end - c0);
@@ -101,21 +49,22 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
         src[s] = map[1 + 2 * b + s];
     }
     __syncthreads();
-    // gather old values (threads run down S for a fixed column)
+    // gather old values (threads run down S for a fixed column: coalesced for the panel rows)
     for (int e = threadIdx.x; e < cnt * ncol; e += blockDim.x) {
         const int s = e % cnt, c = e / cnt;
-        V[(size_t)s * kStrip + c] = A[(size_t)src[s] + (size_t)(c0 + c) * lda];
+        V[(size_t)s * kVS + c] = A[(size_t)src[s] + (size_t)(c0 + c) * lda];
     }
     __syncthreads();
     // scatter rows outside the panel (and, without a solve, the panel rows too)
     const int first = do_trsm ? b : 0;
     for (int e = threadIdx.x; e < (cnt - first) * ncol; e += blockDim.x) {
         const int s = first + e % (cnt - first), c = e / (cnt - first);
-        A[(size_t)rows[s] + (size_t)(c0 + c) * lda] = V[(size_t)s * kStrip + c];
+        A[(size_t)rows[s] + (size_t)(c0 + c) * lda] = V[(size_t)s * kVS + c];
     }
     if (!do_trsm) return;
 
     // blocked forward substitution with unit lower L11 on X = V[0:b][0:ncol]
+    const int tc = threadIdx.x % kStrip, tg = threadIdx.x / kStrip, ng = kSwapThreads / kStrip;
     for (int d0 = 0; d0 < b; d0 += kTrsmBlk) {
         const int db = min(kTrsmBlk, b - d0);
         // stage the column slab L11[d0:b, d0:d0+db] (rows d0..b-1)
@@ -125,31 +74,30 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
             const int r = e % slab_rows, c = e / slab_rows;
             Lblk[(size_t)c * b + r] = A[(size_t)(kb + d0 + r) + (size_t)(kb + d0 + c) * lda];
         }
-        __syncthreads();
-        // diagonal block: one thread per column
-        if (threadIdx.x < ncol) {
-            const int c = threadIdx.x;
-            for (int jj = 0; jj < db; ++jj) {
-                const T x = V[(size_t)(d0 + jj) * kStrip + c];
-                for (int ii = jj + 1; ii < db; ++ii)
-                    V[(size_t)(d0 + ii) * kStrip + c] = fma(-Lblk[(size_t)jj * b + ii], x, V[(size_t)(d0 + ii) * kStrip + c]);
+        // diagonal block: rows in parallel, one step per column of L
+        for (int jj = 0; jj < db; ++jj) {
+            __syncthreads();
+            if (tc < ncol) {
+                const T x = V[(size_t)(d0 + jj) * kVS + tc];
+                for (int ii = jj + 1 + tg; ii < db; ii += ng)
+                    V[(size_t)(d0 + ii) * kVS + tc] = fma(-Lblk[(size_t)jj * b + ii], x, V[(size_t)(d0 + ii) * kVS + tc]);
             }
         }
         __syncthreads();
         // rows below the diagonal block: X[r] -= L[r, d0:d0+db] X[d0:d0+db]
         const int below = b - d0 - db;
         for (int e = threadIdx.x; e < below * ncol; e += blockDim.x) {
-            const int r = e % below, c = e / below;
-            T acc = V[(size_t)(d0 + db + r) * kStrip + c];
+            const int c = e % ncol, r = e / ncol;
+            T acc = V[(size_t)(d0 + db + r) * kVS + c];
             for (int jj = 0; jj < db; ++jj)
-                acc = fma(-Lblk[(size_t)jj * b + db + r], V[(size_t)(d0 + jj) * kStrip + c], acc);
-            V[(size_t)(d0 + db + r) * kStrip + c] = acc;
+                acc = fma(-Lblk[(size_t)jj * b + db + r], V[(size_t)(d0 + jj) * kVS + c], acc);
+            V[(size_t)(d0 + db + r) * kVS + c] = acc;
         }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < b * ncol; e += blockDim.x) {
         const int r = e % b, c = e / b;
-        const T x = V[(size_t)r * kStrip + c];
+        const T x = V[(size_t)r * kVS + c];
         A[(size_t)(kb + r) + (size_t)(c0 + c) * lda] = x;
         if (stage) {
             const __nv_bfloat16 hi = to_bf16(x);
@@ -169,16 +117,9 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
 size_t swap_trsm_smem_bytes(int b, size_t elem) {
     size_t a = (size_t)4 * b * sizeof(int);
     a = (a + 15) & ~(size_t)15;
-    a += (size_t)2 * b * kStrip * elem;
+    a += (size_t)2 * b * kVS * elem;
     a += (size_t)kTrsmBlk * b * elem;
     return a + 16;
-}
-
-cudaError_t launch_pivot_map(const int *ipiv, int kb, int b, int *map, int *perm, cudaStream_t s) {
-    size_t smem = (size_t)6 * b * sizeof(int);
-    build_pivot_map<<<1, 256, smem, s>>>(ipiv, kb, b, map, perm);
-    lu_count_launch();
-    return cudaGetLastError();
 }
 
 template <typename T>
