@@ -267,7 +267,7 @@ def run_ours(args):
     # time to backward error 1e-14: mixed precision vs FP64 on a kappa = 1e5 matrix
     tts = None
     if not args.skip_mixed and rank == 0:
-        tts = time_to_solution(args, dev, ms_per_step)
+        tts = time_to_solution(args, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -291,7 +291,7 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def time_to_solution(args, dev, fp64_ms):
+def time_to_solution(args, dev):
     """Mixed-precision solve vs the FP64 factor+solve, both to eta <= 1e-14."""
     import torch
 
@@ -315,12 +315,56 @@ def time_to_solution(args, dev, fp64_ms):
     x = X.view(-1)
     r = B.view(-1) - A.t() @ x
     eta = float(r.abs().max() / (A.abs().sum(0).max() * x.abs().max() + B.abs().max()))
-    return {"n": n, "kappa": MIXED_KAPPA, "reflectors_per_side": MIXED_REFLECTORS, "nrhs": 1,
+    # the FP64 path to the same target: FP64 factorization, FP64 refinement until eta <= 1e-14
+    X64 = torch.zeros_like(B)
+    rep64 = lu.lu_solve_mixed(A, B, X64, fp64_factor=1)
+    torch.cuda.synchronize()
+    x64 = X64.view(-1)
+    r64 = B.view(-1) - A.t() @ x64
+    eta64 = float(r64.abs().max() / (A.abs().sum(0).max() * x64.abs().max() + B.abs().max()))
+    return {"n": n, "kappa": MIXED_KAPPA, "reflectors_per_side": MIXED_REFLECTORS, "nrhs": 1, "target_eta": 1e-14,
             "mixed_ms": rep.t_total_ms, "mixed_wall_ms": wall * 1e3, "mixed_factor_ms": rep.t_factor_ms,
             "mixed_refine_ms": rep.t_refine_ms, "mixed_rung": rep.rung, "mixed_iterations": rep.iterations,
             "mixed_gmres_iters": rep.gmres_iters, "mixed_eta": eta, "mixed_fell_back": rep.fell_back,
-            "fp64_ms": fp64_ms if n == args.n else None,
-            "speedup_vs_fp64": (fp64_ms / rep.t_total_ms) if (n == args.n and rep.t_total_ms > 0) else None}
+            "fp64_ms": rep64.t_total_ms, "fp64_iterations": rep64.iterations, "fp64_eta": eta64,
+            "speedup_vs_fp64": rep64.t_total_ms / rep.t_total_ms if rep.t_total_ms > 0 else None}
+
+
+def run_case(args):
+    """Single-kernel cases for profiling (one launch of the kernel of interest)."""
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    dev = torch.device("cuda", 0)
+    lu.build()
+    if args.case == "tc_update":
+        # split-BF16 trailing update, C 8192 x 8192 FP32 (256 MiB, larger than L2), K = 256
+        m = n = 8192
+        k = 256
+        A = li.uniform_colmajor_torch(m, k, 1, dev, torch.float32)
+        B = li.uniform_colmajor_torch(k, n, 2, dev, torch.float32)
+        C = li.uniform_colmajor_torch(m, n, 3, dev, torch.float32)
+        lu.lu_trailing_update(lu.LU_UPDATE_BF16X3, A, B, C, m, n, k)
+    elif args.case == "fp64_factor":
+        # FP64 factorization, n = 8192 (512 MiB), panel width 16 as in the n = 16384 workload
+        n = 8192
+        A = li.uniform_colmajor_torch(n, n, 5, dev, torch.float64)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        lu.lu_factor(A, ipiv, info, nb=16)
+    elif args.case == "mixed_factor":
+        # FP32 factorization with the split-BF16 update, n = 8192
+        n = 8192
+        A = li.uniform_colmajor_torch(n, n, 5, dev, torch.float32)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        lu.lu_factor(A, ipiv, info, update=lu.LU_UPDATE_BF16X3)
+    else:
+        raise SystemExit(f"unknown case {args.case}")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "ok": True}))
 
 
 def main():
@@ -331,11 +375,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--mixed-n", dest="mixed_n", type=int, default=MIXED_N)
-    ap.add_argument("--cpu-n", dest="cpu_n", type=int, default=4096)
+    ap.add_argument("--cpu-n", dest="cpu_n", type=int, default=8192)
     ap.add_argument("--ref-n", dest="ref_n", type=int, default=2048)
     ap.add_argument("--skip-mixed", dest="skip_mixed", action="store_true")
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
+    ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor"], default=None,
+                    help="run one profiling case instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
