@@ -114,8 +114,9 @@ int lu_solve(lu_dtype dt, int n, int nrhs, const void *dLU, int lda, const int *
  *   Workspace comes from one fixed array in device memory of
  *   lu_solve_noalloc_capacity() bytes (4 MiB) that every GPU loading the
  *   library keeps until exit.  A request needs about
- *   4 n + elem * n * nrhs + 256 ceil(n/64) bytes plus alignment (elem = 8 for
- *   LU_F64, 4 for LU_F32); a larger one returns LU_ERR_SCRATCH and launches
+ *   4 n + elem * n * nrhs + 16 n min(nrhs, 16) + 256 bytes plus alignment
+ *   (elem = 8 for LU_F64, 4 for LU_F32; e.g. n = 65536, nrhs = 1 in FP32
+ *   takes 1.5 MiB); a larger one returns LU_ERR_SCRATCH and launches
  *   nothing.  The first call on a device looks up the array's device address
  *   (make it before any stream capture).  All calls share the array: calls
  *   whose work overlaps on the GPU race and must be serialized by the caller.
@@ -233,6 +234,34 @@ int lu_last_device_status(void *stream, int reset);
  */
 int lu_update_timing(int enable);
 int lu_update_timing_read(long long *launches, double *total_ms, double *flops, double *bytes);
+
+/*
+ * lu_trace -- launch trace of the factorization schedule (section 4's
+ * execution traces, one row per task): with enable != 0, every launch of
+ * lu_factor's blocked loop is bracketed by two CUDA events on the stream it
+ * runs on (stream 0: the panel stream PF, 1: the update stream RU).  Tracing
+ * adds host work per launch; it is off by default.  Returns 0.
+ * lu_trace_read -- waits for the recorded events and writes up to max_events
+ * records into the host array out, times in ms from the earliest recorded
+ * start; clears the record.  Returns the number written (with out == NULL:
+ * the number recorded) or a negative status.
+ */
+enum {
+    LU_TRACE_PANEL = 0,      /* PF3 / RL1: panel factorization of panel `step` */
+    LU_TRACE_SWAP_LEFT = 1,  /* interchanges of panel `step` on the L columns to its left */
+    LU_TRACE_RU1 = 2,        /* interchanges + U12 solve on the RU columns */
+    LU_TRACE_PF1 = 3,        /* interchanges + U12 solve on the next panel's columns */
+    LU_TRACE_PF2 = 4,        /* trailing update of the next panel's columns */
+    LU_TRACE_RU2 = 5         /* trailing update of the RU columns */
+};
+typedef struct {
+    int kind;       /* LU_TRACE_* */
+    int step;       /* iteration k (for LU_TRACE_PANEL: the panel index) */
+    int stream;     /* 0: PF stream, 1: RU stream */
+    float t_start_ms, t_end_ms;
+} lu_trace_event;
+int lu_trace(int enable);
+int lu_trace_read(lu_trace_event *out, int max_events);
 
 /* Number of CUDA kernels this library has launched since it was loaded. */
 long long lu_kernel_launches(void);

@@ -23,13 +23,14 @@ __all__ = [
     "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LuError", "lib", "build",
     "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status",
-    "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_kernel_launches", "to_colmajor", "from_colmajor", "MixedReport",
+    "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_kernel_launches", "to_colmajor", "from_colmajor", "MixedReport",
 ]
 
 LU_F64, LU_F32 = 0, 1
 LU_UPDATE_NATIVE, LU_UPDATE_BF16, LU_UPDATE_BF16X3 = 0, 1, 2
 LU_ERR_CUDA, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED = -100, -101, -102, -103
 LU_ERR_SCRATCH = -104
+LU_TRACE_KINDS = ("panel", "swap_left", "ru1", "pf1", "pf2", "ru2")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -97,6 +98,10 @@ def lib():
         L.lu_update_timing_read.argtypes = [ctypes.POINTER(ctypes.c_longlong)] + [ctypes.POINTER(ctypes.c_double)] * 3
         L.lu_update_timing_read.restype = i
         L.lu_kernel_launches.restype = ctypes.c_longlong
+        L.lu_trace.argtypes = [i]
+        L.lu_trace.restype = i
+        L.lu_trace_read.argtypes = [ctypes.POINTER(TraceEvent), i]
+        L.lu_trace_read.restype = i
         for f in ("lu_factor", "lu_solve", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
                   "lu_trailing_update", "lu_last_device_status"):
             getattr(L, f).restype = i
@@ -227,6 +232,24 @@ def lu_update_timing_read():
     _check("lu_update_timing_read", lib().lu_update_timing_read(ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
                                                                  ctypes.byref(by)))
     return n.value, ms.value, fl.value, by.value
+
+
+class TraceEvent(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("step", ctypes.c_int), ("stream", ctypes.c_int),
+                ("t_start_ms", ctypes.c_float), ("t_end_ms", ctypes.c_float)]
+
+
+def lu_trace(enable: bool) -> int:
+    return lib().lu_trace(int(bool(enable)))
+
+
+def lu_trace_read(max_events: int = 1 << 20):
+    """Recorded launches as dicts (kind name, step, stream, start/end ms), then cleared."""
+    buf = (TraceEvent * max_events)()
+    n = lib().lu_trace_read(buf, max_events)
+    _check("lu_trace_read", n if n < 0 else 0)
+    return [dict(kind=LU_TRACE_KINDS[e.kind], step=e.step, stream=e.stream, t0=e.t_start_ms, t1=e.t_end_ms)
+            for e in buf[:n]]
 
 
 def lu_kernel_launches() -> int:

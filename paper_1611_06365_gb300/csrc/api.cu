@@ -38,7 +38,7 @@ namespace lu {
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, __nv_bfloat16 *stage, int lds, int kpad, int split, int max_ctas,
-                               size_t smem_cap, cudaStream_t s);
+                               size_t smem_cap, int *status, long long bound_ns, cudaStream_t s);
 int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo);
 // swap_trsm.cu
 template <typename T>
@@ -69,7 +69,7 @@ cudaError_t launch_gather_rows(int n, int nrhs, const int *perm, const TI *B, in
 template <typename T>
 cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status, long long bound_ns,
                              int sms, cudaStream_t s);
-size_t trsv_workspace_ints(int n);
+size_t trsv_workspace_ints(int n, int nrhs);
 cudaError_t launch_iota(int *v, int n, cudaStream_t s);
 // batched.cu
 template <typename T>
@@ -183,6 +183,35 @@ bool timing_on() {
     std::lock_guard<std::mutex> lk(g_tmu);
     return g_timing;
 }
+
+// launch trace of the factorization schedule (lu_trace)
+struct TraceRec {
+    int kind, step, stream;
+    cudaEvent_t a, b;
+};
+bool g_trace_on = false;
+std::vector<TraceRec> g_trace;
+
+bool trace_on() {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    return g_trace_on;
+}
+
+// Runs launch() on stream s; when tracing, brackets it with two events.
+template <class F>
+cudaError_t traced(int kind, int step, int sid, cudaStream_t s, F launch) {
+    if (!trace_on()) return launch();
+    TraceRec r{kind, step, sid, nullptr, nullptr};
+    cudaError_t e;
+    if ((e = cudaEventCreate(&r.a)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&r.b)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(r.a, s)) != cudaSuccess) return e;
+    if ((e = launch()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(r.b, s)) != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_trace.push_back(r);
+    return cudaSuccess;
+}
 }  // namespace
 
 void lu_note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
@@ -209,6 +238,7 @@ namespace {
 struct Plan {
     int bo = 0;       // outer panel width
     int bi = 0;       // inner panel width (cluster capacity)
+    bool bi_auto = true;   // per panel: the widest inner width its row count allows
     bool tc = false;  // BF16 tensor-core update
     int nprod = 1;    // 1: BF16, 3: split BF16
     bool lookahead = true;
@@ -236,7 +266,8 @@ Plan make_plan(int n, const lu_opts *o) {
     const int wfit = std::max(1, panel_width_that_fits(std::max(n, 1), sizeof(T), kPanelSmemCap, 64, p.bo > 0 ? bo_fit : 0));
     if (p.bo == 0) p.bo = std::min(32, wfit);
     p.bo = std::min(p.bo, 256);
-    p.bi = (o && o->nb_inner > 0) ? std::min(o->nb_inner, wfit) : std::min(32, wfit);
+    p.bi_auto = !(o && o->nb_inner > 0);
+    p.bi = p.bi_auto ? wfit : std::min(o->nb_inner, wfit);
     p.bi = std::max(1, std::min(p.bi, p.bo));
     p.lookahead = !(o && o->lookahead < 0);
     p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : 16;
@@ -314,9 +345,12 @@ cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, in
 template <typename T>
 cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s) {
     __nv_bfloat16 *stage = (c.pl.tc && kb + w < c.n) ? c.stA[par] : nullptr;
-    return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, std::min(c.pl.bi, w), c.ipiv + kb, kb,
+    // the panel's rows shrink with k, so later panels hold wider inner panels
+    int bi = c.pl.bi;
+    if (c.pl.bi_auto) bi = std::max(bi, panel_width_that_fits(c.n - kb, sizeof(T), kPanelSmemCap, 64, w));
+    return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, std::min(bi, w), c.ipiv + kb, kb,
                                  c.info, c.maps[par], c.perm, stage, c.kinner, c.kpad, c.pl.nprod == 3, c.pl.panel_ctas,
-                                 kPanelSmemCap, s);
+                                 kPanelSmemCap, c.st->status, c.pl.bound, s);
 }
 
 template <typename T>
@@ -369,7 +403,7 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
 
     const int nblk = (n + bo - 1) / bo;
     // prologue: panel 0
-    LU_CUDA_TRY(factor_outer_panel<T>(c, 0, std::min(bo, n), 0, P));
+    LU_CUDA_TRY(traced(LU_TRACE_PANEL, 0, 0, P, [&] { return factor_outer_panel<T>(c, 0, std::min(bo, n), 0, P); }));
     LU_CUDA_TRY(cudaEventRecord(st->evP[0], P));
     for (int k = 0; k < nblk; ++k) {
         const int kb = k * bo, w = std::min(bo, n - kb), par = k & 1;
@@ -378,27 +412,29 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
         const int rest0 = pl.lookahead ? cn0 + wn : cn0;
         // ---- T_RU on U, first part: interchanges left of panel k, RU1 ------------
         LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evP[par], 0));
-        if (kb > 0) LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, 0, kb, 0, U));
-        if (rest0 < n) LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, rest0, n, 1, U));
+        if (kb > 0)
+            LU_CUDA_TRY(traced(LU_TRACE_SWAP_LEFT, k, 1, U, [&] { return swap_trsm<T>(c, kb, w, map, 0, kb, 0, U); }));
+        if (rest0 < n)
+            LU_CUDA_TRY(traced(LU_TRACE_RU1, k, 1, U, [&] { return swap_trsm<T>(c, kb, w, map, rest0, n, 1, U); }));
         // ---- T_PF on P: PF1, PF2 on strip k+1, then PF3 = panel k+1 ------------------
         if (wn > 0 && pl.lookahead) {
             if (k > 0) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par ^ 1], 0));
-            LU_CUDA_TRY(swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P));
-            LU_CUDA_TRY(update<T>(c, par, kb, w, cn0, cn0 + wn, P));
+            LU_CUDA_TRY(traced(LU_TRACE_PF1, k, 0, P, [&] { return swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P); }));
+            LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P, [&] { return update<T>(c, par, kb, w, cn0, cn0 + wn, P); }));
             // RU2 starts after PF2: when both become ready the panel (higher
             // priority) is dispatched first, and RU2's queued CTAs fill the
             // rest of the GPU and later the SMs the panel cluster frees
             LU_CUDA_TRY(cudaEventRecord(st->evPF2, P));
-            LU_CUDA_TRY(factor_outer_panel<T>(c, cn0, wn, par ^ 1, P));
+            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P, [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P); }));
             LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
             LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evPF2, 0));
         }
         // ---- T_RU on U, second part: RU2 ----------------------------------------------
-        if (rest0 < n) LU_CUDA_TRY(update<T>(c, par, kb, w, rest0, n, U));
+        if (rest0 < n) LU_CUDA_TRY(traced(LU_TRACE_RU2, k, 1, U, [&] { return update<T>(c, par, kb, w, rest0, n, U); }));
         LU_CUDA_TRY(cudaEventRecord(st->evU[par], U));
         if (wn > 0 && !pl.lookahead) {
             LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par], 0));
-            LU_CUDA_TRY(factor_outer_panel<T>(c, cn0, wn, par ^ 1, P));
+            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P, [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P); }));
             LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
         }
     }
@@ -426,7 +462,7 @@ int solve_impl(int n, int nrhs, const T *LU, int lda, const int *ipiv, const int
     LU_CUDA_TRY(ws.get(&X, (size_t)n * nrhs));
     LU_CUDA_TRY((launch_gather_rows<T, T>(n, nrhs, perm, B, ldb, X, n, s)));
     int *tws = nullptr;
-    LU_CUDA_TRY(ws.get(&tws, trsv_workspace_ints(n)));
+    LU_CUDA_TRY(ws.get(&tws, trsv_workspace_ints(n, nrhs)));
     LU_CUDA_TRY(launch_trsv_pair<T>(LU, lda, n, nrhs, X, n, tws, st->status, bound, st->sms, s));
     LU_CUDA_TRY(cudaMemcpy2DAsync(B, sizeof(T) * ldb, X, sizeof(T) * n, sizeof(T) * n, nrhs, cudaMemcpyDeviceToDevice, s));
     return LU_OK;
@@ -572,7 +608,7 @@ size_t lu_workspace_size(const char *routine, int n, int nrhs, lu_dtype dt) {
     if (!routine || n < 0 || nrhs < 0) return 0;
     const size_t N = (size_t)n, elem = dt == LU_F64 ? 8 : 4;
     if (!strcmp(routine, "factor")) return 3 * (1 + 4 * 256) * sizeof(int) + (dt == LU_F32 ? 3 * N * 512 * 2 : 0);
-    if (!strcmp(routine, "solve")) return N * sizeof(int) + N * nrhs * elem + trsv_workspace_ints(n) * sizeof(int);
+    if (!strcmp(routine, "solve")) return N * sizeof(int) + N * nrhs * elem + trsv_workspace_ints(n, nrhs) * sizeof(int);
     if (!strcmp(routine, "mixed"))
         return N * N * 4 + N * sizeof(int) * 2 + 3 * N * 512 * 2 + residual_workspace_doubles(n, nrhs) * 8 +
                N * nrhs * (8 * 2 + 4 * 2) + N * 8;
@@ -634,6 +670,46 @@ int lu_update_timing_read(long long *launches, double *total_ms, double *flops, 
     if (flops) *flops = fl;
     if (bytes) *bytes = by;
     return rc;
+}
+
+int lu_trace(int enable) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_trace_on = enable != 0;
+    return LU_OK;
+}
+
+int lu_trace_read(lu_trace_event *out, int max_events) {
+    std::vector<TraceRec> v;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        v.swap(g_trace);
+    }
+    int rc = LU_OK;
+    for (auto &t : v)
+        if (cudaEventSynchronize(t.b) != cudaSuccess) rc = LU_ERR_CUDA;
+    int nout = 0;
+    if (rc == LU_OK && !v.empty()) {
+        // origin: the earliest start event
+        size_t o = 0;
+        for (size_t i = 1; i < v.size(); ++i) {
+            float d = 0.f;
+            if (cudaEventElapsedTime(&d, v[o].a, v[i].a) == cudaSuccess && d < 0.f) o = i;
+        }
+        for (size_t i = 0; i < v.size() && out && nout < max_events; ++i) {
+            float t0 = 0.f, t1 = 0.f;
+            if (cudaEventElapsedTime(&t0, v[o].a, v[i].a) != cudaSuccess ||
+                cudaEventElapsedTime(&t1, v[o].a, v[i].b) != cudaSuccess) {
+                rc = LU_ERR_CUDA;
+                break;
+            }
+            out[nout++] = lu_trace_event{v[i].kind, v[i].step, v[i].stream, t0, t1};
+        }
+    }
+    for (auto &t : v) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    return rc == LU_OK ? (out ? nout : (int)v.size()) : rc;
 }
 
 long long lu_kernel_launches(void) { return g_launches.load(); }

@@ -2,31 +2,41 @@
 //
 // One launch factors a whole outer panel of b_o columns (section 3.1,
 // Figure 1; the outer/inner split of section 4.2, Figure 6).  The panel's m
-// rows are split over the C <= 16 CTAs of a cluster (R rows each).  The inner
-// panel of b_i columns lives in shared memory; per column j:
+// rows are split over the C <= 16 CTAs of a cluster (R rows each), and each
+// thread keeps its rows of the current inner panel (b_i <= BI columns) in
+// registers: a tile of RPT rows x BI columns (rows tid + 512 u).  Per column j:
 //
-//   1. every CTA reduces the (|a|, row) maximum of its rows (warp shuffles,
-//      then shared memory), and PUSHES the candidate (magnitude, row, the
-//      row's b_i values) into a slot of every CTA of the cluster with
-//      distributed-shared-memory stores; the CTA holding row j pushes row j;
-//   2. one hardware cluster barrier (release/acquire) per column;
-//   3. every CTA picks the winner locally (largest magnitude, smallest row on
-//      ties) and the two owners write the interchanged rows;
-//   4. every CTA scales its part of column j by IEEE division and applies the
-//      rank-1 update to its rows, tracking the candidate of column j+1.
+//   1. every warp finds its (|a|, row) maximum (integer keys: the bits of
+//      |a|, compared with warp reductions) and the lane holding it stages
+//      that row in shared memory; the thread holding row j stages row j;
+//   2. after one CTA barrier every warp knows the CTA's candidate, and all
+//      threads PUSH it (key, row index, values) and row j into slots of every
+//      CTA of the cluster with asynchronous 16-byte remote stores that count
+//      down the destination's transaction barrier (st.async + mbarrier);
+//   3. every thread waits on its own CTA's barrier for this column, which
+//      completes when all C candidates and row j have landed;
+//   4. every warp picks the winner from the slots in its own shared memory
+//      (largest magnitude, smallest row on ties); the thread holding row p
+//      takes the old row j, the thread holding row j takes the pivot row, and
+//      every thread scales its rows of column j by IEEE division and applies
+//      the rank-1 update in registers.  The column index is a compile-time
+//      constant in that update (one specialised code block per column), so the
+//      tile never leaves the register file.
 //
 // After each inner panel (when b_o > b_i), still inside the same launch:
 // its interchanges are applied to the panel's other columns (one row map,
 // gather then scatter), U12 := trilu(L11)^{-1} A12 is formed, and the inner
-// trailing update A22 -= L21 U12 runs on each CTA's own rows.  At the end the
-// kernel builds the row map of all b_o interchanges for the rest of the
-// matrix, updates the permutation vector, and, for the tensor-core update,
-// stages L21 as BF16 (optionally split hi/lo) in K-major order.
+// trailing update A22 -= L21 U12 runs on each thread's rows with L21 taken
+// from registers.  At the end the kernel builds the row map of all b_o
+// interchanges for the rest of the matrix, updates the permutation vector,
+// and, for the tensor-core update, stages L21 as BF16 (optionally split
+// hi/lo) in K-major order.
 //
-// Candidate and row-j slots are double-buffered by column parity, so one
-// cluster barrier per column suffices: a CTA writes slot (j+2) & 1 of a peer
-// only after passing barrier j+1, which the peer reaches after reading slot
-// j & 1.
+// Slots, staging rows and barriers are double-buffered by column parity: a CTA
+// pushes column j+2 only after its barrier for column j+1 completed, i.e.
+// after every peer pushed column j+1, which each peer does only after all of
+// its threads finished column j (a CTA barrier separates the two).  No
+// cluster-wide barrier is needed per column.
 #include "common.cuh"
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
@@ -37,55 +47,138 @@ namespace cg = cooperative_groups;
 namespace lu {
 
 constexpr int kPanelThreads = 512;
-constexpr int kPanelWMax = 64;       // inner panel width b_i
+constexpr int kPanelWarps = kPanelThreads / 32;
+constexpr int kPanelWMax = 64;       // widest inner panel b_i
 constexpr int kPanelBoMax = 256;     // outer panel width b_o
 constexpr int kPanelMaxCtas = 16;
-// end-of-panel scratch carved from As: row map (6 b_o ints) + probe table (2 x 4096 ints),
+constexpr int kPanelTileRegs = 64;   // 32-bit registers per thread for the row tile
+constexpr int kPanelMaxRpt = 8;      // rows per thread (R <= 4096)
+// end-of-panel scratch: row map (6 b_o ints) + probe table (2 x 4096 ints),
 // or the BF16 staging tile (32 rows x b_o floats)
 constexpr size_t kPanelScratch = sizeof(int) * (6 * kPanelBoMax + 8192);
 
+// Width BI of the register tile for RPT rows per thread.
+template <typename T, int RPT>
+struct TileWidth {
+    static constexpr int raw = kPanelTileRegs * 4 / (RPT * (int)sizeof(T));
+    static constexpr int BI = raw > kPanelWMax ? kPanelWMax : raw;
+};
+
 template <typename T>
 struct __align__(16) CandSlot {
-    T mag;
-    int row;
-    int pad[(16 - sizeof(T) - sizeof(int)) / sizeof(int)];   // vals start 16-byte aligned
+    unsigned long long key;   // magnitude key of the candidate (see mag_key)
+    int row;                  // panel row, INT_MAX: no candidate
+    int pad;                  // vals start 16-byte aligned
     T vals[kPanelWMax];
 };
 
 template <typename T>
 struct PanelShared {
-    CandSlot<T> cand[2][kPanelMaxCtas];   // pushed by every CTA (double-buffered)
-    __align__(16) T diag[2][kPanelWMax];  // row j, pushed by its owner
-    T urow[kPanelWMax], drow[kPanelWMax];
-    T red_mag[32];
-    int red_idx[32];
-    int bc[4];
-    int piv[kPanelBoMax];                 // this panel's pivots (panel-local rows)
+    CandSlot<T> cand[2][kPanelMaxCtas];      // pushed by every CTA (double-buffered)
+    __align__(16) T diag[2][kPanelWMax];     // row j, pushed by its owner
+    __align__(16) T wst[2][kPanelWarps][kPanelWMax];   // each warp's candidate row
+    __align__(16) T jst[2][kPanelWMax];      // row j, staged by its owner
+    unsigned long long mbar[2];              // transaction barriers of the column exchange
+    unsigned long long red_key[2][kPanelWarps];
+    int red_idx[2][kPanelWarps];
+    int abort;                               // a wait ran out of time
+    int piv[kPanelBoMax];                    // this panel's pivots (panel-local rows)
     int map_rows[2 * kPanelWMax], map_src[2 * kPanelWMax];
     int map_cnt;
     int cnt_s;
-    int first_zero;                       // first column with a zero pivot (-1: none)
+    int first_zero;                          // first column with a zero pivot (-1: none)
 };
 
-template <typename T>
-__device__ __forceinline__ void warp_argmax(T &mag, int &idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        T m2 = __shfl_xor_sync(0xffffffffu, mag, o);
-        int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (lu_better(m2, i2, mag, idx)) { mag = m2; idx = i2; }
+// Magnitude key of x: the bits of |x| as an unsigned integer, which orders
+// non-negative IEEE values like the values themselves; NaN gets no key
+// (the row is not a candidate: NaN never wins a comparison).
+__device__ __forceinline__ bool mag_key(float x, unsigned long long &k) {
+    const unsigned b = __float_as_uint(x) & 0x7fffffffu;
+    k = b;
+    return b <= 0x7f800000u;
+}
+__device__ __forceinline__ bool mag_key(double x, unsigned long long &k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    k = b;
+    return b <= 0x7ff0000000000000ULL;
+}
+__device__ __forceinline__ bool key_better(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+// Warp-wide (key, row) maximum, smallest row on ties; every lane gets the
+// result.  No candidate: key 0, row INT_MAX (loses to any real row).
+__device__ __forceinline__ void warp_argmax_key(unsigned long long &key, int &idx) {
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    const unsigned mine = (hi == mh && lo == ml) ? (unsigned)idx : 0xffffffffu;
+    idx = (int)__reduce_min_sync(0xffffffffu, mine);
+    key = ((unsigned long long)mh << 32) | ml;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned peer_u32(unsigned a, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+// 16-byte asynchronous store into a peer's shared memory; its completion
+// counts 16 bytes down on the peer's transaction barrier.
+__device__ __forceinline__ void st_async16(unsigned peer_addr, int4 v, unsigned peer_mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(peer_addr),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(peer_mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(unsigned mb, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the barrier at mb.  After `bound_ns` of
+// globaltimer time it records LU_ERR_TIMEOUT, marks the CTA aborted (later
+// waits return at once) and returns: the kernel then runs to its end with
+// meaningless values but keeps every CTA's control flow, so no barrier hangs.
+__device__ __forceinline__ void mbar_wait_bounded(unsigned mb, unsigned parity, volatile int *abort, int *status,
+                                                  long long bound_ns) {
+    if (*abort) return;
+    unsigned spins = 0;
+    unsigned long long t0 = 0;
+    while (!mbar_try_wait(mb, parity)) {
+        if ((++spins & 63u) == 0u) {
+            const unsigned long long t = lu_globaltimer();
+            if (t0 == 0) {
+                t0 = t;
+            } else if ((long long)(t - t0) > bound_ns) {
+                *abort = 1;
+                if (status) atomicExch(status, (int)LU_ERR_TIMEOUT);
+                return;
+            }
+            if (*abort) return;
+        }
     }
 }
 
-static inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
-
-// Dynamic shared memory: PanelShared | As[bi][R] (column-major) | U12s[bo-1][bi+1] | gv[ceil(bo/C)][2 bi] | L11s[bi][bi]
+// Dynamic shared memory: PanelShared | scratch | U12s[bo-1][bi+1] | gv[ceil(bo/C)][2 bi] | L11s[bi][bi]
 template <typename T>
 struct PanelLayout {
-    size_t as_off, u12_off, gv_off, l11_off, total;
-    __host__ __device__ PanelLayout(int R, int bi, int bo, int C) {
-        as_off = (sizeof(PanelShared<T>) + 15) & ~(size_t)15;
-        u12_off = as_off + (((size_t)R * bi * sizeof(T) + 15) & ~(size_t)15);
+    size_t scratch_off, u12_off, gv_off, l11_off, total;
+    __host__ __device__ PanelLayout(int bi, int bo, int C) {
+        scratch_off = (sizeof(PanelShared<T>) + 15) & ~(size_t)15;
+        u12_off = scratch_off + ((kPanelScratch + 15) & ~(size_t)15);
         // an inner panel of width wi >= 1 leaves at most bo - 1 columns to its
         // right (A12) and bo - 1 other columns in all (a short inner panel, or a
         // panel with fewer rows than columns, leaves more than bo - bi)
@@ -121,21 +214,105 @@ __device__ int make_row_map(const int *p, int r0, int cnt, int *rows, int *src) 
     return n;
 }
 
-template <typename T>
+// 16-byte vector type for T
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+// Tile row uu (runtime, < RPT) into dst[0..BI) (16-byte aligned shared memory).
+template <typename T, int RPT, int BI>
+__device__ __forceinline__ void stage_tile_row(const T (&a)[RPT][BI], int uu, T *dst) {
+    using V = typename Vec16<T>::type;
+    constexpr int VEC = 16 / sizeof(T);
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        if (u != uu) continue;
+#pragma unroll
+        for (int q = 0; q < BI / VEC; ++q) {
+            T w[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) w[k] = a[u][q * VEC + k];
+            reinterpret_cast<V *>(dst)[q] = *reinterpret_cast<const V *>(w);
+        }
+    }
+}
+
+// Column step LJ (a compile-time constant) of the rank-1 update on this
+// thread's rows below row j: a(i, LJ) /= pv, a(i, c) -= a(i, LJ) u(c) for
+// c > LJ, and the candidate of column LJ + 1 (when LJ + 1 < wi).
+template <typename T, int RPT, int BI, int LJ>
+__device__ __forceinline__ void rank1_step(T (&a)[RPT][BI], const T *__restrict__ urow, T pv, bool zero, int tid, int r0,
+                                           int myR, int j, int wi, unsigned long long &best, int &bidx) {
+    using V = typename Vec16<T>::type;
+    constexpr int VEC = 16 / sizeof(T);
+    constexpr int Q0 = (LJ + 1) / VEC;   // first vector of urow holding a column > LJ
+    bool act[RPT];
+    T l[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int lr = tid + u * kPanelThreads;
+        act[u] = (lr < myR) && (r0 + lr > j) && !zero;
+        l[u] = T(0);
+        if (act[u]) {
+            l[u] = a[u][LJ] / pv;
+            a[u][LJ] = l[u];
+        }
+    }
+#pragma unroll
+    for (int q = Q0; q < BI / VEC; ++q) {
+        V vv = reinterpret_cast<const V *>(urow)[q];
+        const T *w = reinterpret_cast<const T *>(&vv);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            const int c = q * VEC + k;
+            if (c > LJ) {
+#pragma unroll
+                for (int u = 0; u < RPT; ++u)
+                    if (act[u]) a[u][c] = fma(-l[u], w[k], a[u][c]);
+            }
+        }
+    }
+    best = 0;
+    bidx = INT_MAX;
+    if constexpr (LJ + 1 < BI) {
+        if (LJ + 1 < wi) {
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) {
+                const int lr = tid + u * kPanelThreads, i = r0 + lr;
+                unsigned long long k;
+                if (lr < myR && i > j && mag_key(a[u][LJ + 1], k) && key_better(k, i, best, bidx)) { best = k; bidx = i; }
+            }
+        }
+    }
+}
+
+#define LU_PANEL_CASE(L)                                                                                   \
+    case (L):                                                                                              \
+        if constexpr ((L) < BI)                                                                            \
+            rank1_step<T, RPT, BI, ((L) < BI ? (L) : 0)>(a, urow, pv, zero, tid, r0, myR, j, wi, best, bidx); \
+        break;
+#define LU_PANEL_CASE4(L) LU_PANEL_CASE(L) LU_PANEL_CASE((L) + 1) LU_PANEL_CASE((L) + 2) LU_PANEL_CASE((L) + 3)
+#define LU_PANEL_CASE16(L) LU_PANEL_CASE4(L) LU_PANEL_CASE4((L) + 4) LU_PANEL_CASE4((L) + 8) LU_PANEL_CASE4((L) + 12)
+
+template <typename T, int RPT>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, int *__restrict__ ipiv, int row_base,
                      int *__restrict__ info, int *__restrict__ map_out, int *__restrict__ perm,
-                     __nv_bfloat16 *__restrict__ stage, int lds, int kpad, int split) {
+                     __nv_bfloat16 *__restrict__ stage, int lds, int kpad, int split, int *__restrict__ status,
+                     long long bound_ns) {
+    constexpr int BI = TileWidth<T, RPT>::BI;
+    using V = typename Vec16<T>::type;
+    constexpr int VEC = 16 / sizeof(T);
+    static_assert(BI % VEC == 0, "tile width must be a whole number of 16-byte vectors");
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = kPanelThreads / 32;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const PanelLayout<T> lay(R, bi, bo, C);
+    const PanelLayout<T> lay(bi, bo, C);
     PanelShared<T> &S = *reinterpret_cast<PanelShared<T> *>(smem_raw);
-    T *As = reinterpret_cast<T *>(smem_raw + lay.as_off);
+    unsigned char *scratch = smem_raw + lay.scratch_off;
     T *U12s = reinterpret_cast<T *>(smem_raw + lay.u12_off);
     T *gv = reinterpret_cast<T *>(smem_raw + lay.gv_off);
     T *L11s = reinterpret_cast<T *>(smem_raw + lay.l11_off);   // [wi][wi] column-major, inner transitions
@@ -143,120 +320,133 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     const int r0 = rank * R;
     const int myR = max(0, min(R, m - r0));
     const int kmax = min(m, bo);
-    if (tid == 0) S.first_zero = -1;
+    if (tid == 0) {
+        S.first_zero = -1;
+        S.abort = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cl.sync();   // every CTA has started and initialised its barriers before any remote store
+
+    T a[RPT][BI];   // rows r0 + tid + 512 u of the inner panel's columns
 
     for (int jb = 0; jb < kmax; jb += bi) {
         const int wi = min(bi, kmax - jb);
-        // (a) own rows of the inner columns into shared memory
-        for (int c = 0; c < wi; ++c)
-            for (int lr = tid; lr < myR; lr += kPanelThreads)
-                As[(size_t)c * R + lr] = P[(size_t)(r0 + lr) + (size_t)(jb + c) * lda];
-        __syncthreads();
-        T best = T(-1);
+        // (a) own rows at or below the inner panel into registers (coalesced down each column)
+        unsigned long long best = 0;
         int bidx = INT_MAX;
-        for (int lr = tid; lr < myR; lr += kPanelThreads) {
-            const int i = r0 + lr;
-            if (i < jb) continue;
-            T v = lu_abs(As[lr]);
-            if (lu_better(v, i, best, bidx)) { best = v; bidx = i; }
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int lr = tid + u * kPanelThreads, i = r0 + lr;
+            const bool ld = (lr < myR) && (i >= jb);
+#pragma unroll
+            for (int c = 0; c < BI; ++c) a[u][c] = (ld && c < wi) ? P[(size_t)i + (size_t)(jb + c) * lda] : T(0);
+            unsigned long long k;
+            if (ld && mag_key(a[u][0], k) && key_better(k, i, best, bidx)) { best = k; bidx = i; }
         }
-        // (b) column steps: one CTA barrier and one cluster barrier per column
-        constexpr int VEC = 16 / sizeof(T);          // values per 16-byte DSMEM store
+        // (b) column steps: one CTA barrier and one cluster exchange per column
+        const int nvec = (wi + VEC - 1) / VEC;
+        // bytes landing in each CTA per column: C headers and candidate rows, one row j
+        const unsigned xbytes = 16u * (unsigned)(C * (1 + nvec) + nvec);
         for (int lj = 0; lj < wi; ++lj) {
             const int j = jb + lj;
             const int par = j & 1;
-            warp_argmax(best, bidx);
-            if (lane == 0) { S.red_mag[warp] = best; S.red_idx[warp] = bidx; }
-            __syncthreads();   // also orders the previous step's updates before the reads below
-            // every warp reduces the warp candidates itself (no second barrier)
-            T cmag = lane < nwarps ? S.red_mag[lane] : T(-1);
-            int crow = lane < nwarps ? S.red_idx[lane] : INT_MAX;
-            warp_argmax(cmag, crow);
+            const unsigned mb = smem_u32(&S.mbar[par]);
+            if (tid == 0) mbar_arrive_expect(mb, xbytes);
+            warp_argmax_key(best, bidx);
+            // the lane holding the warp's candidate stages it; the owner of row j stages row j
+            if (bidx != INT_MAX && lane == ((bidx - r0) & 31))
+                stage_tile_row<T, RPT, BI>(a, (bidx - r0) / kPanelThreads, S.wst[par][warp]);
             const bool own_j = (j >= r0 && j < r0 + myR);
-            // push the candidate (and row j) into every CTA's slots, 16 bytes per store
-            const int nvec = (wi + VEC - 1) / VEC;
-            for (int e = tid; e < C * (nvec + 1); e += kPanelThreads) {
-                const int d = e / (nvec + 1), q = e % (nvec + 1);
-                CandSlot<T> *dst = cl.map_shared_rank(&S.cand[par][rank], d);
-                if (q == 0) {
-                    dst->mag = cmag;
-                    dst->row = crow;
-                } else if (crow != INT_MAX) {
-                    T v[VEC];
-#pragma unroll
-                    for (int u = 0; u < VEC; ++u) {
-                        const int c = (q - 1) * VEC + u;
-                        v[u] = c < wi ? As[(size_t)c * R + (crow - r0)] : T(0);
+            if (own_j && tid == (j - r0) % kPanelThreads)
+                stage_tile_row<T, RPT, BI>(a, (j - r0) / kPanelThreads, S.jst[par]);
+            if (lane == 0) { S.red_key[par][warp] = best; S.red_idx[par][warp] = bidx; }
+            __syncthreads();
+            // every warp reduces the warp candidates itself (no second barrier)
+            unsigned long long ckey = lane < kPanelWarps ? S.red_key[par][lane] : 0ULL;
+            int crow = lane < kPanelWarps ? S.red_idx[par][lane] : INT_MAX;
+            warp_argmax_key(ckey, crow);
+            // push header, candidate row and row j into every CTA, 16 bytes per store
+            {
+                const int ndiag = own_j ? nvec : 0;
+                const int per = 1 + nvec + ndiag;
+                const int4 *crow_src = reinterpret_cast<const int4 *>(
+                    S.wst[par][crow != INT_MAX ? ((crow - r0) >> 5) & (kPanelWarps - 1) : 0]);
+                const unsigned slot = smem_u32(&S.cand[par][rank]);
+                const unsigned dslot = smem_u32(S.diag[par]);
+                for (int e = tid; e < C * per; e += kPanelThreads) {
+                    const int d = e / per, q = e % per;
+                    int4 v;
+                    unsigned addr;
+                    if (q == 0) {
+                        v = make_int4((int)(unsigned)ckey, (int)(unsigned)(ckey >> 32), crow, 0);
+                        addr = slot;
+                    } else if (q <= nvec) {
+                        v = crow_src[q - 1];
+                        addr = slot + 16u * (unsigned)q;
+                    } else {
+                        v = reinterpret_cast<const int4 *>(S.jst[par])[q - 1 - nvec];
+                        addr = dslot + 16u * (unsigned)(q - 1 - nvec);
                     }
-                    *reinterpret_cast<float4 *>(&dst->vals[(q - 1) * VEC]) = *reinterpret_cast<float4 *>(v);
+                    st_async16(peer_u32(addr, d), v, peer_u32(mb, d));
                 }
             }
-            if (own_j)
-                for (int e = tid; e < C * nvec; e += kPanelThreads) {
-                    const int d = e / nvec, q = e % nvec;
-                    T v[VEC];
-#pragma unroll
-                    for (int u = 0; u < VEC; ++u) {
-                        const int c = q * VEC + u;
-                        v[u] = c < wi ? As[(size_t)c * R + (j - r0)] : T(0);
-                    }
-                    T *dst = cl.map_shared_rank(&S.diag[par][0], d);
-                    *reinterpret_cast<float4 *>(&dst[q * VEC]) = *reinterpret_cast<float4 *>(v);
-                }
-            cl.sync();
+            mbar_wait_bounded(mb, (unsigned)(j >> 1) & 1u, &S.abort, status, bound_ns);
             // winner from the local copies, reduced by every warp (no barrier)
-            T mg = lane < C ? S.cand[par][lane].mag : T(-1);
+            unsigned long long wk = lane < C ? S.cand[par][lane].key : 0ULL;
             int ix = lane < C ? S.cand[par][lane].row : INT_MAX;
-            int src = lane;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                T m2 = __shfl_xor_sync(0xffffffffu, mg, o);
-                int i2 = __shfl_xor_sync(0xffffffffu, ix, o);
-                int s2 = __shfl_xor_sync(0xffffffffu, src, o);
-                if (lu_better(m2, i2, mg, ix)) { mg = m2; ix = i2; src = s2; }
-            }
+            const int mine = ix;
+            warp_argmax_key(wk, ix);
             const bool valid = (ix != INT_MAX);
+            const int src = valid ? __ffs(__ballot_sync(0xffffffffu, mine == ix)) - 1 : 0;
             const int p = valid ? ix : j;   // every candidate NaN: keep row j, as a sequential scan would
             const T *urow = valid ? S.cand[par][src].vals : S.diag[par];
             const T *drow = S.diag[par];    // old row j, the new content of row p
             const T pv = urow[lj];
             const bool zero = (pv == T(0));
-            const int pfinal = zero ? j : p;
             if (tid == 0) {
-                S.piv[j] = pfinal;
+                S.piv[j] = zero ? j : p;
                 if (zero && S.first_zero < 0) S.first_zero = j;
             }
-            // row j becomes the pivot row (nobody reads it again in this panel step)
-            if (!zero && p != j && own_j && tid < wi) As[(size_t)tid * R + (j - r0)] = urow[tid];
-            best = T(-1);
-            bidx = INT_MAX;
-            const bool has_next = (lj + 1 < wi);
-            for (int lr = tid; lr < myR; lr += kPanelThreads) {
-                const int i = r0 + lr;
-                if (i <= j) continue;
-                if (!zero) {
-                    // row p takes the old row j before its own update
-                    const bool swapped = (i == p && p != j);
-                    if (swapped)   // the factored columns of row p are row j's as well
-                        for (int c = 0; c < lj; ++c) As[(size_t)c * R + lr] = drow[c];
-                    const T l = (swapped ? drow[lj] : As[(size_t)lj * R + lr]) / pv;
-                    As[(size_t)lj * R + lr] = l;
-                    for (int c = lj + 1; c < wi; ++c) {
-                        T *a = &As[(size_t)c * R + lr];
-                        *a = fma(-l, urow[c], swapped ? drow[c] : *a);
+            // the interchange: row j takes the pivot row, row p the old row j
+            // (whole rows of the inner panel, factored columns included)
+            if (!zero && p != j) {
+#pragma unroll
+                for (int u = 0; u < RPT; ++u) {
+                    const int lr = tid + u * kPanelThreads;
+                    if (lr >= myR) continue;
+                    const int i = r0 + lr;
+                    if (i == j || i == p) {
+                        const V *s = reinterpret_cast<const V *>(i == j ? urow : drow);
+#pragma unroll
+                        for (int q = 0; q < BI / VEC; ++q) {
+                            V vv = s[q];
+                            const T *w = reinterpret_cast<const T *>(&vv);
+#pragma unroll
+                            for (int k = 0; k < VEC; ++k) a[u][q * VEC + k] = w[k];
+                        }
                     }
                 }
-                if (has_next) {
-                    T v = lu_abs(As[(size_t)(lj + 1) * R + lr]);
-                    if (lu_better(v, i, best, bidx)) { best = v; bidx = i; }
-                }
+            }
+            // scaling and rank-1 update with the column index as a constant
+            switch (lj) {
+                LU_PANEL_CASE16(0)
+                LU_PANEL_CASE16(16)
+                LU_PANEL_CASE16(32)
+                LU_PANEL_CASE16(48)
+                default: break;
             }
         }
-        __syncthreads();
-        // (c) the factored inner panel back to global memory
-        for (int c = 0; c < wi; ++c)
-            for (int lr = tid; lr < myR; lr += kPanelThreads)
-                P[(size_t)(r0 + lr) + (size_t)(jb + c) * lda] = As[(size_t)c * R + lr];
+        // (c) the factored inner panel back to global memory (rows at or below jb)
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int lr = tid + u * kPanelThreads, i = r0 + lr;
+            if (lr >= myR || i < jb) continue;
+#pragma unroll
+            for (int c = 0; c < BI; ++c)
+                if (c < wi) P[(size_t)i + (size_t)(jb + c) * lda] = a[u][c];
+        }
         if (wi >= bo) break;   // the panel is a single inner panel
         cl.sync();
         // (d) the inner interchanges on the panel's other columns, split over the cluster by columns
@@ -306,46 +496,29 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                     const int r = e % wi, c = e / wi;
                     P[(size_t)(jb + r) + (size_t)(c_right + c) * lda] = U12s[(size_t)c * (wi + 1) + r];
                 }
-            // (f) inner update of this CTA's rows below the inner panel: A22 -= L21 U12,
-            // 4 rows x 4 columns per thread (rows r0 + lr, lr = rq + 32 * u)
-            {
-                const int lo = max(0, c_right - r0);          // first own row below the inner panel
-                const int nrow = myR - lo;
-                const int rgroups = (nrow + 127) / 128, cgroups = (nr + 3) / 4;
-                for (int g = tid; g < rgroups * 32 * cgroups; g += kPanelThreads) {
-                    const int rq = g % 32, rest = g / 32;
-                    const int rb = rest % rgroups, cb = rest / rgroups;
-                    const int lr0 = lo + rb * 128 + rq, c0 = cb * 4;
-                    T acc[4][4];
+            // (f) inner update of this thread's rows below the inner panel,
+            // A22 -= L21 U12, with L21 from registers (4 columns at a time)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < RPT; ++u) {
+                const int lr = tid + u * kPanelThreads, i = r0 + lr;
+                if (lr >= myR || i < c_right) continue;
+                T *row = P + (size_t)i + (size_t)c_right * lda;
+                for (int c = 0; c < nr; c += 4) {
+                    T acc[4] = {T(0), T(0), T(0), T(0)};
+                    T old[4];
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-                    for (int kk = 0; kk < wi; ++kk) {
-                        T a[4], bq[4];
+                    for (int v = 0; v < 4; ++v) old[v] = c + v < nr ? row[(size_t)(c + v) * lda] : T(0);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int lr = lr0 + 32 * u;
-                            a[u] = lr < myR ? As[(size_t)kk * R + lr] : T(0);
-                        }
+                    for (int kk = 0; kk < BI; ++kk) {
+                        if (kk < wi) {
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) bq[v] = c0 + v < nr ? U12s[(size_t)(c0 + v) * (wi + 1) + kk] : T(0);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bq[v], acc[u][v]);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int lr = lr0 + 32 * u;
-                        if (lr >= myR) continue;
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            if (c0 + v >= nr) continue;
-                            T *a = &P[(size_t)(r0 + lr) + (size_t)(c_right + c0 + v) * lda];
-                            *a = *a - acc[u][v];
+                            for (int v = 0; v < 4; ++v)
+                                if (c + v < nr) acc[v] = fma(a[u][kk], U12s[(size_t)(c + v) * (wi + 1) + kk], acc[v]);
                         }
                     }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (c + v < nr) row[(size_t)(c + v) * lda] = old[v] - acc[v];
                 }
             }
         }
@@ -361,7 +534,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     // row map of all the panel's interchanges, for the rest of the matrix:
     // [0] count, [1 .. 1+2bo) rows, [1+2bo .. 1+4bo) src (matrix rows)
     if (rank == 0 && map_out) {
-        int *rows = reinterpret_cast<int *>(As);
+        int *rows = reinterpret_cast<int *>(scratch);
         int *src = rows + 2 * kPanelBoMax;
         int *old = src + 2 * kPanelBoMax;
         int *keys = old + 2 * kPanelBoMax;
@@ -404,7 +577,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     }
     // BF16 staging of L21 (panel rows kmax.. become stage rows 0..), K-major
     if (stage) {
-        float *tile = reinterpret_cast<float *>(As);   // 32 rows x kPanelBoMax, reused
+        float *tile = reinterpret_cast<float *>(scratch);   // 32 rows x kPanelBoMax, reused
         for (int rb = max(r0, kmax); rb < r0 + myR; rb += 32) {
             const int nrow = min(32, r0 + myR - rb);
             __syncthreads();
@@ -426,24 +599,45 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     cl.sync();   // no CTA leaves while a peer may still address its shared memory
 }
 
-// Rows per CTA and cluster size for an m-row panel (inner width bi, outer bo).
+// Rows per thread for a CTA of R rows (a power of two).
+static int rows_per_thread(int R) {
+    int r = 1;
+    while (r * kPanelThreads < R) r *= 2;
+    return r;
+}
+
+template <typename T>
+static int tile_width(int rpt) {
+    switch (rpt) {
+        case 1: return TileWidth<T, 1>::BI;
+        case 2: return TileWidth<T, 2>::BI;
+        case 4: return TileWidth<T, 4>::BI;
+        case 8: return TileWidth<T, 8>::BI;
+        default: return 0;
+    }
+}
+
+// Cluster size C and rows per CTA R for an m-row panel of inner width bi:
+// as many CTAs as allowed while each keeps >= 64 rows, more when the
+// register tile cannot hold R rows at width bi.
 template <typename T>
 static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap, int *C_out, int *R_out, size_t *smem_out) {
     auto rows_for = [&](int c) {
-        int r = (m + c - 1) / c;
-        r = (r + 31) & ~31;
-        // the end-of-panel scratch (row map and probe table, or the BF16 tile) reuses As
-        const int rmin = (int)((kPanelScratch / (bi * sizeof(T)) + 31) & ~(size_t)31);
-        return r > rmin ? r : rmin;
+        const int r = (m + c - 1) / c;
+        return (r + 31) & ~31;
+    };
+    auto fits = [&](int c) {
+        const int rpt = rows_per_thread(rows_for(c));
+        return rpt <= kPanelMaxRpt && tile_width<T>(rpt) >= bi;
     };
     if (max_ctas < 1 || max_ctas > kPanelMaxCtas) max_ctas = kPanelMaxCtas;
     int C = 1;
-    // as many CTAs as allowed while each keeps >= 64 rows: the rank-1 updates are the bulk
     while (C < kPanelMaxCtas && C < max_ctas && (m + 2 * C - 1) / (2 * C) >= 64) C *= 2;
-    while (C < kPanelMaxCtas && PanelLayout<T>(rows_for(C), bi, bo, C).total > smem_cap) C *= 2;
+    while (C < kPanelMaxCtas && !fits(C)) C *= 2;
+    if (!fits(C)) return false;
     const int R = rows_for(C);
     while (C > 1 && (long long)(C - 1) * R >= m) --C;
-    const PanelLayout<T> lay(R, bi, bo, C);
+    const PanelLayout<T> lay(bi, bo, C);
     if (lay.total > smem_cap) return false;
     *C_out = C;
     *R_out = R;
@@ -451,24 +645,35 @@ static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap,
     return true;
 }
 
+template <typename T, int RPT>
+static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int bo, int bi, int R, int *ipiv,
+                              int row_base, int *info, int *map_out, int *perm, __nv_bfloat16 *stage, int lds, int kpad,
+                              int split, int *status, long long bound_ns) {
+    cudaError_t e = cudaFuncSetAttribute(panel_factor_cluster<T, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cfg.dynamicSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(panel_factor_cluster<T, RPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    lu_count_launch();
+    return cudaLaunchKernelEx(&cfg, panel_factor_cluster<T, RPT>, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out,
+                              perm, stage, lds, kpad, split, status, bound_ns);
+}
+
 // Host launcher: factor the m x bo panel at P with inner width bi; pivots into
 // ipiv[0..min(m,bo)) as row_base + local + 1; row map into map_out (may be
 // NULL); permutation vector update (may be NULL); optional BF16 staging of
-// L21 (stage rows 0.. = panel rows bo..; lds, kpad, split).
+// L21 (stage rows 0.. = panel rows bo..; lds, kpad, split).  A column
+// exchange that waits longer than bound_ns records LU_ERR_TIMEOUT in *status.
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, __nv_bfloat16 *stage, int lds, int kpad, int split, int max_ctas,
-                               size_t smem_cap, cudaStream_t s) {
+                               size_t smem_cap, int *status, long long bound_ns, cudaStream_t s) {
     if (bi <= 0 || bo <= 0 || bo > kPanelBoMax || m <= 0) return cudaErrorInvalidValue;
     if (bi > bo) bi = bo;
     if (bi > kPanelWMax) return cudaErrorInvalidValue;
     int C = 1, R = 0;
     size_t smem = 0;
     if (!panel_geometry<T>(m, bi, bo, max_ctas, smem_cap, &C, &R, &smem)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(panel_factor_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(panel_factor_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(kPanelThreads, 1, 1);
@@ -481,9 +686,17 @@ cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    lu_count_launch();
-    return cudaLaunchKernelEx(&cfg, panel_factor_cluster<T>, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm,
-                              stage, lds, kpad, split);
+    switch (rows_per_thread(R)) {
+        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
+                                          status, bound_ns);
+        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
+                                          status, bound_ns);
+        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
+                                          status, bound_ns);
+        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
+                                          status, bound_ns);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 // Largest inner width (power of two, <= cap) for which an m-row panel of outer
@@ -501,8 +714,8 @@ int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo) 
 }
 
 template cudaError_t launch_panel_outer<double>(double *, int, int, int, int, int *, int, int *, int *, int *,
-                                                __nv_bfloat16 *, int, int, int, int, size_t, cudaStream_t);
+                                                __nv_bfloat16 *, int, int, int, int, size_t, int *, long long, cudaStream_t);
 template cudaError_t launch_panel_outer<float>(float *, int, int, int, int, int *, int, int *, int *, int *,
-                                               __nv_bfloat16 *, int, int, int, int, size_t, cudaStream_t);
+                                               __nv_bfloat16 *, int, int, int, int, size_t, int *, long long, cudaStream_t);
 
 }  // namespace lu

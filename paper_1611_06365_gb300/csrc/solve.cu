@@ -8,10 +8,13 @@
 // * trsv_blocks: blocked substitution by row blocks of 64.  Warps take row
 //   blocks in order from an atomic ticket; the warp of block I accumulates the
 //   off-diagonal products of its rows as the solutions of earlier blocks are
-//   published (flag per block, release/acquire), then solves its diagonal
-//   block and publishes.  A warp only waits for blocks handed out before its
-//   own, which belong to warps already running, so the chain always advances;
-//   every wait is bounded and records LU_ERR_TIMEOUT on expiry.
+//   published, then solves its diagonal block and publishes.  A solution value
+//   is published as a tagged 64-bit word (32 value bits + a 32-bit pass tag,
+//   two words for a double), so a reader polls the data itself: a word is
+//   valid exactly when its tag matches, with no flag, fence or second load on
+//   the block-to-block chain.  A warp only waits for blocks handed out before
+//   its own, which belong to warps already running, so the chain always
+//   advances; every wait is bounded and records LU_ERR_TIMEOUT on expiry.
 #include "common.cuh"
 #include <algorithm>
 
@@ -20,7 +23,7 @@ namespace lu {
 constexpr int kTB = 64;           // row block
 constexpr int kMaxRhs = 16;       // right-hand sides per pass
 constexpr int kHash = 1024;
-constexpr int kFlagPad = 32;      // one flag per 128-byte line
+constexpr int kFlagPad = 32;      // one ticket per 128-byte line
 constexpr int kTWarps = 2;        // warps per CTA
 
 __global__ void ipiv_to_perm_kernel(const int *__restrict__ ipiv, int n, int *__restrict__ perm) {
@@ -71,21 +74,55 @@ __global__ void gather_rows_kernel(int n, int nrhs, const int *__restrict__ perm
     }
 }
 
+// Tagged words of the published solutions: word w of value v carries 32 bits
+// of v (low half first for a double) and the pass tag in its high half.
+template <typename T> struct TagWords { static constexpr int value = sizeof(T) / 4; };
+
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_word(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void put_tagged(unsigned long long *w, float v, unsigned tag) {
+    st_word(w, ((unsigned long long)tag << 32) | __float_as_uint(v));
+}
+__device__ __forceinline__ void put_tagged(unsigned long long *w, double v, unsigned tag) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    st_word(w, ((unsigned long long)tag << 32) | (b & 0xffffffffULL));
+    st_word(w + 1, ((unsigned long long)tag << 32) | (b >> 32));
+}
+// Reads value words; returns false while any word's tag differs.
+__device__ __forceinline__ bool get_tagged(const unsigned long long *w, unsigned tag, float &v) {
+    const unsigned long long a = ld_word(w);
+    v = __uint_as_float((unsigned)a);
+    return (unsigned)(a >> 32) == tag;
+}
+__device__ __forceinline__ bool get_tagged(const unsigned long long *w, unsigned tag, double &v) {
+    const unsigned long long a = ld_word(w), b = ld_word(w + 1);
+    v = __longlong_as_double((long long)((b << 32) | (a & 0xffffffffULL)));
+    return (unsigned)(a >> 32) == tag && (unsigned)(b >> 32) == tag;
+}
+
 // LOWER: unit lower forward substitution (blocks taken top-down);
 // !LOWER: upper backward substitution (blocks taken bottom-up).
 // One warp per 64-row block (two rows per lane), no CTA-wide barriers: a warp
-// takes its block from the ticket, stages its diagonal block and the
-// off-diagonal block of its last dependency in shared memory while earlier
-// blocks are still being solved, accumulates the products of the earlier
-// published blocks straight from global memory (32 columns of loads in
-// flight), and so keeps only a shared-memory product, the diagonal solve
-// (shuffles) and the publication on the block-to-block chain.  NQ is the
-// number of right-hand sides handled per pass (a compile-time bound, so the
-// per-lane arrays stay in registers).
+// takes its block from the ticket, loads its right-hand sides and stages its
+// diagonal block and the off-diagonal block of its last dependency in shared
+// memory while earlier blocks are still being solved, accumulates the products
+// of the earlier published blocks straight from global memory (32 columns of
+// loads in flight), and so keeps only a shared-memory product, the diagonal
+// solve (shuffles) and the publication on the block-to-block chain.  NQ is
+// the number of right-hand sides handled per pass (a compile-time bound, so
+// the per-lane arrays stay in registers).  W holds the tagged solution words,
+// row i of right-hand side q at W[(q * n + i) * TagWords].
 template <typename T, bool LOWER, int NQ>
 __global__ void __launch_bounds__(32 * kTWarps)
 trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ X, int ldx, int *__restrict__ ticket,
-            int *__restrict__ flags, int *__restrict__ status, long long bound_ns) {
+            unsigned long long *__restrict__ W, unsigned tag, int *__restrict__ status, long long bound_ns) {
+    constexpr int TW = TagWords<T>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T *Dg = reinterpret_cast<T *>(smem_raw) + (size_t)warp * 2 * kTB * kTB;   // diagonal block [c][r]
@@ -99,6 +136,13 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
         const int I = LOWER ? t : nblk - 1 - t;
         const int r0 = I * kTB, rows = min(kTB, n - r0);
         const bool has0 = lane < rows, has1 = lane + 32 < rows;
+        // right-hand sides of the block, loaded before any wait
+        T x0[NQ], x1[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            x0[q] = (q < nrhs && has0) ? X[(size_t)(r0 + lane) + (size_t)q * ldx] : T(0);
+            x1[q] = (q < nrhs && has1) ? X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] : T(0);
+        }
         const int ndep = LOWER ? I : nblk - 1 - I;
         const int Jlast = LOWER ? I - 1 : I + 1;
         const int clast = Jlast * kTB, ncl = ndep > 0 ? min(kTB, n - clast) : 0;
@@ -128,18 +172,37 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
         for (int s = 0; s < ndep; ++s) {
             const int J = LOWER ? s : nblk - 1 - s;
             const int c0 = J * kTB, cols = min(kTB, n - c0);
-            int w = 1;
-            if (lane == 0) w = lu_wait_flag(&flags[(size_t)J * kFlagPad], 1, status, bound_ns) ? 1 : 0;
-            w = __shfl_sync(0xffffffffu, w, 0);
-            if (!w) { ok = false; break; }
+            // poll the tagged solution words of block J
             T y0[NQ], y1[NQ];
+            {
+                unsigned long long t0 = 0;
+                unsigned spins = 0;
+                for (;;) {
+                    bool got = true;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                y0[q] = (q < nrhs && lane < cols) ? __ldcg(&X[(size_t)(c0 + lane) + (size_t)q * ldx]) : T(0);
-                y1[q] = (q < nrhs && lane + 32 < cols) ? __ldcg(&X[(size_t)(c0 + lane + 32) + (size_t)q * ldx]) : T(0);
+                    for (int q = 0; q < NQ; ++q) {
+                        y0[q] = T(0);
+                        y1[q] = T(0);
+                        if (q < nrhs && lane < cols)
+                            got &= get_tagged(W + ((size_t)q * n + c0 + lane) * TW, tag, y0[q]);
+                        if (q < nrhs && lane + 32 < cols)
+                            got &= get_tagged(W + ((size_t)q * n + c0 + lane + 32) * TW, tag, y1[q]);
+                    }
+                    if (__all_sync(0xffffffffu, got)) break;
+                    __nanosleep(spins < 16 ? 20 : 100);
+                    if ((++spins & 15u) == 0u) {
+                        const unsigned long long now = lu_globaltimer();
+                        if (t0 == 0) t0 = now;
+                        // a warp-uniform decision: every lane leaves the loop together
+                        if (__any_sync(0xffffffffu, (long long)(now - t0) > bound_ns)) { ok = false; break; }
+                    }
+                }
+                if (!ok) {
+                    if (lane == 0) atomicExch(status, (int)LU_ERR_TIMEOUT);
+                    break;
+                }
             }
             if (J == Jlast) {
-                __syncwarp();
 #pragma unroll 8
                 for (int c = 0; c < cols; ++c) {
                     const T l0 = Lp[c * kTB + lane], l1 = Lp[c * kTB + lane + 32];
@@ -174,11 +237,10 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
         }
         if (!ok) return;
         // x = b + products, then the diagonal solve (two rows per lane)
-        T x0[NQ], x1[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            x0[q] = (q < nrhs && has0) ? X[(size_t)(r0 + lane) + (size_t)q * ldx] + acc0[q] : T(0);
-            x1[q] = (q < nrhs && has1) ? X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] + acc1[q] : T(0);
+            x0[q] += acc0[q];
+            x1[q] += acc1[q];
         }
         __syncwarp();
         if (LOWER) {
@@ -205,6 +267,14 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
                 }
             }
         }
+        // publish the tagged words first (the chain), then the plain result
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (q < nrhs) {
+                if (has0) put_tagged(W + ((size_t)q * n + r0 + lane) * TW, x0[q], tag);
+                if (has1) put_tagged(W + ((size_t)q * n + r0 + lane + 32) * TW, x1[q], tag);
+            }
+        }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             if (q < nrhs) {
@@ -212,9 +282,6 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
                 if (has1) X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] = x1[q];
             }
         }
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) lu_st_release(&flags[(size_t)I * kFlagPad], 1);
     }
 }
 
@@ -235,44 +302,53 @@ cudaError_t launch_gather_rows(int n, int nrhs, const int *perm, const TI *B, in
     return cudaGetLastError();
 }
 
-// two tickets, then two flag arrays with one flag per 128-byte line
-size_t trsv_workspace_ints(int n) { return (size_t)kFlagPad * (1 + 2 * ((n + kTB - 1) / kTB)); }
+// Two tickets (one 128-byte line each), then the tagged solution words: up
+// to kMaxRhs right-hand sides of n values, two 64-bit words per value (the
+// FP64 size; FP32 uses half).
+size_t trsv_workspace_ints(int n, int nrhs) {
+    const size_t q = (size_t)std::max(1, std::min(nrhs, kMaxRhs));
+    return (size_t)2 * kFlagPad + (size_t)4 * q * (size_t)std::max(n, 1);
+}
 
 template <typename T, int NQ>
-static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, int n, int nq, T *X, int ldx, int *ws, int nblk,
+static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, int n, int nq, T *X, int ldx, int *ws,
                                   int *status, long long bound_ns, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(trsv_blocks<T, true, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(trsv_blocks<T, false, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    trsv_blocks<T, true, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws, ws + kFlagPad, status, bound_ns);
+    unsigned long long *W = reinterpret_cast<unsigned long long *>(ws + 2 * kFlagPad);
+    // the forward pass publishes with tag 1, the backward pass with tag 2 over the
+    // same words: a backward reader never mistakes a forward value for its own
+    trsv_blocks<T, true, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws, W, 1u, status, bound_ns);
     lu_count_launch();
-    trsv_blocks<T, false, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws + 1,
-                                                               ws + kFlagPad + (size_t)nblk * kFlagPad, status, bound_ns);
+    trsv_blocks<T, false, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws + kFlagPad, W, 2u, status,
+                                                               bound_ns);
     lu_count_launch();
     return cudaGetLastError();
 }
 
-// Workspace: trsv_workspace_ints(n) ints, zeroed here before each pass.
+// Workspace: trsv_workspace_ints(n, nrhs) ints, zeroed here before each pass.
 template <typename T>
 cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status,
                              long long bound_ns, int sms, cudaStream_t s) {
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     const int nblk = (n + kTB - 1) / kTB;
-    const size_t wsn = trsv_workspace_ints(n);
     const int grid = std::min((nblk + kTWarps - 1) / kTWarps, 8 * sms);
     const size_t smem = sizeof(T) * (size_t)kTWarps * 2 * kTB * kTB;
     cudaError_t e = cudaSuccess;
     for (int q0 = 0; q0 < nrhs; q0 += kMaxRhs) {
         const int nq = std::min(kMaxRhs, nrhs - q0);
-        e = cudaMemsetAsync(ws, 0, sizeof(int) * wsn, s);
+        // tickets and the words of this pass's right-hand sides
+        const size_t used = (size_t)2 * kFlagPad + (size_t)2 * TagWords<T>::value * nq * n;
+        e = cudaMemsetAsync(ws, 0, sizeof(int) * used, s);
         if (e != cudaSuccess) return e;
         T *Xq = X + (size_t)q0 * ldx;
-        if (nq == 1) e = launch_trsv_nq<T, 1>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
-        else if (nq <= 2) e = launch_trsv_nq<T, 2>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
-        else if (nq <= 4) e = launch_trsv_nq<T, 4>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
-        else if (nq <= 8) e = launch_trsv_nq<T, 8>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
-        else e = launch_trsv_nq<T, 16>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, nblk, status, bound_ns, s);
+        if (nq == 1) e = launch_trsv_nq<T, 1>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
+        else if (nq <= 2) e = launch_trsv_nq<T, 2>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
+        else if (nq <= 4) e = launch_trsv_nq<T, 4>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
+        else if (nq <= 8) e = launch_trsv_nq<T, 8>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
+        else e = launch_trsv_nq<T, 16>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -31,7 +31,7 @@ cudaError_t launch_gather_rows(int n, int nrhs, const int *perm, const TI *B, in
 template <typename T>
 cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status, long long bound_ns,
                              int sms, cudaStream_t s);
-size_t trsv_workspace_ints(int n);
+size_t trsv_workspace_ints(int n, int nrhs);
 }  // namespace lu
 
 namespace {
@@ -49,7 +49,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Bytes of scratch a request needs: status word, flags of the blocked
 // substitution, permutation vector, permuted copy of B.
 size_t scratch_bytes(int n, int nrhs, size_t elem) {
-    return align256(sizeof(int)) + align256(lu::trsv_workspace_ints(n) * sizeof(int)) + align256((size_t)n * sizeof(int)) +
+    return align256(sizeof(int)) + align256(lu::trsv_workspace_ints(n, nrhs) * sizeof(int)) + align256((size_t)n * sizeof(int)) +
            align256((size_t)n * nrhs * elem);
 }
 
@@ -77,7 +77,7 @@ int solve_noalloc(int n, int nrhs, const T *LU, int lda, const int *ipiv, T *B, 
     int *status = reinterpret_cast<int *>(base);
     size_t off = align256(sizeof(int));
     int *tws = reinterpret_cast<int *>(base + off);
-    off += align256(lu::trsv_workspace_ints(n) * sizeof(int));
+    off += align256(lu::trsv_workspace_ints(n, nrhs) * sizeof(int));
     int *perm = reinterpret_cast<int *>(base + off);
     off += align256((size_t)n * sizeof(int));
     T *X = reinterpret_cast<T *>(base + off);

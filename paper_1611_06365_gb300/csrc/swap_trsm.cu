@@ -17,85 +17,149 @@ namespace lu {
 constexpr int kSwapThreads = 256;
 constexpr int kStrip = 32;          // columns per CTA
 constexpr int kVS = kStrip + 1;      // row stride of the strip buffer (bank-conflict padding)
-constexpr int kTrsmBlk = 32;        // diagonal block of the blocked TRSM
+constexpr int kBelowRows = 64;      // rows of L staged per pass of the off-diagonal update
+
+// Diagonal block of the blocked solve: 32 rows, one per lane.
+template <typename T> struct TrsmBlk { static constexpr int value = 32; };
 
 // map layout in global memory (written by the panel kernel): [0] = count,
 // [1 .. 1+2b) rows, [1+2b .. 1+4b) src
 
 template <typename T> __device__ __forceinline__ __nv_bfloat16 to_bf16(T v) { return __float2bfloat16_rn((float)v); }
 
+// Shared memory: rows/src [4b ints] | V [2b][kVS] | Ld [DB][DB + 1] (row-major) | Lc [kBelowRows][DB + 4]
+template <typename T>
+struct SwapLayout {
+    size_t v_off, ld_off, lc_off, total;
+    __host__ __device__ explicit SwapLayout(int b) {
+        constexpr int DB = TrsmBlk<T>::value;
+        v_off = (((size_t)4 * b * sizeof(int)) + 15) & ~(size_t)15;
+        ld_off = v_off + ((((size_t)2 * b * kVS * sizeof(T)) + 15) & ~(size_t)15);
+        lc_off = ld_off + (((size_t)DB * (DB + 1) * sizeof(T) + 15) & ~(size_t)15);
+        total = lc_off + (size_t)kBelowRows * (DB + 4) * sizeof(T) + 16;
+    }
+};
+
 // For the column strip [c_begin + kStrip*blockIdx.x, ... ) within [c_begin, c_end):
 //   apply the row map (all rows of S), then, if do_trsm, solve
 //   X := trilu(L11)^{-1} X for the b panel rows (L11 = A[kb:kb+b, kb:kb+b])
 //   and store X back (and, if stage != NULL, as BF16 into stage[(c - stage_c0)*ldst + r]).
+// The solve is blocked by DB = 32 rows.  In a diagonal block lane r of every
+// warp holds row r of L and of the warp's strip columns in registers; step k
+// broadcasts the finished x[k] with a shuffle and lanes r > k subtract
+// L[r][k] x[k] (every element takes its updates in increasing k, as in the
+// unblocked substitution).  Then all threads update the rows below,
+// X[r] -= L[r, blk] X[blk].
 template <typename T>
-__global__ void __launch_bounds__(kSwapThreads)
+__global__ void __launch_bounds__(kSwapThreads, 2)
 swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restrict__ map, int c_begin,
                  int c_end, int do_trsm, __nv_bfloat16 *__restrict__ stage, int ldst, int stage_c0,
                  int stage_k, int split) {
+    constexpr int DB = TrsmBlk<T>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SwapLayout<T> lay(b);
     const int cnt = map[0];
     int *rows = reinterpret_cast<int *>(smem_raw);              // [2b]
     int *src = rows + 2 * b;                                     // [2b]
-    T *V = reinterpret_cast<T *>(smem_raw + (((size_t)4 * b * sizeof(int) + 15) & ~(size_t)15));
-    // V: [2b][kVS], rows of S by strip column (X = first b rows)
-    T *Lblk = V + (size_t)2 * b * kVS;                          // [kTrsmBlk][b] column slab of L11
+    T *V = reinterpret_cast<T *>(smem_raw + lay.v_off);          // [2b][kVS], rows of S by strip column (X = first b rows)
+    T *Ld = reinterpret_cast<T *>(smem_raw + lay.ld_off);        // [DB][DB + 1] diagonal block of L11, row-major
+    T *Lc = reinterpret_cast<T *>(smem_raw + lay.lc_off);        // [kBelowRows][DB + 4] rows of L below the block
 
     const int c0 = c_begin + blockIdx.x * kStrip;
     const int ncol = min(kStrip, c_end - c0);
     if (ncol <= 0) return;
-    for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
+    const int tid = threadIdx.x;
+    for (int s = tid; s < cnt; s += blockDim.x) {
         rows[s] = map[1 + s];
         src[s] = map[1 + 2 * b + s];
     }
     __syncthreads();
     // gather old values (threads run down S for a fixed column: coalesced for the panel rows)
-    for (int e = threadIdx.x; e < cnt * ncol; e += blockDim.x) {
+    for (int e = tid; e < cnt * ncol; e += blockDim.x) {
         const int s = e % cnt, c = e / cnt;
         V[(size_t)s * kVS + c] = A[(size_t)src[s] + (size_t)(c0 + c) * lda];
     }
     __syncthreads();
     // scatter rows outside the panel (and, without a solve, the panel rows too)
     const int first = do_trsm ? b : 0;
-    for (int e = threadIdx.x; e < (cnt - first) * ncol; e += blockDim.x) {
+    for (int e = tid; e < (cnt - first) * ncol; e += blockDim.x) {
         const int s = first + e % (cnt - first), c = e / (cnt - first);
         A[(size_t)rows[s] + (size_t)(c0 + c) * lda] = V[(size_t)s * kVS + c];
     }
     if (!do_trsm) return;
 
-    // blocked forward substitution with unit lower L11 on X = V[0:b][0:ncol]
-    const int tc = threadIdx.x % kStrip, tg = threadIdx.x / kStrip, ng = kSwapThreads / kStrip;
-    for (int d0 = 0; d0 < b; d0 += kTrsmBlk) {
-        const int db = min(kTrsmBlk, b - d0);
-        // stage the column slab L11[d0:b, d0:d0+db] (rows d0..b-1)
-        __syncthreads();
-        const int slab_rows = b - d0;
-        for (int e = threadIdx.x; e < slab_rows * db; e += blockDim.x) {
-            const int r = e % slab_rows, c = e / slab_rows;
-            Lblk[(size_t)c * b + r] = A[(size_t)(kb + d0 + r) + (size_t)(kb + d0 + c) * lda];
+    const T *L11 = A + (size_t)kb + (size_t)kb * lda;
+    for (int d0 = 0; d0 < b; d0 += DB) {
+        const int db = min(DB, b - d0);
+        // diagonal block (strictly lower part; zero outside the block), row-major
+        for (int e = tid; e < DB * DB; e += blockDim.x) {
+            const int r = e % DB, k = e / DB;
+            Ld[(size_t)r * (DB + 1) + k] = (r > k && r < db && k < db) ? L11[(size_t)(d0 + r) + (size_t)(d0 + k) * lda] : T(0);
         }
-        // diagonal block: rows in parallel, one step per column of L
-        for (int jj = 0; jj < db; ++jj) {
-            __syncthreads();
-            if (tc < ncol) {
-                const T x = V[(size_t)(d0 + jj) * kVS + tc];
-                for (int ii = jj + 1 + tg; ii < db; ii += ng)
-                    V[(size_t)(d0 + ii) * kVS + tc] = fma(-Lblk[(size_t)jj * b + ii], x, V[(size_t)(d0 + ii) * kVS + tc]);
+        __syncthreads();
+        {
+            constexpr int CPW = kStrip / (kSwapThreads / 32);   // strip columns per warp
+            const int r = tid & 31, cw = (tid >> 5) * CPW;
+            T lrow[DB];
+#pragma unroll
+            for (int k = 0; k < DB; ++k) lrow[k] = Ld[(size_t)r * (DB + 1) + k];
+            T x[CPW];
+#pragma unroll
+            for (int u = 0; u < CPW; ++u) x[u] = (r < db && cw + u < ncol) ? V[(size_t)(d0 + r) * kVS + cw + u] : T(0);
+#pragma unroll
+            for (int k = 0; k < DB - 1; ++k) {
+#pragma unroll
+                for (int u = 0; u < CPW; ++u) {
+                    const T xk = __shfl_sync(0xffffffffu, x[u], k);
+                    if (r > k) x[u] = fma(-lrow[k], xk, x[u]);
+                }
             }
+#pragma unroll
+            for (int u = 0; u < CPW; ++u)
+                if (r < db && cw + u < ncol) V[(size_t)(d0 + r) * kVS + cw + u] = x[u];
         }
         __syncthreads();
-        // rows below the diagonal block: X[r] -= L[r, d0:d0+db] X[d0:d0+db]
-        const int below = b - d0 - db;
-        for (int e = threadIdx.x; e < below * ncol; e += blockDim.x) {
-            const int c = e % ncol, r = e / ncol;
-            T acc = V[(size_t)(d0 + db + r) * kVS + c];
-            for (int jj = 0; jj < db; ++jj)
-                acc = fma(-Lblk[(size_t)jj * b + db + r], V[(size_t)(d0 + jj) * kVS + c], acc);
-            V[(size_t)(d0 + db + r) * kVS + c] = acc;
+        // rows below the block: X[r] -= L[r, d0:d0+db] X[d0:d0+db], kBelowRows rows per pass
+        for (int rb = d0 + db; rb < b; rb += kBelowRows) {
+            const int nr = min(kBelowRows, b - rb);
+            for (int e = tid; e < kBelowRows * DB; e += blockDim.x) {
+                const int r = e % kBelowRows, k = e / kBelowRows;
+                Lc[(size_t)r * (DB + 4) + k] = (r < nr && k < db) ? L11[(size_t)(rb + r) + (size_t)(d0 + k) * lda] : T(0);
+            }
+            __syncthreads();
+            {
+                // thread: column c, rows rq + 8 i (i < 8); each element takes its
+                // updates in increasing k, as in the unblocked substitution
+                const int c = tid & 31, rq = tid >> 5;
+                T acc[kBelowRows / 8];
+#pragma unroll
+                for (int i = 0; i < kBelowRows / 8; ++i) {
+                    const int r = rq + 8 * i;
+                    acc[i] = (r < nr && c < ncol) ? V[(size_t)(rb + r) * kVS + c] : T(0);
+                }
+                for (int k = 0; k < db; k += 4) {
+                    T xv[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) xv[v] = (k + v < db) ? V[(size_t)(d0 + k + v) * kVS + c] : T(0);
+#pragma unroll
+                    for (int i = 0; i < kBelowRows / 8; ++i) {
+                        const T *lr = Lc + (size_t)(rq + 8 * i) * (DB + 4) + k;
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[i] = fma(-lr[v], xv[v], acc[i]);
+                    }
+                }
+                if (c < ncol) {
+#pragma unroll
+                    for (int i = 0; i < kBelowRows / 8; ++i) {
+                        const int r = rq + 8 * i;
+                        if (r < nr) V[(size_t)(rb + r) * kVS + c] = acc[i];
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < b * ncol; e += blockDim.x) {
+    for (int e = tid; e < b * ncol; e += blockDim.x) {
         const int r = e % b, c = e / b;
         const T x = V[(size_t)r * kVS + c];
         A[(size_t)(kb + r) + (size_t)(c0 + c) * lda] = x;
@@ -106,7 +170,7 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
         }
     }
     if (stage) {   // zero K padding (b < stage_k on a short last panel)
-        for (int e = threadIdx.x; e < (stage_k - b) * ncol; e += blockDim.x) {
+        for (int e = tid; e < (stage_k - b) * ncol; e += blockDim.x) {
             const int r = b + e % (stage_k - b), c = e / (stage_k - b);
             stage[(size_t)(c0 + c - stage_c0) * ldst + r] = __float2bfloat16_rn(0.f);
             if (split) stage[(size_t)(c0 + c - stage_c0) * ldst + stage_k + r] = __float2bfloat16_rn(0.f);
@@ -115,11 +179,7 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
 }
 
 size_t swap_trsm_smem_bytes(int b, size_t elem) {
-    size_t a = (size_t)4 * b * sizeof(int);
-    a = (a + 15) & ~(size_t)15;
-    a += (size_t)2 * b * kVS * elem;
-    a += (size_t)kTrsmBlk * b * elem;
-    return a + 16;
+    return elem == 8 ? SwapLayout<double>(b).total : SwapLayout<float>(b).total;
 }
 
 template <typename T>
