@@ -37,6 +37,9 @@ MIXED_KAPPA = 1e5
 MIXED_REFLECTORS = 256
 SM_COUNT = 152
 FP64_PEAK_TFLOPS = 2 * 2 * SM_COUNT * 2.07e9 / 1e12   # 2 DFMA (4 flop) / clk / SM at 2070 MHz = 1.259
+FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * 2.07e9 / 1e12  # 128 FFMA (256 flop) / clk / SM at 2070 MHz = 80.5
+BATCH_COUNT = 10000
+BATCH_SEED = 20161106 + 1000 * 4      # family 4 (batched LU)
 
 
 def flops_lu(n):
@@ -268,6 +271,9 @@ def run_ours(args):
     tts = None
     if not args.skip_mixed and rank == 0:
         tts = time_to_solution(args, dev)
+    batched = None
+    if not args.skip_batched and rank == 0:
+        batched = {dt: batched_case(dev, dt, args.steps) for dt in ("f64", "f32")}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -277,7 +283,7 @@ def run_ours(args):
                    "entries": "uniform [-1,1)", "l2": "inputs larger than L2 (2 GiB FP64 matrix per step)",
                    "parallelism": f"replicas x{ws}", "eta_fp64": eta},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "time_to_solution": tts,
+        "time_to_solution": tts, "batched": batched,
     }
     if rank == 0 and not args.skip_cpu:
         dt, threads = oracle_sample(args.cpu_n, SEED)
@@ -289,6 +295,95 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def batched_case(dev, dtype, steps):
+    """10 000 LUs + solves of orders uniform in [16, 256] (odd members diagonally
+    dominant), b = A * ones, one CUDA graph per step (restore, factor, solve)."""
+    import numpy as np
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    code = lu.LU_F64 if dtype == "f64" else lu.LU_F32
+    sizes = li.batch_sizes(BATCH_COUNT, 16, 256, seed=BATCH_SEED)
+    offs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
+    roffs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64))])
+    buf0 = torch.empty(int(offs[-1]), dtype=tdt, device=dev)
+    rhs0 = torch.empty(int(roffs[-1]), dtype=tdt, device=dev)
+    for t, n in enumerate(sizes):
+        n = int(n)
+        A = li.uniform_colmajor_torch(n, n, BATCH_SEED + 1 + t, dev, torch.float64)
+        if t % 2 == 1:
+            A.view(-1)[:: n + 1] += n
+        buf0[int(offs[t]):int(offs[t + 1])] = A.view(-1).to(tdt)
+        rhs0[int(roffs[t]):int(roffs[t + 1])] = (A.to(tdt).double().t() @ torch.ones(n, dtype=torch.float64,
+                                                                                       device=dev)).to(tdt)
+    buf, rhs = buf0.clone(), rhs0.clone()
+    esz = buf.element_size()
+    ns = torch.tensor(sizes, dtype=torch.int32, device=dev)
+    ptrA = torch.tensor([buf.data_ptr() + int(o) * esz for o in offs[:-1]], dtype=torch.int64, device=dev)
+    ipiv = torch.zeros(int(roffs[-1]), dtype=torch.int32, device=dev)
+    ptrP = torch.tensor([ipiv.data_ptr() + int(o) * 4 for o in roffs[:-1]], dtype=torch.int64, device=dev)
+    ptrB = torch.tensor([rhs.data_ptr() + int(o) * esz for o in roffs[:-1]], dtype=torch.int64, device=dev)
+    info = torch.zeros(BATCH_COUNT, dtype=torch.int32, device=dev)
+
+    def body():
+        buf.copy_(buf0)
+        rhs.copy_(rhs0)
+        lu.lu_factor_batched(code, ns, ptrA, ns, ptrP, info, 256)
+        lu.lu_solve_batched(code, 1, ns, ptrA, ns, ptrP, ptrB, ns, 256)
+
+    body()                                   # library state and workspace pools before capture
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        body()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        body()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    reps = max(3, steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / reps
+    # the restore copies alone, to separate them from the factor + solve time
+    e0.record()
+    for _ in range(reps):
+        buf.copy_(buf0)
+        rhs.copy_(rhs0)
+    e1.record()
+    torch.cuda.synchronize()
+    restore_ms = e0.elapsed_time(e1) / reps
+    g.replay()
+    torch.cuda.synchronize()
+    infos = info.cpu().numpy()
+    x = rhs.cpu().numpy().astype(np.float64)
+    err = float(np.max(np.abs(x - 1.0)))
+    # x = ones up to kappa * eps of each member (FP32: a loose sanity bound)
+    assert np.all(infos == 0) and err < (1e-6 if dtype == "f64" else 1.0), (dtype, err)
+    flops = float(np.sum(2.0 / 3.0 * sizes.astype(np.float64) ** 3 + 2.0 * sizes.astype(np.float64) ** 2))
+    lu_ms = step_ms - restore_ms
+    peak = FP64_PEAK_TFLOPS if dtype == "f64" else FP32_PEAK_TFLOPS
+    achieved = flops / (lu_ms / 1e3) / 1e12
+    return {"count": BATCH_COUNT, "n_range": [16, 256], "seed": BATCH_SEED, "graph": True,
+            "step_ms": step_ms, "restore_ms": restore_ms, "factor_solve_ms": lu_ms,
+            "gflops": flops / (lu_ms / 1e3) / 1e9, "max_abs_err_x_minus_1": err,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "peak_note": "derived: " + ("2 DFMA" if dtype == "f64" else "128 FFMA") +
+                                      "/clk/SM x 152 SMs x 2070 MHz"}}
 
 
 def time_to_solution(args, dev):
@@ -379,6 +474,7 @@ def main():
     ap.add_argument("--ref-n", dest="ref_n", type=int, default=2048)
     ap.add_argument("--skip-mixed", dest="skip_mixed", action="store_true")
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
+    ap.add_argument("--skip-batched", dest="skip_batched", action="store_true")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor"], default=None,
                     help="run one profiling case instead of the benchmark")
     args = ap.parse_args()

@@ -127,23 +127,32 @@ size_t lu_solve_noalloc_capacity(void);
 
 /*
  * lu_factor_batched -- lu_factor applied to `batch` independent matrices of
- * possibly different orders in ONE launch (one CTA per matrix).
+ * possibly different orders in ONE factorization launch.
  *   d_n    device int[batch], orders (0 <= n_t <= max_n).
  *   d_A    device array of device pointers, matrix t in column-major.
  *   d_lda  device int[batch] (lda_t >= max(1, n_t)).
  *   d_ipiv device array of device int* (n_t entries each).
  *   d_info device int[batch].
  *   max_n  host int, >= every n_t; at most 1024.
- *   Each matrix is factored with the unblocked right-looking algorithm of
- *   section 3.1 (Figure 1, left) with partial pivoting.
+ *   opts   NULL or opts->nb: 0 = automatic; 16 or 32 = the blocked kernel
+ *          with that panel width (max_n <= 256; section 3.1, Figure 1 right:
+ *          persistent CTAs take matrices largest first from a queue, panel
+ *          rows in registers, U12 solve and trailing update on chip);
+ *          1 = the unblocked kernel (Figure 1 left, one CTA per matrix, the
+ *          only one for max_n > 256).  Other values return -9.  Both kernels
+ *          apply the same fused multiply-adds in the same order to every
+ *          element, so their factors and pivots are identical.
+ *   The blocked kernel allocates a small stream-ordered workspace (the queue
+ *   and the size order, 4 (batch + 32) bytes).
  */
 int lu_factor_batched(lu_dtype dt, int batch, const int *d_n, void *const *d_A, const int *d_lda,
                       int *const *d_ipiv, int *d_info, int max_n, const lu_opts *opts, void *stream);
 
 /*
- * lu_solve_batched -- lu_solve for each member of a batch (one CTA per
- * matrix), nrhs right-hand sides each.  d_B: device array of device pointers,
- * d_ldb device int[batch].
+ * lu_solve_batched -- lu_solve for each member of a batch, nrhs right-hand
+ * sides each (max_n <= 256: one warp per matrix and right-hand side; larger:
+ * one CTA per matrix).  d_B: device array of device pointers, d_ldb device
+ * int[batch].
  */
 int lu_solve_batched(lu_dtype dt, int batch, int nrhs, const int *d_n, const void *const *d_LU,
                      const int *d_lda, const int *const *d_ipiv, void *const *d_B, const int *d_ldb,

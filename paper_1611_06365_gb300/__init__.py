@@ -178,10 +178,12 @@ def lu_solve_noalloc_capacity() -> int:
     return lib().lu_solve_noalloc_capacity()
 
 
-def lu_factor_batched(dtype_code, ns, A_ptrs, ldas, ipiv_ptrs, infos, max_n, *, stream=None):
-    """Batched factorization; all arguments are device tensors (pointer arrays as int64)."""
+def lu_factor_batched(dtype_code, ns, A_ptrs, ldas, ipiv_ptrs, infos, max_n, *, nb=0, stream=None):
+    """Batched factorization; all arguments are device tensors (pointer arrays as int64).
+    nb: 0 automatic, 16 or 32 blocked panel width, 1 the unblocked kernel."""
+    o = LuOpts(nb, 0, 0, 0, 0, 0)
     return _check("lu_factor_batched", lib().lu_factor_batched(dtype_code, ns.shape[0], _ptr(ns), _ptr(A_ptrs), _ptr(ldas),
-                                                                _ptr(ipiv_ptrs), _ptr(infos), max_n, None,
+                                                                _ptr(ipiv_ptrs), _ptr(infos), max_n, ctypes.byref(o),
                                                                 _stream(stream)))
 
 

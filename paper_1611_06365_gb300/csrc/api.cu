@@ -71,6 +71,15 @@ cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ld
                              int sms, cudaStream_t s);
 size_t trsv_workspace_ints(int n, int nrhs);
 cudaError_t launch_iota(int *v, int n, cudaStream_t s);
+// batched_blocked.cu
+constexpr int kBatchedBlockedMaxN = 256;
+size_t batched_blocked_workspace_ints(int batch);
+template <typename T>
+cudaError_t launch_getrf_batched_blocked(int batch, const int *ns, T *const *As, const int *ldas, int *const *ipivs,
+                                         int *infos, int nb, int *ws, int sms, cudaStream_t s);
+template <typename T>
+cudaError_t launch_getrs_batched_warp(int batch, int nrhs, const int *ns, const T *const *LUs, const int *ldas,
+                                      const int *const *ipivs, T *const *Bs, const int *ldbs, int sms, cudaStream_t s);
 // batched.cu
 template <typename T>
 cudaError_t launch_getrf_batched(int batch, const int *ns, T *const *As, const int *ldas, int *const *ipivs, int *infos,
@@ -515,7 +524,6 @@ int lu_solve(lu_dtype dt, int n, int nrhs, const void *dLU, int lda, const int *
 
 int lu_factor_batched(lu_dtype dt, int batch, const int *d_n, void *const *d_A, const int *d_lda, int *const *d_ipiv,
                       int *d_info, int max_n, const lu_opts *opts, void *stream) {
-    (void)opts;
     if (dt != LU_F64 && dt != LU_F32) return -1;
     if (batch < 0) return -2;
     if (batch > 0 && !d_n) return -3;
@@ -525,11 +533,30 @@ int lu_factor_batched(lu_dtype dt, int batch, const int *d_n, void *const *d_A, 
     if (batch > 0 && !d_info) return -7;
     if (max_n < 0 || max_n > 1024) return -8;
     if (batch > 2147483647 / 2) return -2;
+    const int nb = opts ? opts->nb : 0;
+    if (nb != 0 && nb != 1 && nb != 16 && nb != 32) return -9;
+    if ((nb == 16 || nb == 32) && max_n > kBatchedBlockedMaxN) return -9;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (nb == 1 || max_n > kBatchedBlockedMaxN) {
+        // the unblocked kernel: one CTA per matrix, the algorithm of Figure 1 (left) as written
+        if (dt == LU_F64)
+            LU_CUDA_TRY(launch_getrf_batched<double>(batch, d_n, reinterpret_cast<double *const *>(d_A), d_lda, d_ipiv, d_info, max_n, s));
+        else
+            LU_CUDA_TRY(launch_getrf_batched<float>(batch, d_n, reinterpret_cast<float *const *>(d_A), d_lda, d_ipiv, d_info, max_n, s));
+        return LU_OK;
+    }
+    if (batch == 0) return LU_OK;
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
+    Workspace ws(s);
+    int *bws = nullptr;
+    LU_CUDA_TRY(ws.get(&bws, batched_blocked_workspace_ints(batch)));
     if (dt == LU_F64)
-        LU_CUDA_TRY(launch_getrf_batched<double>(batch, d_n, reinterpret_cast<double *const *>(d_A), d_lda, d_ipiv, d_info, max_n, s));
+        LU_CUDA_TRY(launch_getrf_batched_blocked<double>(batch, d_n, reinterpret_cast<double *const *>(d_A), d_lda, d_ipiv,
+                                                         d_info, nb, bws, st->sms, s));
     else
-        LU_CUDA_TRY(launch_getrf_batched<float>(batch, d_n, reinterpret_cast<float *const *>(d_A), d_lda, d_ipiv, d_info, max_n, s));
+        LU_CUDA_TRY(launch_getrf_batched_blocked<float>(batch, d_n, reinterpret_cast<float *const *>(d_A), d_lda, d_ipiv,
+                                                        d_info, nb, bws, st->sms, s));
     return LU_OK;
 }
 
@@ -546,6 +573,20 @@ int lu_solve_batched(lu_dtype dt, int batch, int nrhs, const int *d_n, const voi
     if (batch > 0 && !d_ldb) return -9;
     if (max_n < 0 || max_n > 1024) return -10;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (max_n <= kBatchedBlockedMaxN) {
+        // one warp per (matrix, right-hand side)
+        DevState *st = nullptr;
+        LU_CUDA_TRY(dev_state(&st));
+        if (dt == LU_F64)
+            LU_CUDA_TRY(launch_getrs_batched_warp<double>(batch, nrhs, d_n, reinterpret_cast<const double *const *>(d_LU),
+                                                          d_lda, d_ipiv, reinterpret_cast<double *const *>(d_B), d_ldb,
+                                                          st->sms, s));
+        else
+            LU_CUDA_TRY(launch_getrs_batched_warp<float>(batch, nrhs, d_n, reinterpret_cast<const float *const *>(d_LU),
+                                                         d_lda, d_ipiv, reinterpret_cast<float *const *>(d_B), d_ldb,
+                                                         st->sms, s));
+        return LU_OK;
+    }
     if (dt == LU_F64)
         LU_CUDA_TRY(launch_getrs_batched<double>(batch, nrhs, d_n, reinterpret_cast<const double *const *>(d_LU), d_lda, d_ipiv,
                                                  reinterpret_cast<double *const *>(d_B), d_ldb, max_n, s));

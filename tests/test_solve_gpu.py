@@ -124,3 +124,36 @@ def test_batched_dyadic_exact():
         LU = li.from_device_colmajor(devA[t], n)
         assert np.array_equal(piv[t].cpu().numpy()[:n], expected_ipiv(perm))
         assert np.array_equal(np.triu(LU), U) and np.array_equal(np.tril(LU, -1) + np.eye(n), L)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_blocked_equals_unblocked(dtype):
+    """The blocked batched kernel (panel widths 16 and 32) applies every element's
+    fused multiply-adds in the unblocked order: factors, pivots and info are the
+    same bits as the unblocked kernel's (nb = 1), ragged orders, a singular member
+    and a member with ties included."""
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    sizes = [1, 2, 15, 16, 17, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 200, 255, 256]
+    mats = li.batch_matrices(np.array(sizes), seed=li.BASE_SEED + 3100)
+    mats.append(np.zeros((40, 40)))                     # every pivot zero
+    sing = li.uniform(70, 70, seed=3101)
+    sing[:, 35] = 0.0                                   # zero column: info = 36 unless an earlier pivot is zero
+    mats.append(sing)
+    mats.append(li.wilkinson(48))                       # magnitude ties in every column
+    code = lu.LU_F64 if dtype == "f64" else lu.LU_F32
+    results = {}
+    for nb in (1, 16, 32):
+        devA, piv, ns, ptrA, ptrP, lds, info = _batch_buffers(mats, dtype)
+        lu.lu_factor_batched(code, ns, ptrA, lds, ptrP, info, 256, nb=nb)
+        torch.cuda.synchronize()
+        results[nb] = ([t.cpu().numpy().copy() for t in devA], [p.cpu().numpy().copy() for p in piv], info.cpu().numpy().copy())
+    ref = results[1]
+    assert ref[2][-3] == 1 and ref[2][-2] > 0
+    for nb in (16, 32):
+        got = results[nb]
+        assert np.array_equal(got[2], ref[2])
+        for t in range(len(mats)):
+            assert np.array_equal(got[1][t], ref[1][t]), (nb, t)
+            assert np.array_equal(got[0][t].view(np.uint8), ref[0][t].view(np.uint8)), (nb, t)
