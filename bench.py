@@ -456,6 +456,25 @@ def run_case(args):
         ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
         lu.lu_factor(A, ipiv, info, update=lu.LU_UPDATE_BF16X3)
+    elif args.case in ("batched_f64", "batched_f32"):
+        # the batched workload (10 000 orders in [16, 256]): one factorization launch
+        import numpy as np
+        tdt = torch.float64 if args.case == "batched_f64" else torch.float32
+        code = lu.LU_F64 if args.case == "batched_f64" else lu.LU_F32
+        sizes = li.batch_sizes(BATCH_COUNT, 16, 256, seed=BATCH_SEED)
+        offs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
+        roffs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64))])
+        buf = li.uniform_colmajor_torch(1, int(offs[-1]), BATCH_SEED, dev, tdt).view(-1)
+        for t in range(1, BATCH_COUNT, 2):             # odd members diagonally dominant
+            n_t = int(sizes[t])
+            buf[int(offs[t]):int(offs[t + 1])].view(n_t, n_t).diagonal().add_(n_t)
+        esz = buf.element_size()
+        ns = torch.tensor(sizes, dtype=torch.int32, device=dev)
+        ptrA = torch.tensor([buf.data_ptr() + int(o) * esz for o in offs[:-1]], dtype=torch.int64, device=dev)
+        ipiv = torch.zeros(int(roffs[-1]), dtype=torch.int32, device=dev)
+        ptrP = torch.tensor([ipiv.data_ptr() + int(o) * 4 for o in roffs[:-1]], dtype=torch.int64, device=dev)
+        info = torch.zeros(BATCH_COUNT, dtype=torch.int32, device=dev)
+        lu.lu_factor_batched(code, ns, ptrA, ns, ptrP, info, 256)
     else:
         raise SystemExit(f"unknown case {args.case}")
     torch.cuda.synchronize()
@@ -475,7 +494,8 @@ def main():
     ap.add_argument("--skip-mixed", dest="skip_mixed", action="store_true")
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
     ap.add_argument("--skip-batched", dest="skip_batched", action="store_true")
-    ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor"], default=None,
+    ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32"],
+                    default=None,
                     help="run one profiling case instead of the benchmark")
     args = ap.parse_args()
     if args.case:
