@@ -60,9 +60,14 @@ enum {
 enum {
     LU_UPDATE_NATIVE = 0,  /* same precision as the storage (FP64 / FP32 SIMT) */
     LU_UPDATE_BF16 = 1,    /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
-    LU_UPDATE_BF16X3 = 2   /* split BF16 on tcgen05: x = hi + lo, three products
+    LU_UPDATE_BF16X3 = 2,  /* split BF16 on tcgen05: x = hi + lo, three products
                               hi*hi + hi*lo + lo*hi per pair, FP32 accumulate
                               (about 16 significant bits per product) */
+    LU_UPDATE_FP8 = 3      /* FP8 e4m3 on tcgen05 (kind::f8f6f4), FP32 accumulate;
+                              each staged row of L21 and column of U12 is
+                              multiplied by the power of two that brings its
+                              largest magnitude into (224, 448], and the
+                              epilogue applies the exact inverse factors */
 };
 
 /* Tuning knobs.  Pass NULL for the built-in choice; a zero field means "auto". */
@@ -162,7 +167,8 @@ int lu_solve_batched(lu_dtype dt, int batch, int nrhs, const int *d_n, const voi
  * 30 iterations, tol 1e-14, GMRES-IR and FP64 fallback both enabled, no
  * fp64_factor. */
 typedef struct {
-    int update;          /* LU_UPDATE_BF16X3 (default), LU_UPDATE_BF16 or LU_UPDATE_NATIVE (FP32) */
+    int update;          /* LU_UPDATE_BF16X3 (default), LU_UPDATE_BF16, LU_UPDATE_FP8 or
+                            LU_UPDATE_NATIVE (FP32) */
     int nb;              /* outer panel width for the FP32 factorization (0 = auto) */
     int max_iter;        /* refinement iterations before declaring a stall (0 = 30) */
     double tol;          /* target normwise backward error (0 = 1e-14) */
@@ -206,7 +212,8 @@ int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const double *dB,
  * paper): C := C - A * B with C m x n FP32 column-major (ldc), A m x k and
  * B k x n.  `update` selects LU_UPDATE_BF16 (operands rounded to BF16,
  * tcgen05 tensor cores, FP32 accumulate), LU_UPDATE_BF16X3 (split BF16,
- * three products) or LU_UPDATE_NATIVE (FP32 SIMT).
+ * three products), LU_UPDATE_FP8 (e4m3 with power-of-two scales per row of
+ * A and column of B; k <= 256) or LU_UPDATE_NATIVE (FP32 SIMT).
  * A (lda) and B (ldb) are FP32 column-major device matrices.  Exposed so
  * the update kernel can be tested and timed on its own.
  */

@@ -37,29 +37,34 @@ namespace lu {
 // panel.cu
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
-                               int *perm, __nv_bfloat16 *stage, int lds, int kpad, int split, int max_ctas,
-                               size_t smem_cap, int *status, long long bound_ns, cudaStream_t s);
+                               int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
+                               cudaStream_t s);
 int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo);
 // swap_trsm.cu
 template <typename T>
 cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c_begin, int c_end, int do_trsm,
-                             __nv_bfloat16 *stage, int ldst, int stage_c0, int stage_k, int split, cudaStream_t s);
+                             StageDesc sd, int stage_c0, cudaStream_t s);
 // gemm_simt.cu
 template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s);
 // gemm_tc.cu
-cudaError_t make_stage_maps(CUtensorMap *mapA, const __nv_bfloat16 *stageA, int rowsA, CUtensorMap *mapB,
-                            const __nv_bfloat16 *stageB, int colsB, int kinner, int lds);
+cudaError_t make_stage_maps(CUtensorMap *mapA, const void *stageA, int rowsA, CUtensorMap *mapB, const void *stageB,
+                            int colsB, int kinner, int lds, int fp8);
 int tc_box_rows();
 int tc_box_cols();
-cudaError_t make_stage_map(CUtensorMap *map, const __nv_bfloat16 *base, int kpad, int outer, int lds, int box_outer);
+cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8);
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
-                           int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s);
+                           int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
+                           const float *scaleA, const float *scaleB);
+cudaError_t launch_stage_rows_fp8(int rows, int k, int kpad, const float *L, int ld, unsigned char *stage, int lds,
+                                  float *scale, cudaStream_t s);
+cudaError_t launch_stage_cols_fp8(int k, int kpad, int cols, const float *B, int ld, unsigned char *stage, int lds,
+                                  float *scale, cudaStream_t s);
 cudaError_t launch_stage_rows(int rows, int k, int kpad, const float *L, int ld, __nv_bfloat16 *stage, int lds, int split,
                               cudaStream_t s);
 cudaError_t launch_stage_cols(int k, int kpad, int cols, const float *B, int ld, __nv_bfloat16 *stage, int lds, int split,
                               cudaStream_t s);
-int tc_kpad(int k);
+int tc_kpad(int k, int fp8);
 int tc_max_k();
 bool tc_c_aligned(const float *C, int ldc);
 // solve.cu
@@ -248,8 +253,8 @@ struct Plan {
     int bo = 0;       // outer panel width
     int bi = 0;       // inner panel width (cluster capacity)
     bool bi_auto = true;   // per panel: the widest inner width its row count allows
-    bool tc = false;  // BF16 tensor-core update
-    int nprod = 1;    // 1: BF16, 3: split BF16
+    bool tc = false;  // tensor-core update
+    int fmt = 0;      // staging format: 0 BF16, 1 split BF16, 2 FP8 e4m3 (StageDesc)
     bool lookahead = true;
     int panel_ctas = 16;
     long long bound = 2000000000LL;
@@ -258,11 +263,14 @@ struct Plan {
 template <typename T>
 Plan make_plan(int n, const lu_opts *o) {
     Plan p;
-    const bool tc = (sizeof(T) == 4) && o && (o->update == LU_UPDATE_BF16 || o->update == LU_UPDATE_BF16X3);
+    const bool tc = (sizeof(T) == 4) && o &&
+                    (o->update == LU_UPDATE_BF16 || o->update == LU_UPDATE_BF16X3 || o->update == LU_UPDATE_FP8);
     p.tc = tc;
-    p.nprod = (o && o->update == LU_UPDATE_BF16X3) ? 3 : 1;
+    p.fmt = (o && o->update == LU_UPDATE_BF16X3) ? 1 : ((o && o->update == LU_UPDATE_FP8) ? 2 : 0);
     if (tc) {
-        p.bo = (o && o->nb > 0) ? o->nb : (n >= 8192 ? 256 : (n >= 2048 ? 128 : 64));
+        // the factorization is panel-bound up to n ~ 16k (the update is HBM-bound
+        // with C traffic 8 n^3 / (3 b_o)): narrower panels keep the panel chain short
+        p.bo = (o && o->nb > 0) ? o->nb : (n >= 24576 ? 128 : 64);
         p.bo = std::min(p.bo, tc_max_k());
     } else if (sizeof(T) == 4) {
         p.bo = (o && o->nb > 0) ? o->nb : 128;
@@ -295,8 +303,10 @@ struct FactorCtx {
     Plan pl;
     DevState *st;
     int *maps[2];         // row maps of panels k (parity)
-    __nv_bfloat16 *stA[2] = {nullptr, nullptr};
-    __nv_bfloat16 *stB = nullptr;
+    unsigned char *stA[2] = {nullptr, nullptr};   // staged L21 of panels k (parity), bytes
+    unsigned char *stB = nullptr;                 // staged U12
+    float *scA[2] = {nullptr, nullptr};           // FP8: row scales of stA
+    float *scB = nullptr;                         // FP8: column scales of stB
     int kpad = 0;
     int kinner = 0;   // staged elements per row/column (kpad, or 2 kpad when split)
     CUtensorMap mapA[2], mapB;
@@ -321,7 +331,7 @@ cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cu
     if ((e = update_launch<T>(c, k_par, kb, w, c0, c1, s)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t.b, s)) != cudaSuccess) return e;
     const int k = c.pl.tc ? c.kpad : w;
-    const double opw = c.pl.tc ? 2.0 : (double)sizeof(T);
+    const double opw = c.pl.tc ? (c.pl.fmt == 2 ? 1.0 : 2.0) : (double)sizeof(T);
     t.flops = 2.0 * m * nn * (double)w;
     t.bytes = 2.0 * m * nn * sizeof(T) + (double)m * k * opw + (double)k * nn * opw;
     std::lock_guard<std::mutex> lk(g_tmu);
@@ -335,9 +345,9 @@ cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int
     const int m = c.n - r0, nn = c1 - c0;
     if constexpr (sizeof(T) == 4) {
         if (c.pl.tc)
-            return launch_gemm_tc(c.pl.nprod, m, nn, c.kpad, c.mapA[k_par], 0, c.mapB, c0 - r0,
-                                  reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda,
-                                  c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status, c.pl.bound, s);
+            return launch_gemm_tc(c.pl.fmt == 1 ? 3 : (c.pl.fmt == 2 ? 8 : 1), m, nn, c.kpad, c.mapA[k_par], 0, c.mapB,
+                                  c0 - r0, reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda,
+                                  c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status, c.pl.bound, s, c.scA[k_par], c.scB);
     }
     return launch_gemm_simt<T>(m, nn, w, c.A + r0 + (size_t)kb * c.lda, c.lda, c.A + kb + (size_t)c0 * c.lda, c.lda,
                                c.A + r0 + (size_t)c0 * c.lda, c.lda, s);
@@ -345,21 +355,23 @@ cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int
 
 template <typename T>
 cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, int c1, int do_trsm, cudaStream_t s) {
-    __nv_bfloat16 *stage = (do_trsm && c.pl.tc) ? c.stB : nullptr;
-    return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, stage, c.kinner, kb + w, c.kpad, c.pl.nprod == 3, s);
+    StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt};
+    if (do_trsm && c.pl.tc) { sd.ptr = c.stB; sd.scale = c.scB; }
+    return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, sd, kb + w, s);
 }
 
 // Factor outer panel at column kb (width w) on stream s: one cluster launch
 // that also leaves the row map in maps[par], updates perm and stages L21.
 template <typename T>
 cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s) {
-    __nv_bfloat16 *stage = (c.pl.tc && kb + w < c.n) ? c.stA[par] : nullptr;
+    StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt};
+    if (c.pl.tc && kb + w < c.n) { sd.ptr = c.stA[par]; sd.scale = c.scA[par]; }
     // the panel's rows shrink with k, so later panels hold wider inner panels
     int bi = c.pl.bi;
     if (c.pl.bi_auto) bi = std::max(bi, panel_width_that_fits(c.n - kb, sizeof(T), kPanelSmemCap, 64, w));
     return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, std::min(bi, w), c.ipiv + kb, kb,
-                                 c.info, c.maps[par], c.perm, stage, c.kinner, c.kpad, c.pl.nprod == 3, c.pl.panel_ctas,
-                                 kPanelSmemCap, c.st->status, c.pl.bound, s);
+                                 c.info, c.maps[par], c.perm, sd, c.pl.panel_ctas, kPanelSmemCap, c.st->status,
+                                 c.pl.bound, s);
 }
 
 template <typename T>
@@ -398,12 +410,19 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
     LU_CUDA_TRY(ws.get(&c.tile_ctr, 2));
     if (perm) LU_CUDA_TRY(launch_iota(perm, n, caller));
     if (pl.tc) {
-        c.kpad = tc_kpad(bo);
-        c.kinner = c.kpad * (pl.nprod == 3 ? 2 : 1);
-        for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.stA[i], (size_t)n * c.kinner));
-        LU_CUDA_TRY(ws.get(&c.stB, (size_t)n * c.kinner));
-        for (int i = 0; i < 2; ++i) LU_CUDA_TRY(make_stage_map(&c.mapA[i], c.stA[i], c.kinner, n, c.kinner, tc_box_rows()));
-        LU_CUDA_TRY(make_stage_map(&c.mapB, c.stB, c.kinner, n, c.kinner, tc_box_cols()));
+        const int fp8 = pl.fmt == 2;
+        c.kpad = tc_kpad(bo, fp8);
+        c.kinner = c.kpad * (pl.fmt == 1 ? 2 : 1);
+        const size_t esz = fp8 ? 1 : 2;
+        for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.stA[i], (size_t)n * c.kinner * esz));
+        LU_CUDA_TRY(ws.get(&c.stB, (size_t)n * c.kinner * esz));
+        if (fp8) {
+            for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.scA[i], (size_t)n));
+            LU_CUDA_TRY(ws.get(&c.scB, (size_t)n));
+        }
+        for (int i = 0; i < 2; ++i)
+            LU_CUDA_TRY(make_stage_map(&c.mapA[i], c.stA[i], c.kinner, n, c.kinner, tc_box_rows(), fp8));
+        LU_CUDA_TRY(make_stage_map(&c.mapB, c.stB, c.kinner, n, c.kinner, tc_box_cols(), fp8));
     }
     cudaStream_t P = st->P, U = st->U;
     LU_CUDA_TRY(cudaEventRecord(st->evIn, caller));
@@ -492,7 +511,8 @@ int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info, c
     if (n > 0 && !d_ipiv) return -5;
     if (!d_info) return -6;
     if (opts && (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 ||
-                 (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3)))
+                 (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
+                  opts->update != LU_UPDATE_FP8)))
         return -7;
     if (opts && opts->update != LU_UPDATE_NATIVE && dt != LU_F32) return -7;
     if (opts && opts->update != LU_UPDATE_NATIVE && opts->nb > tc_max_k()) return -7;
@@ -598,7 +618,8 @@ int lu_solve_batched(lu_dtype dt, int batch, int nrhs, const int *d_n, const voi
 
 int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda, const float *dB, int ldb, float *dC,
                        int ldc, void *stream) {
-    if (update != LU_UPDATE_NATIVE && update != LU_UPDATE_BF16 && update != LU_UPDATE_BF16X3) return -1;
+    if (update != LU_UPDATE_NATIVE && update != LU_UPDATE_BF16 && update != LU_UPDATE_BF16X3 && update != LU_UPDATE_FP8)
+        return -1;
     if (m < 0) return -2;
     if (n < 0) return -3;
     if (k < 0 || (update != LU_UPDATE_NATIVE && k > tc_max_k())) return -4;
@@ -617,20 +638,39 @@ int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda
     DevState *st = nullptr;
     LU_CUDA_TRY(dev_state(&st));
     Workspace ws(s);
-    const int kpad = tc_kpad(k);
+    const int fp8 = update == LU_UPDATE_FP8;
+    const int kpad = tc_kpad(k, fp8);
     const int split = update == LU_UPDATE_BF16X3;
     const int kinner = kpad * (split ? 2 : 1);
-    __nv_bfloat16 *sa = nullptr, *sb = nullptr;
-    LU_CUDA_TRY(ws.get(&sa, (size_t)m * kinner));
-    LU_CUDA_TRY(ws.get(&sb, (size_t)n * kinner));
-    LU_CUDA_TRY(launch_stage_rows(m, k, kpad, dA, lda, sa, kinner, split, s));
-    LU_CUDA_TRY(launch_stage_cols(k, kpad, n, dB, ldb, sb, kinner, split, s));
+    const int nprod = fp8 ? 8 : (split ? 3 : 1);
+    void *sa = nullptr, *sb = nullptr;
+    float *scA = nullptr, *scB = nullptr;
+    if (fp8) {
+        unsigned char *a8 = nullptr, *b8 = nullptr;
+        LU_CUDA_TRY(ws.get(&a8, (size_t)m * kinner));
+        LU_CUDA_TRY(ws.get(&b8, (size_t)n * kinner));
+        LU_CUDA_TRY(ws.get(&scA, (size_t)m));
+        LU_CUDA_TRY(ws.get(&scB, (size_t)n));
+        LU_CUDA_TRY(launch_stage_rows_fp8(m, k, kpad, dA, lda, a8, kinner, scA, s));
+        LU_CUDA_TRY(launch_stage_cols_fp8(k, kpad, n, dB, ldb, b8, kinner, scB, s));
+        sa = a8;
+        sb = b8;
+    } else {
+        __nv_bfloat16 *a16 = nullptr, *b16 = nullptr;
+        LU_CUDA_TRY(ws.get(&a16, (size_t)m * kinner));
+        LU_CUDA_TRY(ws.get(&b16, (size_t)n * kinner));
+        LU_CUDA_TRY(launch_stage_rows(m, k, kpad, dA, lda, a16, kinner, split, s));
+        LU_CUDA_TRY(launch_stage_cols(k, kpad, n, dB, ldb, b16, kinner, split, s));
+        sa = a16;
+        sb = b16;
+    }
     CUtensorMap ma, mb;
     int *ctr = nullptr;
     LU_CUDA_TRY(ws.get(&ctr, 1));
-    LU_CUDA_TRY(make_stage_maps(&ma, sa, m, &mb, sb, n, kinner, kinner));
+    LU_CUDA_TRY(make_stage_maps(&ma, sa, m, &mb, sb, n, kinner, kinner, fp8));
     if (tc_c_aligned(dC, ldc)) {
-        LU_CUDA_TRY(launch_gemm_tc(split ? 3 : 1, m, n, kpad, ma, 0, mb, 0, dC, ldc, ctr, st->status, lu_spin_bound_ns(nullptr), s));
+        LU_CUDA_TRY(launch_gemm_tc(nprod, m, n, kpad, ma, 0, mb, 0, dC, ldc, ctr, st->status, lu_spin_bound_ns(nullptr), s,
+                                   scA, scB));
     } else {
         // the kernel moves C with TMA (16-byte aligned rows): work on an aligned copy
         const int ldt = (m + 3) & ~3;
@@ -638,7 +678,8 @@ int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda
         LU_CUDA_TRY(ws.get(&ct, (size_t)ldt * n));
         LU_CUDA_TRY(cudaMemcpy2DAsync(ct, sizeof(float) * ldt, dC, sizeof(float) * ldc, sizeof(float) * m, n,
                                       cudaMemcpyDeviceToDevice, s));
-        LU_CUDA_TRY(launch_gemm_tc(split ? 3 : 1, m, n, kpad, ma, 0, mb, 0, ct, ldt, ctr, st->status, lu_spin_bound_ns(nullptr), s));
+        LU_CUDA_TRY(launch_gemm_tc(nprod, m, n, kpad, ma, 0, mb, 0, ct, ldt, ctr, st->status, lu_spin_bound_ns(nullptr), s,
+                                   scA, scB));
         LU_CUDA_TRY(cudaMemcpy2DAsync(dC, sizeof(float) * ldc, ct, sizeof(float) * ldt, sizeof(float) * m, n,
                                       cudaMemcpyDeviceToDevice, s));
     }

@@ -1,6 +1,7 @@
 // Shared device/host helpers of liblu (CUDA path only).
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_fp8.h>
 #include <cstdint>
 #include <cstdio>
 #include "../../include/lu.h"
@@ -81,3 +82,35 @@ __device__ __forceinline__ bool lu_better(T mag_a, int idx_a, T mag_b, int idx_b
 }
 
 static inline int lu_ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Where and how the tensor-core update's operands are staged (the panel
+// kernel stages L21, the interchange/solve kernel stages U12):
+//   fmt 0: BF16; 1: BF16 hi | lo halves (hi at k, lo at kpad + k);
+//   2: FP8 e4m3 scaled by a power of two per staged row or column, whose
+//      inverse goes to scale[].
+// ptr == NULL: no staging.  lds and kpad count elements of the staged type.
+struct StageDesc {
+    void *ptr;
+    float *scale;
+    int lds;
+    int kpad;
+    int fmt;
+};
+
+// Power-of-two scaling into the e4m3 range: the multiplier 2^e with the
+// largest e such that amax * 2^e <= 448 (the largest finite e4m3 value), and
+// its inverse; 1 for a zero or non-finite amax.  e is clamped so both stay
+// normal FP32 numbers.
+__device__ __forceinline__ float lu_fp8_scale(float amax, float *inv) {
+    if (!(amax > 0.f) || !(amax <= 3.0e38f)) { *inv = 1.f; return 1.f; }
+    int q = 0;
+    const float mant = frexpf(amax, &q);            // amax = mant * 2^q, mant in [0.5, 1)
+    int e = (mant <= 0.875f) ? 9 - q : 8 - q;       // 448 = 0.875 * 2^9
+    e = e > 126 ? 126 : (e < -126 ? -126 : e);
+    *inv = ldexpf(1.f, -e);
+    return ldexpf(1.f, e);
+}
+
+__device__ __forceinline__ unsigned char lu_to_e4m3(float x) {
+    return (unsigned char)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}

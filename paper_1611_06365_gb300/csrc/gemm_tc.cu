@@ -1,7 +1,9 @@
 // Trailing update RL3 / PF2 / RU2 (section 3.1, Figure 1 right; section 3.2,
 // Figure 3) on the 5th-generation tensor cores: C := C - A * B with C in FP32
 // and the operands A = L21 and B = U12 rounded to BF16 (or split into two
-// BF16 halves, three products).
+// BF16 halves, three products), or to FP8 e4m3 with a power-of-two scale per
+// staged row of A and per staged column of B (the epilogue multiplies the
+// FP32 accumulator by the two exact reciprocal scales).
 //
 // Persistent, warp-specialized kernel, one CTA per SM, 128 x 128 tiles of C
 // taken from a global atomic tile queue; all data movement through TMA:
@@ -9,7 +11,8 @@
 //            128 rows x 128 columns, four 128 x 32 boxes) into the C buffer
 //            once the previous tile's store has drained it; the K chunks of
 //            the A and B tiles (128-byte swizzle) into a ring of stages;
-//   warp 1   MMA issuer: tcgen05.mma kind::f16 (M=128, N=128, K=16) into one
+//   warp 1   MMA issuer: tcgen05.mma kind::f16 (M=128, N=128, K=16) or
+//            kind::f8f6f4 (K=32) into one
 //            of two TMEM accumulators; tcgen05.commit frees stages and hands
 //            the accumulator to the epilogue;
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator, C := C - acc in shared
@@ -19,10 +22,13 @@
 // mbarrier wait is bounded; on expiry the kernel records LU_ERR_TIMEOUT, waits
 // once more (bounded) for its own copies, frees its TMEM and returns.
 //
-// Operand staging (BF16, K contiguous, K padded to a multiple of 64 with zeros):
+// Operand staging (K contiguous, K padded with zeros to one 128-byte swizzle
+// span: 64 BF16 or 128 FP8 elements):
 //   A: row-major, element (i, k) at stageA[i * lds + k]  (the panel's L21)
 //   B: column-major, element (k, j) at stageB[j * lds + k]  (U12 by columns)
-// With the split, the low halves follow at k + kpad.
+// With the split, the low halves follow at k + kpad.  FP8 staging carries
+// scaleA[i] (= 2^-e_i, the inverse of the factor applied to row i) and
+// scaleB[j].
 #include "common.cuh"
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -33,6 +39,7 @@ namespace lu {
 constexpr int kTcBM = 128;
 constexpr int kTcBN = 128;
 constexpr int kTcBK = 64;            // one 128-byte swizzle span of BF16
+constexpr int kTcBK8 = 128;          // one 128-byte swizzle span of FP8
 constexpr int kTcMaxK = 256;
 constexpr int kTcThreads = 192;      // 6 warps: TMA, MMA, 4 x epilogue
 constexpr int kTcChunkA = kTcBM * kTcBK * 2;   // 16 KB
@@ -115,6 +122,20 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t
         : "memory");
 }
 
+// Instruction descriptor of kind::f8f6f4: D=F32, A=B=E4M3 (format 0), both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_e4m3(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -135,14 +156,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// NPROD: 1 = BF16, 3 = split BF16 (three products), 8 = FP8 e4m3 with scales.
 template <int NPROD>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, int a_row0,
                const __grid_constant__ CUtensorMap mapB, int b_col0, const __grid_constant__ CUtensorMap mapC,
-               int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns) {
-    constexpr int NSPLIT = NPROD == 1 ? 1 : 2;
+               int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns,
+               const float *__restrict__ scaleA, const float *__restrict__ scaleB) {
+    constexpr bool FP8 = NPROD == 8;
+    constexpr int BK = FP8 ? kTcBK8 : kTcBK;        // K elements per 128-byte chunk
+    constexpr int NSPLIT = NPROD == 3 ? 2 : 1;
     constexpr uint32_t kStageBytes = (uint32_t)NSPLIT * (kTcChunkA + kTcChunkB);
-    constexpr int kStages = NPROD == 1 ? 4 : 2;
+    constexpr int kStages = NSPLIT == 1 ? 4 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -160,7 +185,7 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
     volatile int *acc_tile = reinterpret_cast<volatile int *>(tmem_slot + 2 + kStages);  // [2]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nk = K / kTcBK;                       // K is a multiple of kTcBK
+    const int nk = K / BK;                          // K is a multiple of BK
     const int kpad_off = K;                         // lo halves start at x = K
     const int mt = (m + kTcBM - 1) / kTcBM, ntl = (n + kTcBN - 1) / kTcBN;
     const int ntiles = mt * ntl;
@@ -208,11 +233,11 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
                     } else {
                         mbar_expect_tx(fb, kStageBytes);
-                        tma_load_2d(st, &mapA, kc * kTcBK, a_row0 + tm, fb);
-                        tma_load_2d(st + NSPLIT * kTcChunkA, &mapB, kc * kTcBK, b_col0 + tn, fb);
+                        tma_load_2d(st, &mapA, kc * BK, a_row0 + tm, fb);
+                        tma_load_2d(st + NSPLIT * kTcChunkA, &mapB, kc * BK, b_col0 + tn, fb);
                         if (NSPLIT == 2) {
-                            tma_load_2d(st + kTcChunkA, &mapA, kpad_off + kc * kTcBK, a_row0 + tm, fb);
-                            tma_load_2d(st + 2 * kTcChunkA + kTcChunkB, &mapB, kpad_off + kc * kTcBK, b_col0 + tn, fb);
+                            tma_load_2d(st + kTcChunkA, &mapA, kpad_off + kc * BK, a_row0 + tm, fb);
+                            tma_load_2d(st + 2 * kTcChunkA + kTcChunkB, &mapB, kpad_off + kc * BK, b_col0 + tn, fb);
                         }
                     }
                     if (++s == kStages) { s = 0; ph ^= 1u; }
@@ -233,7 +258,7 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = umma_idesc_bf16(kTcBM, kTcBN);
+            const uint32_t idesc = FP8 ? umma_idesc_e4m3(kTcBM, kTcBN) : umma_idesc_bf16(kTcBM, kTcBN);
             int s = 0;
             uint32_t ph = 0;
             for (int it = 0;; ++it) {
@@ -265,9 +290,12 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
                     const uint32_t sAh = st, sAl = st + kTcChunkA;
                     const uint32_t sBh = st + NSPLIT * kTcChunkA, sBl = sBh + kTcChunkB;
 #pragma unroll
-                    for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                    for (int kk = 0; kk < 4; ++kk) {   // four MMAs of 32 bytes of K per 128-byte chunk
                         const uint32_t first = (kc | kk) == 0 ? 0u : 1u;
-                        umma_bf16(acc, umma_desc_sw128(sAh + kk * 32), umma_desc_sw128(sBh + kk * 32), idesc, first);
+                        if (FP8)
+                            umma_e4m3(acc, umma_desc_sw128(sAh + kk * 32), umma_desc_sw128(sBh + kk * 32), idesc, first);
+                        else
+                            umma_bf16(acc, umma_desc_sw128(sAh + kk * 32), umma_desc_sw128(sBh + kk * 32), idesc, first);
                         if (NPROD == 3) {
                             umma_bf16(acc, umma_desc_sw128(sAh + kk * 32), umma_desc_sw128(sBl + kk * 32), idesc, 1u);
                             umma_bf16(acc, umma_desc_sw128(sAl + kk * 32), umma_desc_sw128(sBh + kk * 32), idesc, 1u);
@@ -302,13 +330,24 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
             if (!ok || *abort_flag) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = tmem + (uint32_t)(a * kTcBN) + ((uint32_t)(q * 32) << 16);
+            // FP8: undo the staging scales (powers of two: exact)
+            const float sa = FP8 ? (tm + r < m ? scaleA[a_row0 + tm + r] : 0.f) : 1.f;
 #pragma unroll
             for (int h = 0; h < kTcBN / 32; ++h) {
                 float v[32];
                 tmem_ld32(acc + (uint32_t)(h * 32), v);
                 float *box = Cs + (size_t)h * (kTcBM * kTcCBox);   // box h: [32 cols][128 rows]
+                if (FP8) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) box[c * kTcBM + r] -= v[c];
+                    for (int c = 0; c < 32; ++c) {
+                        const int col = tn + h * 32 + c;
+                        const float sb = col < n ? __ldg(&scaleB[b_col0 + col]) : 0.f;
+                        box[c * kTcBM + r] -= v[c] * sa * sb;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) box[c * kTcBM + r] -= v[c];
+                }
             }
             // accumulator read: the MMAs of the tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -382,6 +421,41 @@ __global__ void stage_cols_bf16(int k, int kpad, int cols, const float *__restri
     }
 }
 
+// L21 (rows x k, FP32 column-major) -> e4m3 row-major stage[i * lds + kk], one
+// power-of-two scale per row: scale[i] = the inverse multiplier.  One warp per row.
+__global__ void stage_rows_fp8(int rows, int k, int kpad, const float *__restrict__ L, int ld,
+                               unsigned char *__restrict__ stage, int lds, float *__restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < rows; i += gridDim.x * (blockDim.x >> 5)) {
+        float amax = 0.f;
+        for (int kk = lane; kk < k; kk += 32) amax = fmaxf(amax, fabsf(L[(size_t)i + (size_t)kk * ld]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        float inv;
+        const float mul = lu_fp8_scale(amax, &inv);
+        if (lane == 0) scale[i] = inv;
+        for (int kk = lane; kk < kpad; kk += 32)
+            stage[(size_t)i * lds + kk] = kk < k ? lu_to_e4m3(L[(size_t)i + (size_t)kk * ld] * mul) : (unsigned char)0;
+    }
+}
+
+// B (k x cols, FP32 column-major) -> e4m3 stage[j * lds + kk], one scale per column.
+__global__ void stage_cols_fp8(int k, int kpad, int cols, const float *__restrict__ B, int ld,
+                               unsigned char *__restrict__ stage, int lds, float *__restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < cols; j += gridDim.x * (blockDim.x >> 5)) {
+        float amax = 0.f;
+        for (int kk = lane; kk < k; kk += 32) amax = fmaxf(amax, fabsf(B[(size_t)kk + (size_t)j * ld]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        float inv;
+        const float mul = lu_fp8_scale(amax, &inv);
+        if (lane == 0) scale[j] = inv;
+        for (int kk = lane; kk < kpad; kk += 32)
+            stage[(size_t)j * lds + kk] = kk < k ? lu_to_e4m3(B[(size_t)kk + (size_t)j * ld] * mul) : (unsigned char)0;
+    }
+}
+
 // ---- host side ---------------------------------------------------------------
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -397,27 +471,29 @@ static cudaError_t get_encoder() {
     return cudaSuccess;
 }
 
-// 2-D BF16 map over a K-major staging buffer: inner dimension kpad (elements),
-// outer dimension `outer` rows/columns, leading dimension lds elements.
-cudaError_t make_stage_map(CUtensorMap *map, const __nv_bfloat16 *base, int kpad, int outer, int lds, int box_outer) {
+// 2-D map over a K-major staging buffer (BF16, or FP8 bytes when fp8): inner
+// dimension kinner elements, outer dimension `outer` rows/columns, leading
+// dimension lds elements; boxes of one 128-byte swizzle span x box_outer.
+cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8) {
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
-    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)(outer > 0 ? outer : 1)};
-    cuuint64_t strides[1] = {(cuuint64_t)lds * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_outer};
+    const int esz = fp8 ? 1 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)kinner, (cuuint64_t)(outer > 0 ? outer : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)lds * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(fp8 ? kTcBK8 : kTcBK), (cuuint32_t)box_outer};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box,
-                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = g_encode(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// kinner: elements per staged row/column (kpad, or 2 kpad with split)
-cudaError_t make_stage_maps(CUtensorMap *mapA, const __nv_bfloat16 *stageA, int rowsA, CUtensorMap *mapB,
-                            const __nv_bfloat16 *stageB, int colsB, int kinner, int lds) {
-    cudaError_t e = make_stage_map(mapA, stageA, kinner, rowsA, lds, kTcBM);
+// kinner: elements per staged row/column (kpad, or 2 kpad when split)
+cudaError_t make_stage_maps(CUtensorMap *mapA, const void *stageA, int rowsA, CUtensorMap *mapB, const void *stageB,
+                            int colsB, int kinner, int lds, int fp8) {
+    cudaError_t e = make_stage_map(mapA, stageA, kinner, rowsA, lds, kTcBM, fp8);
     if (e != cudaSuccess) return e;
-    return make_stage_map(mapB, stageB, kinner, colsB, lds, kTcBN);
+    return make_stage_map(mapB, stageB, kinner, colsB, lds, kTcBN, fp8);
 }
 
 int tc_box_rows() { return kTcBM; }
@@ -440,19 +516,39 @@ static cudaError_t make_c_map(CUtensorMap *map, float *C, int m, int n, int ldc)
 
 bool tc_c_aligned(const float *C, int ldc) { return ((uintptr_t)C % 16 == 0) && (ldc % 4 == 0); }
 
+template <int NPROD>
+static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
+                                  int b_col0, const CUtensorMap &mapC, int *tile_ctr, int *status, long long bound_ns,
+                                  const float *scaleA, const float *scaleB, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    gemm_update_tc<NPROD><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
+                                                             bound_ns, scaleA, scaleB);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
 // C[m x n] -= A[a_row0 + (0..m), 0..K) * B[0..K, b_col0 + (0..n)] through the maps
-// (nprod = 1: BF16 operands; nprod = 3: split BF16, staging holds hi | lo).
+// (nprod = 1: BF16 operands; 3: split BF16, staging holds hi | lo; 8: FP8 e4m3
+// with the row scales scaleA[a_row0 + i] and column scales scaleB[b_col0 + j]).
 // C must be 16-byte aligned with ldc a multiple of 4 (tc_c_aligned).
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
-                           int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s) {
+                           int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
+                           const float *scaleA, const float *scaleB) {
     if (m <= 0 || n <= 0 || K <= 0) return cudaSuccess;
-    if (K > kTcMaxK || K % kTcBK != 0 || (nprod != 1 && nprod != 3)) return cudaErrorInvalidValue;
+    if (nprod != 1 && nprod != 3 && nprod != 8) return cudaErrorInvalidValue;
+    const int bk = nprod == 8 ? kTcBK8 : kTcBK;
+    if (K > (nprod == 8 ? 2 * kTcMaxK : kTcMaxK) || K % bk != 0) return cudaErrorInvalidValue;
+    if (nprod == 8 && (!scaleA || !scaleB)) return cudaErrorInvalidValue;
     if (!tc_c_aligned(C, ldc)) return cudaErrorInvalidValue;
     CUtensorMap mapC;
     cudaError_t ec = make_c_map(&mapC, C, m, n, ldc);
     if (ec != cudaSuccess) return ec;
     static int sms = 0;
-    static bool attr[2] = {false, false};
     if (!sms) {
         int d = 0;
         cudaGetDevice(&d);
@@ -463,25 +559,9 @@ cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &ma
     const int grid = ntiles < sms ? ntiles : sms;
     cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
     if (ez != cudaSuccess) return ez;
-    if (nprod == 1) {
-        if (!attr[0]) {
-            cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-            if (e != cudaSuccess) return e;
-            attr[0] = true;
-        }
-        gemm_update_tc<1><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
-                                                            bound_ns);
-    } else {
-        if (!attr[1]) {
-            cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-            if (e != cudaSuccess) return e;
-            attr[1] = true;
-        }
-        gemm_update_tc<3><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
-                                                            bound_ns);
-    }
-    lu_count_launch();
-    return cudaGetLastError();
+    if (nprod == 1) return launch_tc_mode<1>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s);
+    if (nprod == 3) return launch_tc_mode<3>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s);
+    return launch_tc_mode<8>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, scaleA, scaleB, s);
 }
 
 cudaError_t launch_stage_rows(int rows, int k, int kpad, const float *L, int ld, __nv_bfloat16 *stage, int lds, int split,
@@ -503,7 +583,29 @@ cudaError_t launch_stage_cols(int k, int kpad, int cols, const float *B, int ld,
     return cudaGetLastError();
 }
 
-int tc_kpad(int k) { return ((k + kTcBK - 1) / kTcBK) * kTcBK; }
+cudaError_t launch_stage_rows_fp8(int rows, int k, int kpad, const float *L, int ld, unsigned char *stage, int lds,
+                                  float *scale, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    const int grid = lu_ceil_div(rows, 8) < 152 * 16 ? lu_ceil_div(rows, 8) : 152 * 16;
+    stage_rows_fp8<<<grid, 256, 0, s>>>(rows, k, kpad, L, ld, stage, lds, scale);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_cols_fp8(int k, int kpad, int cols, const float *B, int ld, unsigned char *stage, int lds,
+                                  float *scale, cudaStream_t s) {
+    if (cols <= 0) return cudaSuccess;
+    const int grid = lu_ceil_div(cols, 8) < 152 * 16 ? lu_ceil_div(cols, 8) : 152 * 16;
+    stage_cols_fp8<<<grid, 256, 0, s>>>(k, kpad, cols, B, ld, stage, lds, scale);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+// K padded to whole 128-byte chunks: 64 BF16 or 128 FP8 elements
+int tc_kpad(int k, int fp8) {
+    const int bk = fp8 ? kTcBK8 : kTcBK;
+    return ((k + bk - 1) / bk) * bk;
+}
 int tc_max_k() { return kTcMaxK; }
 
 }  // namespace lu

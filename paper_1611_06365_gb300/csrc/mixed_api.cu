@@ -101,7 +101,8 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     if (ldb < std::max(1, n)) return -6;
     if (n > 0 && nrhs > 0 && !dX) return -7;
     if (ldx < std::max(1, n)) return -8;
-    if (opts && (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3))
+    if (opts && (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
+                 opts->update != LU_UPDATE_FP8))
         return -9;
     if (opts && (opts->nb < 0 || opts->max_iter < 0 || opts->tol < 0 || opts->gmres_restart < 0)) return -9;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -29,8 +29,8 @@
 // trailing update A22 -= L21 U12 runs on each thread's rows with L21 taken
 // from registers.  At the end the kernel builds the row map of all b_o
 // interchanges for the rest of the matrix, updates the permutation vector,
-// and, for the tensor-core update, stages L21 as BF16 (optionally split
-// hi/lo) in K-major order.
+// and, for the tensor-core update, stages L21 in K-major order: BF16,
+// BF16 split into hi/lo, or FP8 e4m3 with a power-of-two scale per row.
 //
 // Slots, staging rows and barriers are double-buffered by column parity: a CTA
 // pushes column j+2 only after its barrier for column j+1 completed, i.e.
@@ -298,8 +298,7 @@ template <typename T, int RPT>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, int *__restrict__ ipiv, int row_base,
                      int *__restrict__ info, int *__restrict__ map_out, int *__restrict__ perm,
-                     __nv_bfloat16 *__restrict__ stage, int lds, int kpad, int split, int *__restrict__ status,
-                     long long bound_ns) {
+                     StageDesc sd, int *__restrict__ status, long long bound_ns) {
     constexpr int BI = TileWidth<T, RPT>::BI;
     using V = typename Vec16<T>::type;
     constexpr int VEC = 16 / sizeof(T);
@@ -575,9 +574,12 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             for (int s = tid; s < n; s += kPanelThreads) perm[row_base + rows[s]] = old[s];
         }
     }
-    // BF16 staging of L21 (panel rows kmax.. become stage rows 0..), K-major
-    if (stage) {
+    // staging of L21 for the tensor-core update (panel rows kmax.. become stage
+    // rows 0..), K-major, in 32-row chunks through shared memory
+    if (sd.ptr) {
         float *tile = reinterpret_cast<float *>(scratch);   // 32 rows x kPanelBoMax, reused
+        float *rowmul = tile + 32 * kPanelBoMax;              // FP8: the rows' scale factors
+        const int kpad = sd.kpad;
         for (int rb = max(r0, kmax); rb < r0 + myR; rb += 32) {
             const int nrow = min(32, r0 + myR - rb);
             __syncthreads();
@@ -586,13 +588,37 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                 tile[(size_t)r * kPanelBoMax + k] = (float)P[(size_t)(rb + r) + (size_t)k * lda];
             }
             __syncthreads();
-            for (int e = tid; e < nrow * kpad; e += kPanelThreads) {
-                const int r = e / kpad, k = e % kpad;
-                const float x = k < kmax ? tile[(size_t)r * kPanelBoMax + k] : 0.f;
-                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                __nv_bfloat16 *dst = stage + (size_t)(rb + r - kmax) * lds;
-                dst[k] = hi;
-                if (split) dst[kpad + k] = __float2bfloat16_rn(x - __bfloat162float(hi));
+            if (sd.fmt == 2) {
+                // one power-of-two scale per row: 16 threads per row reduce |x|
+                const int r = tid >> 4, sub = tid & 15;
+                float amax = 0.f;
+                if (r < nrow)
+                    for (int k = sub; k < kmax; k += 16) amax = fmaxf(amax, fabsf(tile[(size_t)r * kPanelBoMax + k]));
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                float inv;
+                const float mul = lu_fp8_scale(amax, &inv);
+                if (sub == 0 && r < nrow) {
+                    rowmul[r] = mul;
+                    sd.scale[rb + r - kmax] = inv;
+                }
+                __syncthreads();
+                unsigned char *st8 = static_cast<unsigned char *>(sd.ptr);
+                for (int e = tid; e < nrow * kpad; e += kPanelThreads) {
+                    const int rr = e / kpad, k = e % kpad;
+                    st8[(size_t)(rb + rr - kmax) * sd.lds + k] =
+                        k < kmax ? lu_to_e4m3(tile[(size_t)rr * kPanelBoMax + k] * rowmul[rr]) : (unsigned char)0;
+                }
+            } else {
+                __nv_bfloat16 *st16 = static_cast<__nv_bfloat16 *>(sd.ptr);
+                for (int e = tid; e < nrow * kpad; e += kPanelThreads) {
+                    const int r = e / kpad, k = e % kpad;
+                    const float x = k < kmax ? tile[(size_t)r * kPanelBoMax + k] : 0.f;
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                    __nv_bfloat16 *dst = st16 + (size_t)(rb + r - kmax) * sd.lds;
+                    dst[k] = hi;
+                    if (sd.fmt == 1) dst[kpad + k] = __float2bfloat16_rn(x - __bfloat162float(hi));
+                }
             }
         }
     }
@@ -647,8 +673,7 @@ static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap,
 
 template <typename T, int RPT>
 static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int bo, int bi, int R, int *ipiv,
-                              int row_base, int *info, int *map_out, int *perm, __nv_bfloat16 *stage, int lds, int kpad,
-                              int split, int *status, long long bound_ns) {
+                              int row_base, int *info, int *map_out, int *perm, StageDesc sd, int *status, long long bound_ns) {
     cudaError_t e = cudaFuncSetAttribute(panel_factor_cluster<T, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.dynamicSmemBytes);
     if (e != cudaSuccess) return e;
@@ -656,18 +681,18 @@ static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int
     if (e != cudaSuccess) return e;
     lu_count_launch();
     return cudaLaunchKernelEx(&cfg, panel_factor_cluster<T, RPT>, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out,
-                              perm, stage, lds, kpad, split, status, bound_ns);
+                              perm, sd, status, bound_ns);
 }
 
 // Host launcher: factor the m x bo panel at P with inner width bi; pivots into
 // ipiv[0..min(m,bo)) as row_base + local + 1; row map into map_out (may be
 // NULL); permutation vector update (may be NULL); optional BF16 staging of
-// L21 (stage rows 0.. = panel rows bo..; lds, kpad, split).  A column
+// L21 (stage rows 0.. = panel rows bo.., as described by sd).  A column
 // exchange that waits longer than bound_ns records LU_ERR_TIMEOUT in *status.
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
-                               int *perm, __nv_bfloat16 *stage, int lds, int kpad, int split, int max_ctas,
-                               size_t smem_cap, int *status, long long bound_ns, cudaStream_t s) {
+                               int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
+                               cudaStream_t s) {
     if (bi <= 0 || bo <= 0 || bo > kPanelBoMax || m <= 0) return cudaErrorInvalidValue;
     if (bi > bo) bi = bo;
     if (bi > kPanelWMax) return cudaErrorInvalidValue;
@@ -687,14 +712,10 @@ cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     switch (rows_per_thread(R)) {
-        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
-                                          status, bound_ns);
-        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
-                                          status, bound_ns);
-        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
-                                          status, bound_ns);
-        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, stage, lds, kpad, split,
-                                          status, bound_ns);
+        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
+        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
+        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
+        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -713,9 +734,9 @@ int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo) 
     return 0;
 }
 
-template cudaError_t launch_panel_outer<double>(double *, int, int, int, int, int *, int, int *, int *, int *,
-                                                __nv_bfloat16 *, int, int, int, int, size_t, int *, long long, cudaStream_t);
-template cudaError_t launch_panel_outer<float>(float *, int, int, int, int, int *, int, int *, int *, int *,
-                                               __nv_bfloat16 *, int, int, int, int, size_t, int *, long long, cudaStream_t);
+template cudaError_t launch_panel_outer<double>(double *, int, int, int, int, int *, int, int *, int *, int *, StageDesc,
+                                                int, size_t, int *, long long, cudaStream_t);
+template cudaError_t launch_panel_outer<float>(float *, int, int, int, int, int *, int, int *, int *, int *, StageDesc, int,
+                                               size_t, int *, long long, cudaStream_t);
 
 }  // namespace lu

@@ -43,7 +43,9 @@ struct SwapLayout {
 // For the column strip [c_begin + kStrip*blockIdx.x, ... ) within [c_begin, c_end):
 //   apply the row map (all rows of S), then, if do_trsm, solve
 //   X := trilu(L11)^{-1} X for the b panel rows (L11 = A[kb:kb+b, kb:kb+b])
-//   and store X back (and, if stage != NULL, as BF16 into stage[(c - stage_c0)*ldst + r]).
+//   and store X back (and, if sd.ptr != NULL, staged for the tensor-core update
+//   as column c - stage_c0 of the staging buffer: BF16, BF16 hi/lo or FP8 with
+//   a power-of-two scale per column).
 // The solve is blocked by DB = 32 rows.  In a diagonal block lane r of every
 // warp holds row r of L and of the warp's strip columns in registers; step k
 // broadcasts the finished x[k] with a shuffle and lanes r > k subtract
@@ -53,8 +55,7 @@ struct SwapLayout {
 template <typename T>
 __global__ void __launch_bounds__(kSwapThreads, 2)
 swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restrict__ map, int c_begin,
-                 int c_end, int do_trsm, __nv_bfloat16 *__restrict__ stage, int ldst, int stage_c0,
-                 int stage_k, int split) {
+                 int c_end, int do_trsm, StageDesc sd, int stage_c0) {
     constexpr int DB = TrsmBlk<T>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SwapLayout<T> lay(b);
@@ -159,21 +160,51 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
             __syncthreads();
         }
     }
+    if (sd.ptr && sd.fmt == 2) {
+        // FP8 staging: one power-of-two scale per column, 8 threads per column
+        float *colmul = reinterpret_cast<float *>(Lc);
+        const int c = tid >> 3, sub = tid & 7;
+        float amax = 0.f;
+        if (c < ncol)
+            for (int r = sub; r < b; r += 8) amax = fmaxf(amax, fabsf((float)V[(size_t)r * kVS + c]));
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        float inv;
+        const float mul = lu_fp8_scale(amax, &inv);
+        if (sub == 0 && c < ncol) {
+            colmul[c] = mul;
+            sd.scale[c0 + c - stage_c0] = inv;
+        }
+        __syncthreads();
+    }
+    const int kpad = sd.kpad;
     for (int e = tid; e < b * ncol; e += blockDim.x) {
         const int r = e % b, c = e / b;
         const T x = V[(size_t)r * kVS + c];
         A[(size_t)(kb + r) + (size_t)(c0 + c) * lda] = x;
-        if (stage) {
-            const __nv_bfloat16 hi = to_bf16(x);
-            stage[(size_t)(c0 + c - stage_c0) * ldst + r] = hi;
-            if (split) stage[(size_t)(c0 + c - stage_c0) * ldst + stage_k + r] = to_bf16((float)x - __bfloat162float(hi));
+        if (sd.ptr) {
+            const size_t col = (size_t)(c0 + c - stage_c0) * sd.lds;
+            if (sd.fmt == 2) {
+                static_cast<unsigned char *>(sd.ptr)[col + r] = lu_to_e4m3((float)x * reinterpret_cast<const float *>(Lc)[c]);
+            } else {
+                __nv_bfloat16 *st16 = static_cast<__nv_bfloat16 *>(sd.ptr);
+                const __nv_bfloat16 hi = to_bf16(x);
+                st16[col + r] = hi;
+                if (sd.fmt == 1) st16[col + kpad + r] = to_bf16((float)x - __bfloat162float(hi));
+            }
         }
     }
-    if (stage) {   // zero K padding (b < stage_k on a short last panel)
-        for (int e = tid; e < (stage_k - b) * ncol; e += blockDim.x) {
-            const int r = b + e % (stage_k - b), c = e / (stage_k - b);
-            stage[(size_t)(c0 + c - stage_c0) * ldst + r] = __float2bfloat16_rn(0.f);
-            if (split) stage[(size_t)(c0 + c - stage_c0) * ldst + stage_k + r] = __float2bfloat16_rn(0.f);
+    if (sd.ptr) {   // zero K padding (b < kpad on a short last panel)
+        for (int e = tid; e < (kpad - b) * ncol; e += blockDim.x) {
+            const int r = b + e % (kpad - b), c = e / (kpad - b);
+            const size_t col = (size_t)(c0 + c - stage_c0) * sd.lds;
+            if (sd.fmt == 2) {
+                static_cast<unsigned char *>(sd.ptr)[col + r] = 0;
+            } else {
+                __nv_bfloat16 *st16 = static_cast<__nv_bfloat16 *>(sd.ptr);
+                st16[col + r] = __float2bfloat16_rn(0.f);
+                if (sd.fmt == 1) st16[col + kpad + r] = __float2bfloat16_rn(0.f);
+            }
         }
     }
 }
@@ -184,8 +215,7 @@ size_t swap_trsm_smem_bytes(int b, size_t elem) {
 
 template <typename T>
 cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c_begin, int c_end,
-                             int do_trsm, __nv_bfloat16 *stage, int ldst, int stage_c0, int stage_k, int split,
-                             cudaStream_t s) {
+                             int do_trsm, StageDesc sd, int stage_c0, cudaStream_t s) {
     if (c_end <= c_begin) return cudaSuccess;
     size_t smem = swap_trsm_smem_bytes(b, sizeof(T));
     static bool attr_set[2] = {false, false};
@@ -195,12 +225,11 @@ cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c
         attr_set[sizeof(T) == 8] = true;
     }
     int grid = lu_ceil_div(c_end - c_begin, kStrip);
-    swap_trsm_kernel<T><<<grid, kSwapThreads, smem, s>>>(A, lda, kb, b, map, c_begin, c_end, do_trsm,
-                                                         stage, ldst, stage_c0, stage_k, split);
+    swap_trsm_kernel<T><<<grid, kSwapThreads, smem, s>>>(A, lda, kb, b, map, c_begin, c_end, do_trsm, sd, stage_c0);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_swap_trsm<double>(double *, int, int, int, const int *, int, int, int, __nv_bfloat16 *, int, int, int, int, cudaStream_t);
-template cudaError_t launch_swap_trsm<float>(float *, int, int, int, const int *, int, int, int, __nv_bfloat16 *, int, int, int, int, cudaStream_t);
+template cudaError_t launch_swap_trsm<double>(double *, int, int, int, const int *, int, int, int, StageDesc, int, cudaStream_t);
+template cudaError_t launch_swap_trsm<float>(float *, int, int, int, const int *, int, int, int, StageDesc, int, cudaStream_t);
 
 }  // namespace lu

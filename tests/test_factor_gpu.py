@@ -64,9 +64,13 @@ def test_schedule_invariance_bits():
         assert np.array_equal(LU, ref)
 
 
-@pytest.mark.parametrize("dtype,update", [("f64", 0), ("f32", 0), ("f32", 1), ("f32", 2)])
+@pytest.mark.parametrize("dtype,update", [("f64", 0), ("f32", 0), ("f32", 1), ("f32", 2), ("f32", 3)])
 @pytest.mark.parametrize("n", [40, 300, 1030])
 def test_dyadic_exact_all_paths(n, dtype, update):
+    """L entries k/8 and U integers in [-8, 8] are exact in FP64, FP32, BF16
+    and e4m3, so every path, the FP8 update included, recovers P, L, U exactly
+    (for FP8 this also shows that the tensor cores accumulate these products
+    exactly in FP32)."""
     A, perm, L, U = li.dyadic_plu(n, seed=500 + n)
     LU, ipiv, info, _, _ = factor_gpu(A, dtype, update=update)
     assert info == 0
@@ -143,7 +147,7 @@ def test_f32_bf16x3_update_backward_error(oracle_mod):
     assert np.max(np.abs(np.tril(LU, -1))) <= 1.0
 
 
-@pytest.mark.parametrize("update", [1, 2])
+@pytest.mark.parametrize("update", [1, 2, 3])
 def test_f32_tc_update_large_lookahead_invariance(update):
     """The tensor-core path under look-ahead on and off gives identical bits."""
     A = li.uniform(2304, 2304, seed=16)

@@ -54,6 +54,69 @@ def test_trailing_update_bf16_vs_fp32_reference(m, n, k, split):
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
 
 
+def _e4m3(x):
+    """Round to nearest (ties to even) onto the e4m3 grid: 3 fraction bits,
+    normal exponents down to -6, subnormal quantum 2^-9, largest value 448."""
+    x = np.asarray(x, dtype=np.float64)
+    ax = np.abs(x)
+    e = np.floor(np.log2(np.where(ax > 0, ax, 1.0)))
+    q = 2.0 ** (np.maximum(e, -6.0) - 3.0)
+    return np.sign(x) * np.minimum(np.round(ax / q) * q, 448.0)
+
+
+def _pow2_to_448(amax):
+    """The power of two 2^e with the largest e such that amax * 2^e <= 448."""
+    amax = np.asarray(amax, dtype=np.float64)
+    mant, q = np.frexp(np.where(amax > 0, amax, 1.0))
+    e = np.where(mant <= 0.875, 9 - q, 8 - q)
+    e = np.clip(np.where(amax > 0, e, 0), -126, 126)
+    return 2.0 ** e
+
+
+def test_pow2_scale_definition():
+    """The scale puts the largest magnitude in (224, 448]."""
+    amax = np.array([1.0, 0.875, 0.876, 448.0, 449.0, 3e-5, 7.0])
+    s = _pow2_to_448(amax)
+    assert np.all(amax * s <= 448.0) and np.all(amax * s > 224.0)
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 256), (1000, 77, 100), (5, 3, 16), (700, 900, 192)])
+def test_trailing_update_fp8_vs_reference(m, n, k):
+    """C - A B with each row of A and each column of B scaled by a power of two
+    into the e4m3 range, rounded to e4m3, multiplied in FP32 and unscaled:
+    products of two e4m3 values are exact in FP32 and the scales are exact, so
+    the only difference from the exact sum of the same products is the FP32
+    accumulation."""
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    A = li.uniform(m, k, seed=11 + m)
+    B = li.uniform(k, n, seed=12 + n)
+    C = li.uniform(m, n, seed=13 + k)
+    A[0, :] *= 1e-3                                   # rows and columns of different magnitudes
+    B[:, 0] *= 37.0
+    dA = li.to_device_colmajor(A, dev(), torch.float32)
+    dB = li.to_device_colmajor(B, dev(), torch.float32)
+    dC = li.to_device_colmajor(C, dev(), torch.float32)
+    lu.lu_trailing_update(lu.LU_UPDATE_FP8, dA, dB, dC, m, n, k)
+    torch.cuda.synchronize()
+    got = li.from_device_colmajor(dC, m)
+    A32 = A.astype(np.float32).astype(np.float64)
+    B32 = B.astype(np.float32).astype(np.float64)
+    C32 = C.astype(np.float32).astype(np.float64)
+    sa = _pow2_to_448(np.max(np.abs(A32), axis=1))
+    sb = _pow2_to_448(np.max(np.abs(B32), axis=0))
+    qa = _e4m3(A32 * sa[:, None])
+    qb = _e4m3(B32 * sb[None, :])
+    prod = (qa @ qb) / sa[:, None] / sb[None, :]
+    mag = (np.abs(qa) @ np.abs(qb)) / sa[:, None] / sb[None, :]
+    ref = C32 - prod
+    bound = k * 2.0 ** -23 * mag + 2.0 ** -23 * np.abs(ref) + 1e-30
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+    # e4m3 keeps 4 significant bits: the product is within 2^-3 of the FP32 one, relative to |A||B|
+    assert np.max(np.abs(prod - A32 @ B32) / (np.abs(A32) @ np.abs(B32) + 1e-30)) <= 2.0 ** -3
+
+
 def test_trailing_update_native_fp32():
     import torch
 
@@ -106,6 +169,24 @@ def test_mixed_kappa_ladder(oracle_mod, kappa, rung_max):
     assert rep.rung <= rung_max
     # forward error within kappa * eta (with a safety factor)
     assert np.max(np.abs(X - xt)) / np.max(np.abs(xt)) <= 100 * kappa * max(eta, 1e-16)
+
+
+@pytest.mark.parametrize("kind,rung_max", [("dominant", 0), ("kappa10", 1), ("kappa1e3", 2)])
+def test_mixed_fp8_update(oracle_mod, kind, rung_max):
+    """With the FP8 update (4 significant bits per operand) the FP32 factors
+    are a weak preconditioner: classic refinement converges on a diagonally
+    dominant matrix, GMRES-IR on a kappa = 10 matrix, and a kappa = 1e3 matrix
+    may need the FP64 factorization.  Every rung ends at eta <= 1e-14."""
+    import paper_1611_06365_gb300 as lu
+    n = 600
+    if kind == "dominant":
+        A = li.diag_dominant(n, seed=li.BASE_SEED + 2140)
+    else:
+        A = li.kappa_matrix(n, 10.0 if kind == "kappa10" else 1e3, seed=li.BASE_SEED + 2150, k=n)
+    B = A @ np.ones((n, 1))
+    X, rep = _mixed(A, B, update=lu.LU_UPDATE_FP8)
+    eta = oracle_mod.backward_error(A, X, B)
+    assert eta <= 1e-14 and rep.rung <= rung_max, (rep.as_dict(), eta)
 
 
 def test_mixed_kappa_1e12_falls_back(oracle_mod):
