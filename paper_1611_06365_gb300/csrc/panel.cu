@@ -117,6 +117,19 @@ __device__ __forceinline__ void warp_argmax_key(unsigned long long &key, int &id
     key = ((unsigned long long)mh << 32) | ml;
 }
 
+// The same for keys that fit in 32 bits (FP32 magnitudes): two reductions.
+__device__ __forceinline__ void warp_argmax_key32(unsigned long long &key, int &idx) {
+    const unsigned k32 = (unsigned)key;
+    const unsigned mk = __reduce_max_sync(0xffffffffu, k32);
+    idx = (int)__reduce_min_sync(0xffffffffu, k32 == mk ? (unsigned)idx : 0xffffffffu);
+    key = mk;
+}
+template <typename T>
+__device__ __forceinline__ void warp_argmax_t(unsigned long long &key, int &idx) {
+    if constexpr (sizeof(T) == 4) warp_argmax_key32(key, idx);
+    else warp_argmax_key(key, idx);
+}
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // Address of the same shared-memory location in CTA `rank` of the cluster.
@@ -353,7 +366,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             const int par = j & 1;
             const unsigned mb = smem_u32(&S.mbar[par]);
             if (tid == 0) mbar_arrive_expect(mb, xbytes);
-            warp_argmax_key(best, bidx);
+            warp_argmax_t<T>(best, bidx);
             // the lane holding the warp's candidate stages it; the owner of row j stages row j
             if (bidx != INT_MAX && lane == ((bidx - r0) & 31))
                 stage_tile_row<T, RPT, BI>(a, (bidx - r0) / kPanelThreads, S.wst[par][warp]);
@@ -365,7 +378,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             // every warp reduces the warp candidates itself (no second barrier)
             unsigned long long ckey = lane < kPanelWarps ? S.red_key[par][lane] : 0ULL;
             int crow = lane < kPanelWarps ? S.red_idx[par][lane] : INT_MAX;
-            warp_argmax_key(ckey, crow);
+            warp_argmax_t<T>(ckey, crow);
             // push header, candidate row and row j into every CTA, 16 bytes per store
             {
                 const int ndiag = own_j ? nvec : 0;
@@ -393,10 +406,11 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             }
             mbar_wait_bounded(mb, (unsigned)(j >> 1) & 1u, &S.abort, status, bound_ns);
             // winner from the local copies, reduced by every warp (no barrier)
-            unsigned long long wk = lane < C ? S.cand[par][lane].key : 0ULL;
-            int ix = lane < C ? S.cand[par][lane].row : INT_MAX;
+            const int4 hdr = lane < C ? *reinterpret_cast<const int4 *>(&S.cand[par][lane]) : make_int4(0, 0, INT_MAX, 0);
+            unsigned long long wk = ((unsigned long long)(unsigned)hdr.y << 32) | (unsigned)hdr.x;
+            int ix = hdr.z;
             const int mine = ix;
-            warp_argmax_key(wk, ix);
+            warp_argmax_t<T>(wk, ix);
             const bool valid = (ix != INT_MAX);
             const int src = valid ? __ffs(__ballot_sync(0xffffffffu, mine == ix)) - 1 : 0;
             const int p = valid ? ix : j;   // every candidate NaN: keep row j, as a sequential scan would
