@@ -71,6 +71,18 @@ __device__ __forceinline__ void bb_warp_argmax(unsigned long long &key, int &idx
     key = ((unsigned long long)mh << 32) | ml;
 }
 
+__device__ __forceinline__ void bb_warp_argmax32(unsigned long long &key, int &idx) {
+    const unsigned k32 = (unsigned)key;
+    const unsigned mk = __reduce_max_sync(0xffffffffu, k32);
+    idx = (int)__reduce_min_sync(0xffffffffu, k32 == mk ? (unsigned)idx : 0xffffffffu);
+    key = mk;
+}
+template <typename T>
+__device__ __forceinline__ void bb_argmax_t(unsigned long long &key, int &idx) {
+    if constexpr (sizeof(T) == 4) bb_warp_argmax32(key, idx);
+    else bb_warp_argmax(key, idx);
+}
+
 // Column step LJ of the panel on this thread's row i (panel-local): scaling
 // and rank-1 update for i > LJ, and the candidate key of column LJ+1.
 template <typename T, int NB, int LJ>
@@ -130,7 +142,7 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
         for (int lj = 0; lj < w; ++lj) {
             const int par = colstep & 1;
             ++colstep;
-            bb_warp_argmax(best, bidx);
+            bb_argmax_t<T>(best, bidx);
             if (bidx != INT_MAX && lane == (bidx & 31)) {
 #pragma unroll
                 for (int q = 0; q < NB / VEC; ++q) reinterpret_cast<V *>(S.wst[par][warp])[q] = reinterpret_cast<const V *>(a)[q];
@@ -143,7 +155,7 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
             __syncthreads();
             unsigned long long ck = lane < kBBWarps ? S.red_key[par][lane] : 0ULL;
             int cr = lane < kBBWarps ? S.red_idx[par][lane] : INT_MAX;
-            bb_warp_argmax(ck, cr);
+            bb_argmax_t<T>(ck, cr);
             const bool valid = cr != INT_MAX;
             const int p = valid ? cr : lj;   // no candidate (all NaN): keep row lj
             const T *urow = valid ? S.wst[par][cr >> 5] : S.jst[par];
@@ -178,6 +190,10 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
             const int nother = n - w;   // columns [0, k) and [k + w, n)
             for (int cc = tid; cc < nother; cc += kBBThreads) {
                 T *colp = A + (size_t)(cc < k ? cc : cc + w) * lda + k;
+                // bring the column's rows k..n-1 into L1 first: the interchanges
+                // below are a dependent chain of loads and stores
+                for (int r = 0; r < m; r += 128 / (int)sizeof(T))
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(colp + r));
                 for (int j = 0; j < w; ++j) {
                     const int q = S.piv[j];
                     if (q != j) {
@@ -197,23 +213,24 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
             T lrow[NB];
 #pragma unroll
             for (int q = 0; q < NB / VEC; ++q) reinterpret_cast<V *>(lrow)[q] = reinterpret_cast<const V *>(S.L21[r < w ? r : 0])[q];
-            for (int cb = warp * 4; cb < nc; cb += kBBWarps * 4) {
-                T x[4];
+            constexpr int TC = 4;   // columns per warp pass
+            for (int cb = warp * TC; cb < nc; cb += kBBWarps * TC) {
+                T x[TC];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < TC; ++u)
                     x[u] = (r < w && cb + u < nc) ? A[(size_t)(k + r) + (size_t)(k + w + cb + u) * lda] : T(0);
 #pragma unroll
                 for (int q = 0; q < NB - 1; ++q) {
                     if (q + 1 < w) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < TC; ++u) {
                             const T xq = __shfl_sync(0xffffffffu, x[u], q);
                             if (r > q) x[u] = fma(-lrow[q], xq, x[u]);
                         }
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < TC; ++u) {
                     if (cb + u < nc) {
                         if (r < w) A[(size_t)(k + r) + (size_t)(k + w + cb + u) * lda] = x[u];
                         if (r < NB) S.U12[cb + u][r] = r < w ? x[u] : T(0);
@@ -233,37 +250,36 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
 #pragma unroll
                 for (int q = 0; q < NB / VEC; ++q) reinterpret_cast<V *>(l)[q] = reinterpret_cast<const V *>(S.L21[w + r])[q];
                 T *rowp = A + (size_t)(k + w + r) + (size_t)(k + w) * lda;
-                int c = g;
-                for (; c + G < nc; c += 2 * G) {
-                    T x0 = rowp[(size_t)c * lda], x1 = rowp[(size_t)(c + G) * lda];
-                    const T *u0 = S.U12[c], *u1 = S.U12[c + G];
+                // four columns (c, c+G, c+2G, c+3G) per step; the next four are
+                // loaded before this step's products (software pipelining)
+                constexpr int CG = 4;
+                T xc[CG], xn[CG];
+#pragma unroll
+                for (int v = 0; v < CG; ++v) xc[v] = g + v * G < nc ? rowp[(size_t)(g + v * G) * lda] : T(0);
+                for (int c = g; c < nc; c += CG * G) {
+#pragma unroll
+                    for (int v = 0; v < CG; ++v) {
+                        const int cn = c + (CG + v) * G;
+                        xn[v] = cn < nc ? rowp[(size_t)cn * lda] : T(0);
+                    }
 #pragma unroll
                     for (int q = 0; q < NB / VEC; ++q) {
-                        V v0 = reinterpret_cast<const V *>(u0)[q], v1 = reinterpret_cast<const V *>(u1)[q];
-                        const T *p0 = reinterpret_cast<const T *>(&v0), *p1 = reinterpret_cast<const T *>(&v1);
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            if (q * VEC + v < w) {
-                                x0 = fma(-l[q * VEC + v], p0[v], x0);
-                                x1 = fma(-l[q * VEC + v], p1[v], x1);
-                            }
+                        for (int v = 0; v < CG; ++v) {
+                            const int cv = c + v * G;
+                            V uv = reinterpret_cast<const V *>(S.U12[cv < nc ? cv : 0])[q];
+                            const T *up = reinterpret_cast<const T *>(&uv);
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e)
+                                if (q * VEC + e < w) xc[v] = fma(-l[q * VEC + e], up[e], xc[v]);
                         }
                     }
-                    rowp[(size_t)c * lda] = x0;
-                    rowp[(size_t)(c + G) * lda] = x1;
-                }
-                if (c < nc) {
-                    T x0 = rowp[(size_t)c * lda];
-                    const T *u0 = S.U12[c];
 #pragma unroll
-                    for (int q = 0; q < NB / VEC; ++q) {
-                        V v0 = reinterpret_cast<const V *>(u0)[q];
-                        const T *p0 = reinterpret_cast<const T *>(&v0);
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            if (q * VEC + v < w) x0 = fma(-l[q * VEC + v], p0[v], x0);
+                    for (int v = 0; v < CG; ++v) {
+                        const int cv = c + v * G;
+                        if (cv < nc) rowp[(size_t)cv * lda] = xc[v];
+                        xc[v] = xn[v];
                     }
-                    rowp[(size_t)c * lda] = x0;
                 }
             }
         }
@@ -272,8 +288,10 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
     return info;
 }
 
+// two CTAs per SM; three for FP32 with 16-column panels (fewer registers and
+// less shared memory), so more matrices are in flight to hide L2 latency
 template <typename T, int NB>
-__global__ void __launch_bounds__(kBBThreads, 2)
+__global__ void __launch_bounds__(kBBThreads, (sizeof(T) == 4 && NB == 16) ? 3 : 2)
 getrf_batched_blocked(const int *__restrict__ ns, T *const *__restrict__ As, const int *__restrict__ ldas,
                       int *const *__restrict__ ipivs, int *__restrict__ infos, const int *__restrict__ order, int count,
                       int *__restrict__ queue) {
@@ -455,13 +473,13 @@ static cudaError_t launch_bb(int batch, const int *ns, T *const *As, const int *
 }
 
 // Blocked batched factorization for max_n <= 256; nb = panel width (16 or
-// 32; 0 picks 32 for FP32, 16 for FP64).  ws: batched_blocked_workspace_ints
+// 32; 0 picks 16: the panel's per-column chain is the latency that matters).  ws: batched_blocked_workspace_ints
 // ints of device memory.
 template <typename T>
 cudaError_t launch_getrf_batched_blocked(int batch, const int *ns, T *const *As, const int *ldas, int *const *ipivs,
                                          int *infos, int nb, int *ws, int sms, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
-    if (nb == 0) nb = sizeof(T) == 4 ? 32 : 16;
+    if (nb == 0) nb = 16;
     if (nb == 32) return launch_bb<T, 32>(batch, ns, As, ldas, ipivs, infos, ws, sms, s);
     if (nb == 16) return launch_bb<T, 16>(batch, ns, As, ldas, ipivs, infos, ws, sms, s);
     return cudaErrorInvalidValue;
