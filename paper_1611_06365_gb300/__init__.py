@@ -137,11 +137,20 @@ def _check(name, rc):
     return rc
 
 
+def _ld(t):
+    """Leading dimension of a column-major (n_cols, ld) tensor.  With a single
+    column the stride of dimension 0 is arbitrary in torch (any value is
+    contiguous), so the column length is used."""
+    if t.dim() != 2:
+        return t.shape[0]
+    return t.stride(0) if t.shape[0] > 1 else max(t.shape[1], 1)
+
+
 def _cm_dims(A, n=None):
     """(n, ld) of a column-major tensor of shape (n_cols, ld)."""
-    if A.dim() != 2 or A.stride(1) != 1:
+    if A.dim() != 2 or (A.stride(1) != 1 and A.shape[1] > 1):
         raise ValueError("column-major matrix expected: a (n_cols, ld) tensor with unit inner stride")
-    return (A.shape[0] if n is None else n), A.stride(0)
+    return (A.shape[0] if n is None else n), _ld(A)
 
 
 def lu_factor(A, ipiv, info, n=None, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0,
@@ -157,7 +166,7 @@ def lu_solve(LU, ipiv, B, n=None, nrhs=None, *, stream=None):
     """B := A^{-1} B with the factors of lu_factor.  B: column-major (nrhs, ldb)."""
     n, lda = _cm_dims(LU, n)
     nrhs = B.shape[0] if nrhs is None else nrhs
-    ldb = B.stride(0) if B.dim() == 2 else B.shape[0]
+    ldb = _ld(B)
     return _check("lu_solve", lib().lu_solve(_dtype_code(LU), n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B), ldb,
                                               _stream(stream)))
 
@@ -169,7 +178,7 @@ def lu_solve_noalloc(LU, ipiv, B, n=None, nrhs=None, *, status=None, stream=None
     latency-critical loops).  Calls that overlap on the GPU must not share it."""
     n, lda = _cm_dims(LU, n)
     nrhs = B.shape[0] if nrhs is None else nrhs
-    ldb = B.stride(0) if B.dim() == 2 else B.shape[0]
+    ldb = _ld(B)
     return _check("lu_solve_noalloc", lib().lu_solve_noalloc(_dtype_code(LU), n, nrhs, _ptr(LU), lda, _ptr(ipiv),
                                                               _ptr(B), ldb, _ptr(status), _stream(stream)))
 
@@ -200,15 +209,15 @@ def lu_solve_mixed(A, B, X, n=None, *, update=LU_UPDATE_BF16X3, nb=0, max_iter=0
     nrhs = B.shape[0]
     o = MixedOpts(update, nb, max_iter, tol, allow_gmres, allow_fallback, gmres_restart, fp64_factor)
     rep = MixedReport()
-    _check("lu_solve_mixed", lib().lu_solve_mixed(n, nrhs, _ptr(A), lda, _ptr(B), B.stride(0), _ptr(X), X.stride(0),
+    _check("lu_solve_mixed", lib().lu_solve_mixed(n, nrhs, _ptr(A), lda, _ptr(B), _ld(B), _ptr(X), _ld(X),
                                                   ctypes.byref(o), ctypes.byref(rep), _stream(stream)))
     return rep
 
 
 def lu_trailing_update(update, A, B, C, m, n, k, *, stream=None):
     """C := C - A B (FP32 column-major tensors: A (k, lda), B (n, ldb), C (n, ldc))."""
-    return _check("lu_trailing_update", lib().lu_trailing_update(update, m, n, k, _ptr(A), A.stride(0), _ptr(B),
-                                                                  B.stride(0), _ptr(C), C.stride(0), _stream(stream)))
+    return _check("lu_trailing_update", lib().lu_trailing_update(update, m, n, k, _ptr(A), _ld(A), _ptr(B),
+                                                                  _ld(B), _ptr(C), _ld(C), _stream(stream)))
 
 
 def lu_workspace_size(routine: str, n: int, nrhs: int, dtype_code: int) -> int:
