@@ -279,6 +279,25 @@ typedef struct {
 int lu_trace(int enable);
 int lu_trace_read(lu_trace_event *out, int max_events);
 
+/*
+ * lu_wait_selftest -- exercises the bounded device waits without any fault:
+ * launches the blocked forward substitution on a 128 x 128 triangle with
+ * the first row block withheld, so the second block's wait for it runs out
+ * after bound_ns of GPU time.  Returns the status the kernel recorded
+ * (LU_ERR_TIMEOUT when the bound works), synchronizing the stream; a
+ * negative argument / CUDA error code otherwise.  The device stays usable.
+ */
+int lu_wait_selftest(long long bound_ns, void *stream);
+
+/*
+ * lu_div_selftest -- compares the substitutions' correctly rounded quotient
+ * (Markstein's correction from a precomputed reciprocal) with the IEEE
+ * division on `count` hashed operand pairs of type dt (seed selects them).
+ * Returns the number of pairs whose results differ in any bit (0 expected),
+ * synchronizing the stream; negative on an argument or CUDA error.
+ */
+long long lu_div_selftest(lu_dtype dt, long long count, unsigned long long seed, void *stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded. */
 long long lu_kernel_launches(void);
 

@@ -23,7 +23,7 @@ __all__ = [
     "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8", "LuError", "lib", "build",
     "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status",
-    "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_kernel_launches", "to_colmajor", "from_colmajor", "MixedReport",
+    "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches", "to_colmajor", "from_colmajor", "MixedReport",
 ]
 
 LU_F64, LU_F32 = 0, 1
@@ -98,6 +98,10 @@ def lib():
         L.lu_update_timing_read.argtypes = [ctypes.POINTER(ctypes.c_longlong)] + [ctypes.POINTER(ctypes.c_double)] * 3
         L.lu_update_timing_read.restype = i
         L.lu_kernel_launches.restype = ctypes.c_longlong
+        L.lu_div_selftest.argtypes = [i, ctypes.c_longlong, ctypes.c_ulonglong, vp]
+        L.lu_div_selftest.restype = ctypes.c_longlong
+        L.lu_wait_selftest.argtypes = [ctypes.c_longlong, vp]
+        L.lu_wait_selftest.restype = i
         L.lu_trace.argtypes = [i]
         L.lu_trace.restype = i
         L.lu_trace_read.argtypes = [ctypes.POINTER(TraceEvent), i]
@@ -261,6 +265,16 @@ def lu_trace_read(max_events: int = 1 << 20):
     _check("lu_trace_read", n if n < 0 else 0)
     return [dict(kind=LU_TRACE_KINDS[e.kind], step=e.step, stream=e.stream, t0=e.t_start_ms, t1=e.t_end_ms)
             for e in buf[:n]]
+
+
+def lu_wait_selftest(bound_ns: int, stream=None) -> int:
+    """Status recorded by a forward substitution whose first block is withheld (LU_ERR_TIMEOUT expected)."""
+    return lib().lu_wait_selftest(int(bound_ns), _stream(stream))
+
+
+def lu_div_selftest(dtype_code: int, count: int, seed: int = 1, stream=None) -> int:
+    """Pairs on which the substitutions' quotient differs from IEEE division (0 expected)."""
+    return lib().lu_div_selftest(dtype_code, int(count), int(seed), _stream(stream))
 
 
 def lu_kernel_launches() -> int:

@@ -75,6 +75,10 @@ template <typename T>
 cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status, long long bound_ns,
                              int sms, cudaStream_t s);
 size_t trsv_workspace_ints(int n, int nrhs);
+cudaError_t launch_trsv_timeout_selftest(const float *LU, int n, float *X, int *ws, int *status, long long bound_ns,
+                                         cudaStream_t s);
+cudaError_t launch_div_selftest(int dt64, long long count, unsigned long long seed, unsigned long long *mismatch,
+                                cudaStream_t s);
 cudaError_t launch_iota(int *v, int n, cudaStream_t s);
 // batched_blocked.cu
 constexpr int kBatchedBlockedMaxN = 256;
@@ -709,6 +713,44 @@ const char *lu_status_string(int code) {
     }
     if (code < 0 && code > -100) return "invalid argument (return value -i names argument i)";
     return "unknown status";
+}
+
+int lu_wait_selftest(long long bound_ns, void *stream) {
+    if (bound_ns <= 0) return -1;
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = 2 * 64;   // two row blocks: block 1 waits on block 0, which nobody solves
+    Workspace ws(s);
+    float *LU = nullptr, *X = nullptr;
+    int *tw = nullptr, *status = nullptr;
+    LU_CUDA_TRY(ws.get(&LU, (size_t)n * n));
+    LU_CUDA_TRY(ws.get(&X, (size_t)n));
+    LU_CUDA_TRY(ws.get(&tw, trsv_workspace_ints(n, 1)));
+    LU_CUDA_TRY(ws.get(&status, 1));
+    LU_CUDA_TRY(cudaMemsetAsync(LU, 0, sizeof(float) * n * n, s));
+    LU_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(float) * n, s));
+    LU_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    LU_CUDA_TRY(launch_trsv_timeout_selftest(LU, n, X, tw, status, bound_ns, s));
+    int v = 0;
+    LU_CUDA_TRY(cudaMemcpyAsync(&v, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaStreamSynchronize(s));
+    return v;
+}
+
+long long lu_div_selftest(lu_dtype dt, long long count, unsigned long long seed, void *stream) {
+    if (dt != LU_F64 && dt != LU_F32) return -1;
+    if (count < 0) return -2;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    unsigned long long *bad = nullptr;
+    LU_CUDA_TRY(ws.get(&bad, 1));
+    LU_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+    LU_CUDA_TRY(launch_div_selftest(dt == LU_F64, count, seed, bad, s));
+    unsigned long long h = 0;
+    LU_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaStreamSynchronize(s));
+    return (long long)h;
 }
 
 int lu_last_device_status(void *stream, int reset) {

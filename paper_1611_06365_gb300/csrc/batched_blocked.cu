@@ -421,13 +421,38 @@ getrs_batched_warp(int batch, int nrhs, const int *__restrict__ ns, const T *con
                             if (c4 * VEC + v < cols) acc = fma(-u[c4 * VEC + v], xp[v], acc);
                     }
                 } else {
-                    // diagonal block: lane c holds u(r, r) in u[lane]
+                    // diagonal block: lane c holds u(r, r) in u[lane]; its reciprocal off the
+                    // chain, lu_div_fast on the chain, the IEEE division again if any lane's
+                    // division left the safe range
+                    T dg = u[0];
+#pragma unroll
+                    for (int c = 1; c < 32; ++c)
+                        if (lane == c) dg = u[c];
+                    if (!has) dg = T(1);
+                    const T rdg = T(1) / dg;
+                    const bool okd = lu_div_range<T>::in(dg);
+                    const T acc0 = acc;
+                    T pre = T(0);   // the operand of this lane's division, checked after the chain
 #pragma unroll
                     for (int c = 31; c >= 0; --c) {
                         if (c < cols) {
-                            if (lane == c) acc = acc / u[c];
+                            if (lane == c) {
+                                pre = acc;
+                                acc = lu_div_fast(acc, dg, rdg);
+                            }
                             const T xc = __shfl_sync(0xffffffffu, acc, c);
                             if (lane < c) acc = fma(-u[c], xc, acc);
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, has && !lu_div_safe(pre, okd))) {
+                        acc = acc0;
+#pragma unroll
+                        for (int c = 31; c >= 0; --c) {
+                            if (c < cols) {
+                                if (lane == c) acc = acc / dg;
+                                const T xc = __shfl_sync(0xffffffffu, acc, c);
+                                if (lane < c) acc = fma(-u[c], xc, acc);
+                            }
                         }
                     }
                 }

@@ -114,3 +114,39 @@ __device__ __forceinline__ float lu_fp8_scale(float amax, float *inv) {
 __device__ __forceinline__ unsigned char lu_to_e4m3(float x) {
     return (unsigned char)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
 }
+
+// Correctly rounded quotient x / d on a latency-critical chain, from a
+// reciprocal computed beforehand off the chain: Markstein's correction
+// (P. Markstein, "Computation of elementary functions on the IBM RISC
+// System/6000 processor", IBM J. Res. Dev. 34(1), 1990): with rcp = RN(1/d)
+// and q = RN(x * rcp) (within one ulp of x / d), the residual e = x - q d is
+// exact in one fused multiply-add and RN(q + e rcp) = RN(x / d).  The
+// theorem needs no overflow or underflow in these steps: lu_div_safe tells
+// whether |d| and |x| (or x = 0) lie well inside the exponent range; callers
+// redo the rare unsafe cases with the IEEE division.
+template <typename T> struct lu_div_range;
+template <> struct lu_div_range<float> {
+    static constexpr unsigned lo = (127u - 60u) << 23, hi = (127u + 60u) << 23;   // 2^-60 .. 2^60
+    __device__ static bool in(float v) {
+        const unsigned b = __float_as_uint(v) & 0x7fffffffu;
+        return b >= lo && b < hi;
+    }
+};
+template <> struct lu_div_range<double> {
+    static constexpr unsigned long long lo = (1023ull - 500ull) << 52, hi = (1023ull + 500ull) << 52;   // 2^-500 .. 2^500
+    __device__ static bool in(double v) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+        return b >= lo && b < hi;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ bool lu_div_safe(T x, bool ok_d) {
+    return ok_d && (x == T(0) || lu_div_range<T>::in(x));
+}
+
+template <typename T>
+__device__ __forceinline__ T lu_div_fast(T x, T d, T rcp) {
+    const T q = x * rcp;
+    return fma(fma(-q, d, x), rcp, q);
+}

@@ -254,16 +254,52 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
                 }
             }
         } else {
+            // the diagonal of this lane's two rows and its reciprocals, off the chain;
+            // the chain divides with lu_div_fast, and a block where any division was
+            // outside its safe range is solved again with the IEEE division
+            const T d0 = has0 ? Dg[lane * kTB + lane] : T(1), d1 = has1 ? Dg[(lane + 32) * kTB + lane + 32] : T(1);
+            const T rc0 = T(1) / d0, rc1 = T(1) / d1;
+            const bool ok0 = lu_div_range<T>::in(d0), ok1 = lu_div_range<T>::in(d1);
+            T s0[NQ], s1[NQ], p0[NQ], p1[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) { s0[q] = x0[q]; s1[q] = x1[q]; p0[q] = T(0); p1[q] = T(0); }
             for (int jj = rows - 1; jj >= 0; --jj) {
-                const T d = Dg[jj * kTB + jj];
                 const T l0 = Dg[jj * kTB + lane], l1 = Dg[jj * kTB + lane + 32];
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    if (jj < 32 && lane == jj) x0[q] = x0[q] / d;
-                    if (jj >= 32 && lane + 32 == jj) x1[q] = x1[q] / d;
+                    if (jj < 32 && lane == jj) {
+                        p0[q] = x0[q];
+                        x0[q] = lu_div_fast(x0[q], d0, rc0);
+                    }
+                    if (jj >= 32 && lane + 32 == jj) {
+                        p1[q] = x1[q];
+                        x1[q] = lu_div_fast(x1[q], d1, rc1);
+                    }
                     const T y = __shfl_sync(0xffffffffu, jj < 32 ? x0[q] : x1[q], jj & 31);
                     if (lane < jj) x0[q] = fma(-l0, y, x0[q]);
                     if (lane + 32 < jj) x1[q] = fma(-l1, y, x1[q]);
+                }
+            }
+            // the divisions' operands, checked once after the chain
+            bool unsafe = false;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if (has0 && !lu_div_safe(p0[q], ok0)) unsafe = true;
+                if (has1 && !lu_div_safe(p1[q], ok1)) unsafe = true;
+            }
+            if (__any_sync(0xffffffffu, unsafe)) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) { x0[q] = s0[q]; x1[q] = s1[q]; }
+                for (int jj = rows - 1; jj >= 0; --jj) {
+                    const T l0 = Dg[jj * kTB + lane], l1 = Dg[jj * kTB + lane + 32];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        if (jj < 32 && lane == jj) x0[q] = x0[q] / d0;
+                        if (jj >= 32 && lane + 32 == jj) x1[q] = x1[q] / d1;
+                        const T y = __shfl_sync(0xffffffffu, jj < 32 ? x0[q] : x1[q], jj & 31);
+                        if (lane < jj) x0[q] = fma(-l0, y, x0[q]);
+                        if (lane + 32 < jj) x1[q] = fma(-l1, y, x1[q]);
+                    }
                 }
             }
         }
@@ -285,9 +321,45 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
     }
 }
 
+// The same permutation by the plain sequential scan, with the row contents
+// (cont[i]: the original row now at position i) in shared memory: one thread
+// applies the interchanges in order; the others stage the next chunk of
+// ipiv.  n + kPermChunk ints of shared memory.
+constexpr int kPermChunk = 2048;
+__global__ void __launch_bounds__(1024) ipiv_to_perm_smem(const int *__restrict__ ipiv, int n, int *__restrict__ perm) {
+    extern __shared__ int psm[];
+    int *cont = psm, *pv = psm + n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cont[i] = i;
+    for (int c0 = 0; c0 < n; c0 += kPermChunk) {
+        const int cn = min(kPermChunk, n - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cn; i += blockDim.x) pv[i] = ipiv[c0 + i] - 1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int j = 0; j < cn; ++j) {
+                const int p = pv[j], jj = c0 + j;
+                if (p != jj) {
+                    const int t = cont[jj];
+                    cont[jj] = cont[p];
+                    cont[p] = t;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = cont[i];
+}
+
 cudaError_t launch_ipiv_to_perm(const int *ipiv, int n, int *perm, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    ipiv_to_perm_kernel<<<1, 256, 0, s>>>(ipiv, n, perm);
+    const size_t smem = sizeof(int) * ((size_t)n + kPermChunk);
+    if (smem <= 220 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(ipiv_to_perm_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ipiv_to_perm_smem<<<1, 1024, smem, s>>>(ipiv, n, perm);
+    } else {
+        ipiv_to_perm_kernel<<<1, 256, 0, s>>>(ipiv, n, perm);
+    }
     lu_count_launch();
     return cudaGetLastError();
 }
@@ -352,6 +424,78 @@ cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ld
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Self-test of the bounded waits: the forward substitution of an n x n unit
+// lower triangle with the ticket of block 0 already taken, so no warp ever
+// solves block 0 and every other block's poll of its words runs out after
+// bound_ns.  The kernel then records LU_ERR_TIMEOUT in *status and returns;
+// nothing faults and the context stays usable.  ws: trsv_workspace_ints(n, 1)
+// ints; LU and X: n x n and n elements of FP32.
+cudaError_t launch_trsv_timeout_selftest(const float *LU, int n, float *X, int *ws, int *status, long long bound_ns,
+                                         cudaStream_t s) {
+    if (n <= kTB) return cudaErrorInvalidValue;   // needs a second block to wait
+    const size_t used = (size_t)2 * kFlagPad + (size_t)2 * TagWords<float>::value * n;
+    cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int) * used, s);
+    if (e != cudaSuccess) return e;
+    const int one = 1;
+    e = cudaMemcpyAsync(ws, &one, sizeof(int), cudaMemcpyHostToDevice, s);   // block 0's ticket is gone
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(float) * (size_t)kTWarps * 2 * kTB * kTB;
+    e = cudaFuncSetAttribute(trsv_blocks<float, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nblk = (n + kTB - 1) / kTB;
+    trsv_blocks<float, true, 1><<<(nblk + kTWarps - 1) / kTWarps, 32 * kTWarps, smem, s>>>(
+        LU, n, n, 1, X, n, ws, reinterpret_cast<unsigned long long *>(ws + 2 * kFlagPad), 1u, status, bound_ns);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+// Self-test of lu_div_fast against the IEEE division: count mismatching bit
+// patterns over the pairs in its safe range among `count` pairs drawn from a
+// counter hash (both signs, every exponent, significands near 2 included).
+template <typename T>
+__global__ void div_selftest_kernel(long long count, unsigned long long seed, unsigned long long *mismatch) {
+    unsigned long long bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        unsigned long long w = z * 0x9E3779B97F4A7C15ULL;
+        w = (w ^ (w >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        w ^= w >> 27;
+        T x, d;
+        if constexpr (sizeof(T) == 4) {
+            unsigned bx = (unsigned)z, bd = (unsigned)w;
+            if ((i & 7) == 0) bd = (bd & 0x807fffffu) | (((bd >> 23) & 0xffu) << 23) | 0x007ffff0u;   // near-2 significands
+            x = __uint_as_float(bx);
+            d = __uint_as_float(bd);
+        } else {
+            unsigned long long bd = w;
+            if ((i & 7) == 0) bd |= 0x000fffffffffff00ULL;
+            x = __longlong_as_double((long long)z);
+            d = __longlong_as_double((long long)bd);
+        }
+        if (x != x || d != d || d == T(0)) continue;
+        if (!lu_div_safe(x, lu_div_range<T>::in(d))) continue;   // those take the IEEE division
+        const T rcp = T(1) / d;
+        const T a = lu_div_fast(x, d, rcp);
+        const T b = x / d;
+        bool same;
+        if constexpr (sizeof(T) == 4) same = (__float_as_uint(a) == __float_as_uint(b)) || (a != a && b != b);
+        else same = (__double_as_longlong(a) == __double_as_longlong(b)) || (a != a && b != b);
+        if (!same) ++bad;
+    }
+    if (bad) atomicAdd(mismatch, bad);
+}
+
+cudaError_t launch_div_selftest(int dt64, long long count, unsigned long long seed, unsigned long long *mismatch,
+                                cudaStream_t s) {
+    if (dt64) div_selftest_kernel<double><<<1216, 256, 0, s>>>(count, seed, mismatch);
+    else div_selftest_kernel<float><<<1216, 256, 0, s>>>(count, seed, mismatch);
+    lu_count_launch();
+    return cudaGetLastError();
 }
 
 __global__ void iota_kernel(int *v, int n) {
