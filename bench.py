@@ -42,6 +42,15 @@ BATCH_COUNT = 10000
 BATCH_SEED = 20161106 + 1000 * 4      # family 4 (batched LU)
 
 
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def flops_lu(n):
     return 2.0 / 3.0 * n ** 3
 
@@ -407,6 +416,20 @@ def time_to_solution(args, dev):
         torch.cuda.synchronize()
         reps.append((time.perf_counter() - t0, rep))
     wall, rep = min(reps, key=lambda r: r[0])
+    # the tensor-core update inside one more run, against the HBM roofline (C in FP32 read
+    # and written once per launch, staged operands read once)
+    lu.lu_update_timing(True)
+    lu.lu_solve_mixed(A, B, X)
+    torch.cuda.synchronize()
+    lu.lu_update_timing(False)
+    u_n, u_ms, u_flops, u_bytes = lu.lu_update_timing_read()
+    hbm_peak = _measured_peaks().get("hbm_gbs", 6793.0)
+    tc_roof = None
+    if u_ms > 0:
+        gbs = u_bytes / (u_ms / 1e3) / 1e9
+        tc_roof = {"bound": "hbm", "kernel": "gemm_update_tc<3>", "launches": u_n, "total_ms": u_ms,
+                   "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                   "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"}
     x = X.view(-1)
     r = B.view(-1) - A.t() @ x
     eta = float(r.abs().max() / (A.abs().sum(0).max() * x.abs().max() + B.abs().max()))
@@ -422,6 +445,7 @@ def time_to_solution(args, dev):
             "mixed_refine_ms": rep.t_refine_ms, "mixed_rung": rep.rung, "mixed_iterations": rep.iterations,
             "mixed_gmres_iters": rep.gmres_iters, "mixed_eta": eta, "mixed_fell_back": rep.fell_back,
             "fp64_ms": rep64.t_total_ms, "fp64_iterations": rep64.iterations, "fp64_eta": eta64,
+            "update_roofline": tc_roof,
             "speedup_vs_fp64": rep64.t_total_ms / rep.t_total_ms if rep.t_total_ms > 0 else None}
 
 

@@ -334,7 +334,7 @@ cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cu
     if ((e = cudaEventRecord(t.a, s)) != cudaSuccess) return e;
     if ((e = update_launch<T>(c, k_par, kb, w, c0, c1, s)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t.b, s)) != cudaSuccess) return e;
-    const int k = c.pl.tc ? c.kpad : w;
+    const int k = c.pl.tc ? c.kinner : w;   // staged operand width (hi and lo halves with the split)
     const double opw = c.pl.tc ? (c.pl.fmt == 2 ? 1.0 : 2.0) : (double)sizeof(T);
     t.flops = 2.0 * m * nn * (double)w;
     t.bytes = 2.0 * m * nn * sizeof(T) + (double)m * k * opw + (double)k * nn * opw;
