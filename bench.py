@@ -167,6 +167,21 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def combine_ranks(ms_local, steps, flops_per_rank_step, ws, device):
+    """Whole-job timing over independent replicas: the slowest rank's time (an
+    all-reduce MAX when a process group is up) and the flops of all ranks over
+    it.  Returns (ms per step, GFLOP/s)."""
+    import torch
+
+    ms = float(ms_local)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / steps
+    return ms_per_step, ws * flops_per_rank_step / (ms_per_step / 1e3) / 1e9
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -228,13 +243,7 @@ def run_ours(args):
     lu.lu_update_timing(False)
     upd_n, upd_ms, upd_flops, upd_bytes = lu.lu_update_timing_read()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_per_step = ms / args.steps
-    value = ws * flops_lu(n) / (ms_per_step / 1e3) / 1e9
+    ms_per_step, value = combine_ranks(e0.elapsed_time(e1), args.steps, flops_lu(n), ws, dev)
 
     # end-to-end through the C ABI with host buffers (pinned), copies timed
     hA = A0.cpu().pin_memory()
