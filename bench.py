@@ -292,6 +292,7 @@ def run_ours(args):
     batched = None
     if not args.skip_batched and rank == 0:
         batched = {dt: batched_case(dev, dt, args.steps) for dt in ("f64", "f32")}
+    small = small_case(dev) if rank == 0 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -301,7 +302,7 @@ def run_ours(args):
                    "entries": "uniform [-1,1)", "l2": "inputs larger than L2 (2 GiB FP64 matrix per step)",
                    "parallelism": f"replicas x{ws}", "eta_fp64": eta},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "time_to_solution": tts, "batched": batched,
+        "time_to_solution": tts, "batched": batched, "latency_n512": small,
     }
     if rank == 0 and not args.skip_cpu:
         dt, threads = oracle_sample(args.cpu_n, SEED)
@@ -313,6 +314,39 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def small_case(dev):
+    """The n = 512 FP64 factor + solve (b = A * ones) as a latency: median of 20
+    runs, each bracketed by CUDA events; the matrix is restored before each run."""
+    import statistics as st
+
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    n = 512
+    A0 = li.uniform_colmajor_torch(n, n, 20161106 + 1000 * 1, dev, torch.float64)
+    b0 = (A0.t() @ torch.ones(n, dtype=torch.float64, device=dev)).view(1, n)
+    A, b = torch.empty_like(A0), torch.empty_like(b0)
+    ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    times = []
+    for rep in range(23):
+        A.copy_(A0)
+        b.copy_(b0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lu.lu_factor(A, ipiv, info)
+        lu.lu_solve(A, ipiv, b)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep >= 3:
+            times.append(e0.elapsed_time(e1) * 1e3)
+    assert int(info.item()) == 0 and float((b - 1.0).abs().max()) < 1e-10
+    return {"n": n, "us": st.median(times), "us_min": min(times), "gflops": flops_lu(n) / (st.median(times) / 1e6) / 1e9}
 
 
 def batched_case(dev, dtype, steps):

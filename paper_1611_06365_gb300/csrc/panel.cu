@@ -365,7 +365,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             const int j = jb + lj;
             const int par = j & 1;
             const unsigned mb = smem_u32(&S.mbar[par]);
-            if (tid == 0) mbar_arrive_expect(mb, xbytes);
+            if (C > 1 && tid == 0) mbar_arrive_expect(mb, xbytes);
             warp_argmax_t<T>(best, bidx);
             // the lane holding the warp's candidate stages it; the owner of row j stages row j
             if (bidx != INT_MAX && lane == ((bidx - r0) & 31))
@@ -379,8 +379,17 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             unsigned long long ckey = lane < kPanelWarps ? S.red_key[par][lane] : 0ULL;
             int crow = lane < kPanelWarps ? S.red_idx[par][lane] : INT_MAX;
             warp_argmax_t<T>(ckey, crow);
-            // push header, candidate row and row j into every CTA, 16 bytes per store
-            {
+            const T *urow;
+            const T *drow = S.jst[par];    // old row j, the new content of row p
+            int p;
+            bool valid;
+            if (C == 1) {
+                // one CTA holds every row: its candidate is the pivot, no exchange
+                valid = (crow != INT_MAX);
+                p = valid ? crow : j;
+                urow = valid ? S.wst[par][((crow - r0) >> 5) & (kPanelWarps - 1)] : S.jst[par];
+            } else {
+                // push header, candidate row and row j into every CTA, 16 bytes per store
                 const int ndiag = own_j ? nvec : 0;
                 const int per = 1 + nvec + ndiag;
                 const int4 *crow_src = reinterpret_cast<const int4 *>(
@@ -403,19 +412,19 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                     }
                     st_async16(peer_u32(addr, d), v, peer_u32(mb, d));
                 }
+                mbar_wait_bounded(mb, (unsigned)(j >> 1) & 1u, &S.abort, status, bound_ns);
+                // winner from the local copies, reduced by every warp (no barrier)
+                const int4 hdr = lane < C ? *reinterpret_cast<const int4 *>(&S.cand[par][lane]) : make_int4(0, 0, INT_MAX, 0);
+                unsigned long long wk = ((unsigned long long)(unsigned)hdr.y << 32) | (unsigned)hdr.x;
+                int ix = hdr.z;
+                const int mine = ix;
+                warp_argmax_t<T>(wk, ix);
+                valid = (ix != INT_MAX);
+                const int src = valid ? __ffs(__ballot_sync(0xffffffffu, mine == ix)) - 1 : 0;
+                p = valid ? ix : j;   // every candidate NaN: keep row j, as a sequential scan would
+                urow = valid ? S.cand[par][src].vals : S.diag[par];
+                drow = S.diag[par];
             }
-            mbar_wait_bounded(mb, (unsigned)(j >> 1) & 1u, &S.abort, status, bound_ns);
-            // winner from the local copies, reduced by every warp (no barrier)
-            const int4 hdr = lane < C ? *reinterpret_cast<const int4 *>(&S.cand[par][lane]) : make_int4(0, 0, INT_MAX, 0);
-            unsigned long long wk = ((unsigned long long)(unsigned)hdr.y << 32) | (unsigned)hdr.x;
-            int ix = hdr.z;
-            const int mine = ix;
-            warp_argmax_t<T>(wk, ix);
-            const bool valid = (ix != INT_MAX);
-            const int src = valid ? __ffs(__ballot_sync(0xffffffffu, mine == ix)) - 1 : 0;
-            const int p = valid ? ix : j;   // every candidate NaN: keep row j, as a sequential scan would
-            const T *urow = valid ? S.cand[par][src].vals : S.diag[par];
-            const T *drow = S.diag[par];    // old row j, the new content of row p
             const T pv = urow[lj];
             const bool zero = (pv == T(0));
             if (tid == 0) {
@@ -672,7 +681,9 @@ static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap,
     };
     if (max_ctas < 1 || max_ctas > kPanelMaxCtas) max_ctas = kPanelMaxCtas;
     int C = 1;
-    while (C < kPanelMaxCtas && C < max_ctas && (m + 2 * C - 1) / (2 * C) >= 64) C *= 2;
+    // up to one row per thread, one CTA holds the panel: no cluster exchange per column
+    if (m > kPanelThreads || tile_width<T>(1) < bi)
+        while (C < kPanelMaxCtas && C < max_ctas && (m + 2 * C - 1) / (2 * C) >= 64) C *= 2;
     while (C < kPanelMaxCtas && !fits(C)) C *= 2;
     if (!fits(C)) return false;
     const int R = rows_for(C);
