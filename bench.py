@@ -206,6 +206,15 @@ def run_ours(args):
     ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
     info = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # the autotuner picks b_o and the panel team for this order (untimed); every
+    # factorization below leaves its options at zero and so runs the winner
+    tuned = {}
+    if args.tune_file and os.path.exists(args.tune_file):
+        # a table saved by an earlier run: no tuning launches (profiling runs)
+        tuned["loaded"] = {"file": args.tune_file, "entries": lu.lu_tune_load(args.tune_file)}
+        args.no_autotune = True
+    if not args.no_autotune:
+        tuned["fp64"] = lu.lu_autotune(lu.LU_F64, n, budget_ms=args.tune_budget_ms)
 
     def step():
         A.copy_(A0)
@@ -278,21 +287,35 @@ def run_ours(args):
                 "avg_launch_ms": upd_ms / max(1, upd_n),
                 "flops_per_launch": upd_flops / max(1, upd_n),
                 "peak_note": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"}
+    # measured DRAM bytes per flop of the update at the plan's panel width (the update's
+    # depth k): an ncu capture of the same kernel at that k, scaled to the average launch
+    _, plan = lu.lu_plan_info(lu.LU_F64, n)
+    roofline["plan"] = plan
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            tr = json.load(f).get("gemm_update_simt<double>")
-        if tr and tr.get("valid"):
-            roofline["traffic"] = tr["bytes_per_flop"] * roofline["flops_per_launch"]
+            entries = json.load(f).get("gemm_update_simt<double>", [])
+        for tr in entries if isinstance(entries, list) else [entries]:
+            if tr.get("valid") and tr.get("k") == plan["nb"]:
+                roofline["traffic"] = tr["bytes_per_flop"] * roofline["flops_per_launch"]
+                roofline["traffic_source"] = tr.get("source")
 
     # time to backward error 1e-14: mixed precision vs FP64 on a kappa = 1e5 matrix
     tts = None
     if not args.skip_mixed and rank == 0:
+        if not args.no_autotune:
+            tuned["mixed_f32"] = lu.lu_autotune(lu.LU_F32, args.mixed_n, update=lu.LU_UPDATE_BF16X3,
+                                                budget_ms=args.tune_budget_ms)
         tts = time_to_solution(args, dev)
     batched = None
     if not args.skip_batched and rank == 0:
-        batched = {dt: batched_case(dev, dt, args.steps) for dt in ("f64", "f32")}
-    small = small_case(dev) if rank == 0 else None
+        batched = {dt: batched_case(dev, dt, args.steps, tuned if not args.no_autotune else None)
+                   for dt in ("f64", "f32")}
+    small = None
+    if rank == 0:
+        if not args.no_autotune:
+            tuned["fp64_n512"] = lu.lu_autotune(lu.LU_F64, 512)
+        small = small_case(dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -300,7 +323,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"fp64_lu_lookahead_n{n}", "n": n, "lda": n, "nrhs": 1, "seed": SEED,
                    "entries": "uniform [-1,1)", "l2": "inputs larger than L2 (2 GiB FP64 matrix per step)",
-                   "parallelism": f"replicas x{ws}", "eta_fp64": eta},
+                   "parallelism": f"replicas x{ws}", "eta_fp64": eta,
+                   "autotuned": tuned or None},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "time_to_solution": tts, "batched": batched, "latency_n512": small,
     }
@@ -310,6 +334,8 @@ def run_ours(args):
                                 "kind": "oracle",
                                 "sample": f"oracle getrf+getrs on a uniform [-1,1) matrix of order {args.cpu_n} "
                                           f"(same generator), {dt:.1f} s"}
+    if rank == 0 and args.tune_file and "loaded" not in tuned:
+        lu.lu_tune_save(args.tune_file)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -349,7 +375,7 @@ def small_case(dev):
     return {"n": n, "us": st.median(times), "us_min": min(times), "gflops": flops_lu(n) / (st.median(times) / 1e6) / 1e9}
 
 
-def batched_case(dev, dtype, steps):
+def batched_case(dev, dtype, steps, tuned=None):
     """10 000 LUs + solves of orders uniform in [16, 256] (odd members diagonally
     dominant), b = A * ones, one CUDA graph per step (restore, factor, solve)."""
     import numpy as np
@@ -381,6 +407,8 @@ def batched_case(dev, dtype, steps):
     ptrP = torch.tensor([ipiv.data_ptr() + int(o) * 4 for o in roffs[:-1]], dtype=torch.int64, device=dev)
     ptrB = torch.tensor([rhs.data_ptr() + int(o) * esz for o in roffs[:-1]], dtype=torch.int64, device=dev)
     info = torch.zeros(BATCH_COUNT, dtype=torch.int32, device=dev)
+    if tuned is not None:
+        tuned[f"batched_{dtype}"] = lu.lu_autotune_batched(code, ns, 256)
 
     def body():
         buf.copy_(buf0)
@@ -510,12 +538,13 @@ def run_case(args):
         C = li.uniform_colmajor_torch(m, n, 3, dev, torch.float32)
         lu.lu_trailing_update(lu.LU_UPDATE_BF16X3, A, B, C, m, n, k)
     elif args.case == "fp64_factor":
-        # FP64 factorization, n = 8192 (512 MiB), panel width 16 as in the n = 16384 workload
+        # FP64 factorization, n = 8192 (512 MiB), with the plan the autotuner picks for the
+        # n = 16384 workload on GB300 (b_o = 64, an 8-CTA panel team)
         n = 8192
         A = li.uniform_colmajor_torch(n, n, 5, dev, torch.float64)
         ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
-        lu.lu_factor(A, ipiv, info, nb=16)
+        lu.lu_factor(A, ipiv, info, nb=64, panel_ctas=8)
     elif args.case == "mixed_factor":
         # FP32 factorization with the split-BF16 update, n = 8192
         n = 8192
@@ -561,6 +590,12 @@ def main():
     ap.add_argument("--skip-mixed", dest="skip_mixed", action="store_true")
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
     ap.add_argument("--skip-batched", dest="skip_batched", action="store_true")
+    ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
+                    help="run the built-in plans instead of timing candidates first")
+    ap.add_argument("--tune-budget-ms", dest="tune_budget_ms", type=float, default=15000.0,
+                    help="device time the autotuner may spend per order")
+    ap.add_argument("--tune-file", dest="tune_file", default=None,
+                    help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32"],
                     default=None,
                     help="run one profiling case instead of the benchmark")

@@ -91,7 +91,9 @@ typedef struct {
  *   dt    LU_F64 (dA is double*) or LU_F32 (dA is float*).
  *   n     order, n >= 0.               dA    device, n x n, leading dim lda.
  *   lda   >= max(1, n).                d_ipiv device int[n] (output).
- *   d_info device int (output).        opts  host pointer or NULL.
+ *   d_info device int (output).        opts  host pointer or NULL; NULL
+ *   or a zero field takes the autotuner's entry for this order (lu_autotune
+ *   below), else the built-in choice.
  *   On return A holds L (strictly lower, unit diagonal implied) and U.
  */
 int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info,
@@ -219,6 +221,75 @@ int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const double *dB,
  */
 int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda,
                        const float *dB, int ldb, float *dC, int ldc, void *stream);
+
+/*
+ * Autotuner.  Section 3.1 leaves the outer panel width b_o to a trade-off (a
+ * wide panel makes a fast trailing update, a narrow one a short panel chain)
+ * and section 3.2 the number of threads in the panel team; here both, and the
+ * batched panel width, are chosen by timing candidates on the device.
+ *
+ * The process-wide table maps (kind, dt, update, n) to the options that won:
+ * kind 0 = lu_factor of order n (update = the LU_UPDATE_* of the call), kind 1
+ * = lu_factor_batched with max_n = n (update 0).  lu_factor (and the FP32 and
+ * FP64 factorizations inside lu_solve_mixed) fill every option left at zero
+ * (nb, nb_inner, panel_ctas, lookahead) from the entry for their exact order;
+ * lu_factor_batched with nb = 0 takes the entry's nb.  Without an entry the
+ * built-in choice applies.  The table lives in host memory; calls are
+ * thread-safe.
+ */
+typedef struct {
+    lu_opts opts;     /* the fastest candidate (nb always set; other zero fields = built-in) */
+    double ms;        /* its device time (best of three for n <= 4096, else one run) */
+    int candidates;   /* plans timed */
+} lu_tune_result;
+
+/*
+ * lu_autotune -- times lu_factor(dt, n) for candidate plans on a scratch n x n
+ * matrix (entries uniform in [-1, 1), allocated stream-ordered on `stream`,
+ * 2 n^2 elements) and records the fastest in the table.  Candidates: the
+ * built-in plan; b_o in {16, 32, 64} (FP64) or {64, 128, 256} (FP32 and the
+ * tensor-core updates); then panel teams of 8 and 4 CTAs at the best b_o; for
+ * n <= 2048 also the plan without look-ahead.  budget_ms > 0 stops adding
+ * candidates once that much device time has been spent (at least one is timed).
+ * update: LU_UPDATE_* (not NATIVE only with LU_F32).  Synchronizes `stream`.
+ * Returns 0, a negative argument index, LU_ERR_NOMEM, LU_ERR_CUDA or
+ * LU_ERR_TIMEOUT; res (host) receives the winner.
+ */
+int lu_autotune(lu_dtype dt, int n, int update, double budget_ms, lu_tune_result *res, void *stream);
+
+/*
+ * lu_autotune_batched -- times lu_factor_batched with nb = 16, 32 and 1 (only
+ * 1 when max_n > 256) on scratch matrices of the orders in d_n (device
+ * int[batch], read once), best of three runs each, and records the fastest
+ * under (kind 1, dt, 0, max_n).  Synchronizes `stream`.
+ */
+int lu_autotune_batched(lu_dtype dt, int batch, const int *d_n, int max_n, lu_tune_result *res, void *stream);
+
+/*
+ * lu_plan_info -- the plan lu_factor(dt, n, ..., opts) would run, without any
+ * CUDA call: *plan (host) receives the outer width b_o, the inner width of the
+ * first panel, the panel team, lookahead (1 on, -1 off), the update kind and
+ * the wait bound, after the autotuner's table and the built-in choice have
+ * filled the zero fields of opts.  Returns 0 if every panel of the plan fits a
+ * cluster's shared memory, LU_ERR_UNSUPPORTED if one does not (lu_factor then
+ * returns the same code and launches nothing), or -i for a bad argument i.
+ */
+int lu_plan_info(lu_dtype dt, int n, const lu_opts *opts, lu_opts *plan);
+
+/* Table access (host only, no CUDA calls).  lu_tune_get returns 1 and fills
+ * *out when an entry exists, else 0.  lu_tune_put validates and stores an
+ * entry (negative argument index on error).  lu_tune_save writes the table as
+ * text (one entry per line: kind dtype update n nb nb_inner panel_ctas
+ * lookahead ms; '#' starts a comment) and returns the entries written or -1;
+ * lu_tune_load merges such a file and returns the entries read, -1 if it
+ * cannot be read, -2 if any line is malformed or out of range (then nothing is
+ * taken).  lu_tune_count returns the number of entries. */
+int lu_tune_get(int kind, lu_dtype dt, int update, int n, lu_opts *out);
+int lu_tune_put(int kind, lu_dtype dt, int update, int n, const lu_opts *opts, double ms);
+int lu_tune_save(const char *path);
+int lu_tune_load(const char *path);
+int lu_tune_count(void);
+void lu_tune_clear(void);
 
 /*
  * lu_workspace_size -- bytes of internal workspace a call allocates

@@ -23,13 +23,16 @@ __all__ = [
     "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8", "LuError", "lib", "build",
     "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status",
-    "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches", "to_colmajor", "from_colmajor", "MixedReport",
+    "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches",
+    "lu_autotune", "lu_autotune_batched", "lu_tune_get", "lu_tune_put", "lu_tune_save", "lu_tune_load", "lu_tune_count",
+    "lu_tune_clear", "lu_plan_info", "TUNE_FACTOR", "TUNE_BATCHED", "to_colmajor", "from_colmajor", "MixedReport",
 ]
 
 LU_F64, LU_F32 = 0, 1
 LU_UPDATE_NATIVE, LU_UPDATE_BF16, LU_UPDATE_BF16X3, LU_UPDATE_FP8 = 0, 1, 2, 3
 LU_ERR_CUDA, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED = -100, -101, -102, -103
 LU_ERR_SCRATCH = -104
+TUNE_FACTOR, TUNE_BATCHED = 0, 1   # kinds of tuning-table entries
 LU_TRACE_KINDS = ("panel", "swap_left", "ru1", "pf1", "pf2", "ru2")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -46,6 +49,10 @@ class LuError(RuntimeError):
 class LuOpts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("nb_inner", ctypes.c_int), ("panel_ctas", ctypes.c_int),
                 ("lookahead", ctypes.c_int), ("update", ctypes.c_int), ("spin_ns", ctypes.c_longlong)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("opts", LuOpts), ("ms", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 
 class MixedOpts(ctypes.Structure):
@@ -106,6 +113,18 @@ def lib():
         L.lu_trace.restype = i
         L.lu_trace_read.argtypes = [ctypes.POINTER(TraceEvent), i]
         L.lu_trace_read.restype = i
+        L.lu_autotune.argtypes = [i, i, i, ctypes.c_double, ctypes.POINTER(TuneResult), vp]
+        L.lu_autotune_batched.argtypes = [i, i, ip, i, ctypes.POINTER(TuneResult), vp]
+        L.lu_tune_get.argtypes = [i, i, i, i, ctypes.POINTER(LuOpts)]
+        L.lu_tune_put.argtypes = [i, i, i, i, ctypes.POINTER(LuOpts), ctypes.c_double]
+        L.lu_tune_save.argtypes = [ctypes.c_char_p]
+        L.lu_tune_load.argtypes = [ctypes.c_char_p]
+        L.lu_tune_clear.restype = None
+        L.lu_plan_info.argtypes = [i, i, ctypes.POINTER(LuOpts), ctypes.POINTER(LuOpts)]
+        L.lu_plan_info.restype = i
+        for f in ("lu_autotune", "lu_autotune_batched", "lu_tune_get", "lu_tune_put", "lu_tune_save", "lu_tune_load",
+                  "lu_tune_count"):
+            getattr(L, f).restype = i
         for f in ("lu_factor", "lu_solve", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
                   "lu_trailing_update", "lu_last_device_status"):
             getattr(L, f).restype = i
@@ -299,3 +318,67 @@ def from_colmajor(T, m=None):
     """Inverse of to_colmajor: column-major (n, ld) tensor -> row-major (m, n) matrix."""
     m = T.shape[1] if m is None else m
     return T[:, :m].t().contiguous()
+
+
+def _opts_dict(o):
+    return {"nb": o.nb, "nb_inner": o.nb_inner, "panel_ctas": o.panel_ctas, "lookahead": o.lookahead, "update": o.update}
+
+
+def lu_autotune(dtype_code, n, *, update=LU_UPDATE_NATIVE, budget_ms=0.0, stream=None):
+    """Time candidate plans for lu_factor of order n and record the fastest in the
+    tuning table (synchronizes the stream).  Returns {"opts": ..., "ms", "candidates"}."""
+    r = TuneResult()
+    _check("lu_autotune", lib().lu_autotune(dtype_code, n, update, float(budget_ms), ctypes.byref(r), _stream(stream)))
+    return {"opts": _opts_dict(r.opts), "ms": r.ms, "candidates": r.candidates}
+
+
+def lu_autotune_batched(dtype_code, ns, max_n, *, stream=None):
+    """Time the batched panel widths on scratch matrices of the orders in ns (device int32)."""
+    r = TuneResult()
+    _check("lu_autotune_batched", lib().lu_autotune_batched(dtype_code, ns.shape[0], _ptr(ns), max_n, ctypes.byref(r),
+                                                            _stream(stream)))
+    return {"opts": _opts_dict(r.opts), "ms": r.ms, "candidates": r.candidates}
+
+
+def lu_plan_info(dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE):
+    """(status, plan dict) of the plan lu_factor would run for these options (no CUDA call);
+    status 0 = every panel fits, LU_ERR_UNSUPPORTED = one does not."""
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0)
+    p = LuOpts()
+    rc = lib().lu_plan_info(dtype_code, n, ctypes.byref(o), ctypes.byref(p))
+    if rc < 0 and rc > -100:
+        raise LuError("lu_plan_info", rc)
+    return rc, _opts_dict(p)
+
+
+def lu_tune_get(kind, dtype_code, n, *, update=LU_UPDATE_NATIVE):
+    """The table's options for (kind, dtype, update, n) as a dict, or None."""
+    o = LuOpts()
+    return _opts_dict(o) if lib().lu_tune_get(kind, dtype_code, update, n, ctypes.byref(o)) else None
+
+
+def lu_tune_put(kind, dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE, ms=0.0):
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0)
+    return _check("lu_tune_put", lib().lu_tune_put(kind, dtype_code, update, n, ctypes.byref(o), float(ms)))
+
+
+def lu_tune_save(path) -> int:
+    rc = lib().lu_tune_save(os.fsencode(path))
+    if rc < 0:
+        raise LuError("lu_tune_save", rc)
+    return rc
+
+
+def lu_tune_load(path) -> int:
+    rc = lib().lu_tune_load(os.fsencode(path))
+    if rc < 0:
+        raise LuError("lu_tune_load", rc)
+    return rc
+
+
+def lu_tune_count() -> int:
+    return lib().lu_tune_count()
+
+
+def lu_tune_clear() -> None:
+    lib().lu_tune_clear()

@@ -40,6 +40,7 @@ cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, 
                                int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
                                cudaStream_t s);
 int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo);
+bool panel_fits(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_cap);
 // swap_trsm.cu
 template <typename T>
 cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c_begin, int c_end, int do_trsm,
@@ -296,6 +297,19 @@ Plan make_plan(int n, const lu_opts *o) {
     return p;
 }
 
+// Options with every field left at zero filled from the autotuner's table
+// entry for (kind, dt, update, n), when it has one.
+const lu_opts *with_tuned(int kind, lu_dtype dt, int n, const lu_opts *o, lu_opts *buf) {
+    lu_opts t;
+    if (!lu_tune_get(kind, dt, o ? o->update : LU_UPDATE_NATIVE, n, &t)) return o;
+    *buf = o ? *o : lu_opts{};
+    if (buf->nb == 0) buf->nb = t.nb;
+    if (buf->nb_inner == 0) buf->nb_inner = t.nb_inner;
+    if (buf->panel_ctas == 0) buf->panel_ctas = t.panel_ctas;
+    if (buf->lookahead == 0) buf->lookahead = t.lookahead;
+    return buf;
+}
+
 template <typename T>
 struct FactorCtx {
     int n;
@@ -364,16 +378,32 @@ cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, in
     return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, sd, kb + w, s);
 }
 
+// Inner width of the outer panel at column kb (width w) of an order-n
+// factorization: the panel's rows shrink with k, so later panels hold wider
+// inner panels.
+int plan_inner_width(const Plan &pl, int n, size_t elem, int kb, int w) {
+    int bi = pl.bi;
+    if (pl.bi_auto) bi = std::max(bi, panel_width_that_fits(n - kb, elem, kPanelSmemCap, 64, w));
+    return std::min(bi, w);
+}
+
+// Whether every outer panel of the plan fits a cluster.
+bool plan_fits(const Plan &pl, int n, size_t elem) {
+    for (int kb = 0; kb < n; kb += pl.bo) {
+        const int w = std::min(pl.bo, n - kb);
+        if (!panel_fits(n - kb, elem, w, plan_inner_width(pl, n, elem, kb, w), pl.panel_ctas, kPanelSmemCap)) return false;
+    }
+    return true;
+}
+
 // Factor outer panel at column kb (width w) on stream s: one cluster launch
 // that also leaves the row map in maps[par], updates perm and stages L21.
 template <typename T>
 cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s) {
     StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt};
     if (c.pl.tc && kb + w < c.n) { sd.ptr = c.stA[par]; sd.scale = c.scA[par]; }
-    // the panel's rows shrink with k, so later panels hold wider inner panels
-    int bi = c.pl.bi;
-    if (c.pl.bi_auto) bi = std::max(bi, panel_width_that_fits(c.n - kb, sizeof(T), kPanelSmemCap, 64, w));
-    return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, std::min(bi, w), c.ipiv + kb, kb,
+    return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, plan_inner_width(c.pl, c.n, sizeof(T), kb, w),
+                                 c.ipiv + kb, kb,
                                  c.info, c.maps[par], c.perm, sd, c.pl.panel_ctas, kPanelSmemCap, c.st->status,
                                  c.pl.bound, s);
 }
@@ -410,6 +440,8 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
     FactorCtx<T> c;
     c.n = n; c.A = A; c.lda = lda; c.ipiv = ipiv; c.info = info; c.perm = perm; c.pl = pl; c.st = st;
     const int bo = pl.bo;
+    // every panel of the plan must fit a cluster before anything is enqueued
+    if (!plan_fits(pl, n, sizeof(T))) return LU_ERR_UNSUPPORTED;
     for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
     LU_CUDA_TRY(ws.get(&c.tile_ctr, 2));
     if (perm) LU_CUDA_TRY(launch_iota(perm, n, caller));
@@ -507,6 +539,36 @@ int solve_impl(int n, int nrhs, const T *LU, int lda, const int *ipiv, const int
 // ---------------------------------------------------------------------------
 extern "C" {
 
+static bool opts_valid(lu_dtype dt, const lu_opts *opts) {
+    if (!opts) return true;
+    if (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 ||
+        (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
+         opts->update != LU_UPDATE_FP8))
+        return false;
+    if (opts->update != LU_UPDATE_NATIVE && dt != LU_F32) return false;
+    if (opts->update != LU_UPDATE_NATIVE && opts->nb > tc_max_k()) return false;
+    return true;
+}
+
+int lu_plan_info(lu_dtype dt, int n, const lu_opts *opts, lu_opts *plan) {
+    if (dt != LU_F64 && dt != LU_F32) return -1;
+    if (n < 1) return -2;
+    if (!opts_valid(dt, opts)) return -3;
+    if (!plan) return -4;
+    lu_opts tuned;
+    opts = with_tuned(0, dt, n, opts, &tuned);
+    const Plan p = dt == LU_F64 ? make_plan<double>(n, opts) : make_plan<float>(n, opts);
+    const size_t elem = dt == LU_F64 ? 8 : 4;
+    *plan = lu_opts{};
+    plan->nb = p.bo;
+    plan->nb_inner = plan_inner_width(p, n, elem, 0, std::min(p.bo, n));
+    plan->panel_ctas = p.panel_ctas;
+    plan->lookahead = p.lookahead ? 1 : -1;
+    plan->update = opts ? opts->update : LU_UPDATE_NATIVE;
+    plan->spin_ns = p.bound;
+    return plan_fits(p, n, elem) ? LU_OK : LU_ERR_UNSUPPORTED;
+}
+
 int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info, const lu_opts *opts, void *stream) {
     if (dt != LU_F64 && dt != LU_F32) return -1;
     if (n < 0) return -2;
@@ -514,13 +576,10 @@ int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info, c
     if (lda < std::max(1, n)) return -4;
     if (n > 0 && !d_ipiv) return -5;
     if (!d_info) return -6;
-    if (opts && (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 ||
-                 (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
-                  opts->update != LU_UPDATE_FP8)))
-        return -7;
-    if (opts && opts->update != LU_UPDATE_NATIVE && dt != LU_F32) return -7;
-    if (opts && opts->update != LU_UPDATE_NATIVE && opts->nb > tc_max_k()) return -7;
+    if (!opts_valid(dt, opts)) return -7;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lu_opts tuned;
+    opts = with_tuned(0, dt, n, opts, &tuned);
     if (dt == LU_F64) {
         Plan p = make_plan<double>(n, opts);
         return factor_impl<double>(n, static_cast<double *>(dA), lda, d_ipiv, d_info, nullptr, p, s);
@@ -557,8 +616,11 @@ int lu_factor_batched(lu_dtype dt, int batch, const int *d_n, void *const *d_A, 
     if (batch > 0 && !d_info) return -7;
     if (max_n < 0 || max_n > 1024) return -8;
     if (batch > 2147483647 / 2) return -2;
-    const int nb = opts ? opts->nb : 0;
+    int nb = opts ? opts->nb : 0;
     if (nb != 0 && nb != 1 && nb != 16 && nb != 32) return -9;
+    lu_opts tuned;
+    if (nb == 0 && lu_tune_get(1, dt, LU_UPDATE_NATIVE, max_n, &tuned) && (tuned.nb <= 1 || max_n <= kBatchedBlockedMaxN))
+        nb = tuned.nb;
     if ((nb == 16 || nb == 32) && max_n > kBatchedBlockedMaxN) return -9;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (nb == 1 || max_n > kBatchedBlockedMaxN) {
@@ -845,12 +907,21 @@ const char *lu_version(void) { return "liblu 0.1 (sm_103a; cluster panel, tcgen0
 // internal entry points used by the mixed-precision driver (mixed_api.cu)
 namespace lu {
 int factor_f32_internal(int n, float *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s) {
+    lu_opts tuned;
+    o = with_tuned(0, LU_F32, n, o, &tuned);
     Plan p = make_plan<float>(n, o);
     return factor_impl<float>(n, A, lda, ipiv, info, perm, p, s);
 }
 int factor_f64_internal(int n, double *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s) {
+    lu_opts tuned;
+    o = with_tuned(0, LU_F64, n, o, &tuned);
     Plan p = make_plan<double>(n, o);
     return factor_impl<double>(n, A, lda, ipiv, info, perm, p, s);
+}
+int default_outer_width(lu_dtype dt, int n, int update) {
+    lu_opts o = {};
+    o.update = update;
+    return dt == LU_F64 ? make_plan<double>(n, &o).bo : make_plan<float>(n, &o).bo;
 }
 int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s) {
     return solve_impl<float>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s);

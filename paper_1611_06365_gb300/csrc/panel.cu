@@ -41,6 +41,7 @@
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <climits>
+#include <cstddef>
 
 namespace cg = cooperative_groups;
 
@@ -64,11 +65,19 @@ struct TileWidth {
     static constexpr int BI = raw > kPanelWMax ? kPanelWMax : raw;
 };
 
+// FP64 scales the panel column by Markstein's correction from a reciprocal that
+// the warp holding the candidate computes once (on GB300 an FP64 division costs
+// a dozen FP64-pipe operations per row); FP32 divides directly, its division
+// being cheap next to the latency a reciprocal would add to the exchange.
+template <typename T>
+constexpr bool kPanelRcp = sizeof(T) == 8;
+
 template <typename T>
 struct __align__(16) CandSlot {
     unsigned long long key;   // magnitude key of the candidate (see mag_key)
     int row;                  // panel row, INT_MAX: no candidate
-    int pad;                  // vals start 16-byte aligned
+    int pad;
+    T rcp[16 / sizeof(T)];    // [0]: RN(1 / candidate's entry in the current column), FP64 only
     T vals[kPanelWMax];
 };
 
@@ -77,6 +86,7 @@ struct PanelShared {
     CandSlot<T> cand[2][kPanelMaxCtas];      // pushed by every CTA (double-buffered)
     __align__(16) T diag[2][kPanelWMax];     // row j, pushed by its owner
     __align__(16) T wst[2][kPanelWarps][kPanelWMax];   // each warp's candidate row
+    T wrcp[2][kPanelWarps];                  // RN(1 / its entry in the current column)
     __align__(16) T jst[2][kPanelWMax];      // row j, staged by its owner
     unsigned long long mbar[2];              // transaction barriers of the column exchange
     unsigned long long red_key[2][kPanelWarps];
@@ -254,8 +264,8 @@ __device__ __forceinline__ void stage_tile_row(const T (&a)[RPT][BI], int uu, T 
 // thread's rows below row j: a(i, LJ) /= pv, a(i, c) -= a(i, LJ) u(c) for
 // c > LJ, and the candidate of column LJ + 1 (when LJ + 1 < wi).
 template <typename T, int RPT, int BI, int LJ>
-__device__ __forceinline__ void rank1_step(T (&a)[RPT][BI], const T *__restrict__ urow, T pv, bool zero, int tid, int r0,
-                                           int myR, int j, int wi, unsigned long long &best, int &bidx) {
+__device__ __forceinline__ void rank1_step(T (&a)[RPT][BI], const T *__restrict__ urow, T pv, T rcp, bool zero, int tid,
+                                           int r0, int myR, int j, int wi, unsigned long long &best, int &bidx) {
     using V = typename Vec16<T>::type;
     constexpr int VEC = 16 / sizeof(T);
     constexpr int Q0 = (LJ + 1) / VEC;   // first vector of urow holding a column > LJ
@@ -267,7 +277,14 @@ __device__ __forceinline__ void rank1_step(T (&a)[RPT][BI], const T *__restrict_
         act[u] = (lr < myR) && (r0 + lr > j) && !zero;
         l[u] = T(0);
         if (act[u]) {
-            l[u] = a[u][LJ] / pv;
+            const T x = a[u][LJ];
+            if constexpr (kPanelRcp<T>) {
+                // the correctly rounded x / pv from the pivot's reciprocal (Markstein's
+                // correction), IEEE division where an operand is outside its safe range
+                l[u] = lu_div_safe(x, lu_div_range<T>::in(pv)) ? lu_div_fast(x, pv, rcp) : x / pv;
+            } else {
+                l[u] = x / pv;
+            }
             a[u][LJ] = l[u];
         }
     }
@@ -302,7 +319,7 @@ __device__ __forceinline__ void rank1_step(T (&a)[RPT][BI], const T *__restrict_
 #define LU_PANEL_CASE(L)                                                                                   \
     case (L):                                                                                              \
         if constexpr ((L) < BI)                                                                            \
-            rank1_step<T, RPT, BI, ((L) < BI ? (L) : 0)>(a, urow, pv, zero, tid, r0, myR, j, wi, best, bidx); \
+            rank1_step<T, RPT, BI, ((L) < BI ? (L) : 0)>(a, urow, pv, rcp, zero, tid, r0, myR, j, wi, best, bidx); \
         break;
 #define LU_PANEL_CASE4(L) LU_PANEL_CASE(L) LU_PANEL_CASE((L) + 1) LU_PANEL_CASE((L) + 2) LU_PANEL_CASE((L) + 3)
 #define LU_PANEL_CASE16(L) LU_PANEL_CASE4(L) LU_PANEL_CASE4((L) + 4) LU_PANEL_CASE4((L) + 8) LU_PANEL_CASE4((L) + 12)
@@ -316,6 +333,8 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     using V = typename Vec16<T>::type;
     constexpr int VEC = 16 / sizeof(T);
     static_assert(BI % VEC == 0, "tile width must be a whole number of 16-byte vectors");
+    static_assert(offsetof(CandSlot<T>, rcp) == 16 && offsetof(CandSlot<T>, vals) == 32,
+                  "the exchange writes a candidate slot as 16-byte vectors: header, reciprocal, row");
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
@@ -359,8 +378,10 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
         }
         // (b) column steps: one CTA barrier and one cluster exchange per column
         const int nvec = (wi + VEC - 1) / VEC;
-        // bytes landing in each CTA per column: C headers and candidate rows, one row j
-        const unsigned xbytes = 16u * (unsigned)(C * (1 + nvec) + nvec);
+        // bytes landing in each CTA per column: C headers (and reciprocals) and
+        // candidate rows, one row j
+        constexpr int qoff = kPanelRcp<T> ? 2 : 1;   // 16-byte vectors before a candidate row
+        const unsigned xbytes = 16u * (unsigned)(C * (qoff + nvec) + nvec);
         for (int lj = 0; lj < wi; ++lj) {
             const int j = jb + lj;
             const int par = j & 1;
@@ -368,8 +389,12 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             if (C > 1 && tid == 0) mbar_arrive_expect(mb, xbytes);
             warp_argmax_t<T>(best, bidx);
             // the lane holding the warp's candidate stages it; the owner of row j stages row j
-            if (bidx != INT_MAX && lane == ((bidx - r0) & 31))
+            // (FP64: with the reciprocal of its entry in column j, one division per
+            // warp instead of one per row)
+            if (bidx != INT_MAX && lane == ((bidx - r0) & 31)) {
                 stage_tile_row<T, RPT, BI>(a, (bidx - r0) / kPanelThreads, S.wst[par][warp]);
+                if constexpr (kPanelRcp<T>) S.wrcp[par][warp] = T(1) / S.wst[par][warp][lj];
+            }
             const bool own_j = (j >= r0 && j < r0 + myR);
             if (own_j && tid == (j - r0) % kPanelThreads)
                 stage_tile_row<T, RPT, BI>(a, (j - r0) / kPanelThreads, S.jst[par]);
@@ -383,17 +408,21 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             const T *drow = S.jst[par];    // old row j, the new content of row p
             int p;
             bool valid;
+            T rcp;
             if (C == 1) {
                 // one CTA holds every row: its candidate is the pivot, no exchange
                 valid = (crow != INT_MAX);
                 p = valid ? crow : j;
-                urow = valid ? S.wst[par][((crow - r0) >> 5) & (kPanelWarps - 1)] : S.jst[par];
+                const int w = ((crow - r0) >> 5) & (kPanelWarps - 1);
+                urow = valid ? S.wst[par][w] : S.jst[par];
+                if constexpr (kPanelRcp<T>) rcp = valid ? S.wrcp[par][w] : T(1) / urow[lj];
+                else rcp = T(0);
             } else {
-                // push header, candidate row and row j into every CTA, 16 bytes per store
+                // push header, reciprocal, candidate row and row j into every CTA, 16 bytes per store
                 const int ndiag = own_j ? nvec : 0;
-                const int per = 1 + nvec + ndiag;
-                const int4 *crow_src = reinterpret_cast<const int4 *>(
-                    S.wst[par][crow != INT_MAX ? ((crow - r0) >> 5) & (kPanelWarps - 1) : 0]);
+                const int per = qoff + nvec + ndiag;
+                const int cw = crow != INT_MAX ? ((crow - r0) >> 5) & (kPanelWarps - 1) : 0;
+                const int4 *crow_src = reinterpret_cast<const int4 *>(S.wst[par][cw]);
                 const unsigned slot = smem_u32(&S.cand[par][rank]);
                 const unsigned dslot = smem_u32(S.diag[par]);
                 for (int e = tid; e < C * per; e += kPanelThreads) {
@@ -403,12 +432,17 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                     if (q == 0) {
                         v = make_int4((int)(unsigned)ckey, (int)(unsigned)(ckey >> 32), crow, 0);
                         addr = slot;
-                    } else if (q <= nvec) {
-                        v = crow_src[q - 1];
-                        addr = slot + 16u * (unsigned)q;
+                    } else if (kPanelRcp<T> && q == 1) {
+                        T rv[16 / sizeof(T)] = {};
+                        rv[0] = crow != INT_MAX ? S.wrcp[par][cw] : T(0);
+                        v = *reinterpret_cast<const int4 *>(rv);
+                        addr = slot + 16u;
+                    } else if (q < qoff + nvec) {
+                        v = crow_src[q - qoff];
+                        addr = slot + 32u + 16u * (unsigned)(q - qoff);
                     } else {
-                        v = reinterpret_cast<const int4 *>(S.jst[par])[q - 1 - nvec];
-                        addr = dslot + 16u * (unsigned)(q - 1 - nvec);
+                        v = reinterpret_cast<const int4 *>(S.jst[par])[q - qoff - nvec];
+                        addr = dslot + 16u * (unsigned)(q - qoff - nvec);
                     }
                     st_async16(peer_u32(addr, d), v, peer_u32(mb, d));
                 }
@@ -424,6 +458,8 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                 p = valid ? ix : j;   // every candidate NaN: keep row j, as a sequential scan would
                 urow = valid ? S.cand[par][src].vals : S.diag[par];
                 drow = S.diag[par];
+                if constexpr (kPanelRcp<T>) rcp = valid ? S.cand[par][src].rcp[0] : T(1) / urow[lj];
+                else rcp = T(0);
             }
             const T pv = urow[lj];
             const bool zero = (pv == T(0));
@@ -681,8 +717,9 @@ static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap,
     };
     if (max_ctas < 1 || max_ctas > kPanelMaxCtas) max_ctas = kPanelMaxCtas;
     int C = 1;
-    // up to one row per thread, one CTA holds the panel: no cluster exchange per column
-    if (m > kPanelThreads || tile_width<T>(1) < bi)
+    // up to one row per thread, one CTA holds the panel (no cluster exchange per
+    // column) when its tile and its share of the other columns fit
+    if (m > kPanelThreads || tile_width<T>(1) < bi || PanelLayout<T>(bi, bo, 1).total > smem_cap)
         while (C < kPanelMaxCtas && C < max_ctas && (m + 2 * C - 1) / (2 * C) >= 64) C *= 2;
     while (C < kPanelMaxCtas && !fits(C)) C *= 2;
     if (!fits(C)) return false;
@@ -757,6 +794,14 @@ int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo) 
         if (ok) return W;
     }
     return 0;
+}
+
+// Whether launch_panel_outer accepts an m-row panel of outer width bo and inner width bi.
+bool panel_fits(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_cap) {
+    int C = 0, R = 0;
+    size_t sm = 0;
+    return elem == 8 ? panel_geometry<double>(m, bi, bo, max_ctas, smem_cap, &C, &R, &sm)
+                     : panel_geometry<float>(m, bi, bo, max_ctas, smem_cap, &C, &R, &sm);
 }
 
 template cudaError_t launch_panel_outer<double>(double *, int, int, int, int, int *, int, int *, int *, int *, StageDesc,
