@@ -312,7 +312,7 @@ def run_ours(args):
         batched = {dt: batched_case(dev, dt, args.steps, tuned if not args.no_autotune else None)
                    for dt in ("f64", "f32")}
     small = None
-    if rank == 0:
+    if rank == 0 and not args.skip_small:
         if not args.no_autotune:
             tuned["fp64_n512"] = lu.lu_autotune(lu.LU_F64, 512)
         small = small_case(dev)
@@ -590,6 +590,8 @@ def main():
     ap.add_argument("--skip-mixed", dest="skip_mixed", action="store_true")
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
     ap.add_argument("--skip-batched", dest="skip_batched", action="store_true")
+    ap.add_argument("--skip-small", dest="skip_small", action="store_true",
+                    help="skip the n = 512 latency measurement")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="run the built-in plans instead of timing candidates first")
     ap.add_argument("--tune-budget-ms", dest="tune_budget_ms", type=float, default=15000.0,

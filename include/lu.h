@@ -79,6 +79,9 @@ typedef struct {
                           -1: plain blocked RL without look-ahead */
     int update;        /* LU_UPDATE_* (LU_F32 only) */
     long long spin_ns; /* bound for device-side waits in ns (0 = 2 s) */
+    int update_ctas;   /* LU_F32 tensor-core updates: persistent CTAs of the remainder
+                          update RU2 (section 3.2's split of the threads between the panel
+                          and the update); 0 = one per SM */
 } lu_opts;
 
 /*
@@ -249,7 +252,8 @@ typedef struct {
  * 2 n^2 elements) and records the fastest in the table.  Candidates: the
  * built-in plan; b_o in {16, 32, 64} (FP64) or {64, 128, 256} (FP32 and the
  * tensor-core updates); then panel teams of 8 and 4 CTAs at the best b_o; for
- * n <= 2048 also the plan without look-ahead.  budget_ms > 0 stops adding
+ * n <= 2048 also the plan without look-ahead; for the tensor-core updates also
+ * a remainder-update grid of 112 CTAs (update_ctas).  budget_ms > 0 stops adding
  * candidates once that much device time has been spent (at least one is timed).
  * update: LU_UPDATE_* (not NATIVE only with LU_F32).  Synchronizes `stream`.
  * Returns 0, a negative argument index, LU_ERR_NOMEM, LU_ERR_CUDA or

@@ -48,7 +48,8 @@ class LuError(RuntimeError):
 
 class LuOpts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("nb_inner", ctypes.c_int), ("panel_ctas", ctypes.c_int),
-                ("lookahead", ctypes.c_int), ("update", ctypes.c_int), ("spin_ns", ctypes.c_longlong)]
+                ("lookahead", ctypes.c_int), ("update", ctypes.c_int), ("spin_ns", ctypes.c_longlong),
+                ("update_ctas", ctypes.c_int)]
 
 
 class TuneResult(ctypes.Structure):
@@ -177,10 +178,10 @@ def _cm_dims(A, n=None):
 
 
 def lu_factor(A, ipiv, info, n=None, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0,
-              update=LU_UPDATE_NATIVE, spin_ns=0, stream=None):
+              update=LU_UPDATE_NATIVE, spin_ns=0, update_ctas=0, stream=None):
     """P A = L U in place (see include/lu.h).  A: column-major (n, lda) tensor."""
     n, lda = _cm_dims(A, n)
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns)
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns, update_ctas)
     return _check("lu_factor", lib().lu_factor(_dtype_code(A), n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
                                                 ctypes.byref(o), _stream(stream)))
 
@@ -321,7 +322,8 @@ def from_colmajor(T, m=None):
 
 
 def _opts_dict(o):
-    return {"nb": o.nb, "nb_inner": o.nb_inner, "panel_ctas": o.panel_ctas, "lookahead": o.lookahead, "update": o.update}
+    return {"nb": o.nb, "nb_inner": o.nb_inner, "panel_ctas": o.panel_ctas, "lookahead": o.lookahead, "update": o.update,
+            "update_ctas": o.update_ctas}
 
 
 def lu_autotune(dtype_code, n, *, update=LU_UPDATE_NATIVE, budget_ms=0.0, stream=None):
@@ -340,10 +342,10 @@ def lu_autotune_batched(dtype_code, ns, max_n, *, stream=None):
     return {"opts": _opts_dict(r.opts), "ms": r.ms, "candidates": r.candidates}
 
 
-def lu_plan_info(dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE):
+def lu_plan_info(dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE, update_ctas=0):
     """(status, plan dict) of the plan lu_factor would run for these options (no CUDA call);
     status 0 = every panel fits, LU_ERR_UNSUPPORTED = one does not."""
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0)
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas)
     p = LuOpts()
     rc = lib().lu_plan_info(dtype_code, n, ctypes.byref(o), ctypes.byref(p))
     if rc < 0 and rc > -100:
@@ -357,8 +359,9 @@ def lu_tune_get(kind, dtype_code, n, *, update=LU_UPDATE_NATIVE):
     return _opts_dict(o) if lib().lu_tune_get(kind, dtype_code, update, n, ctypes.byref(o)) else None
 
 
-def lu_tune_put(kind, dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE, ms=0.0):
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0)
+def lu_tune_put(kind, dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE,
+                update_ctas=0, ms=0.0):
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas)
     return _check("lu_tune_put", lib().lu_tune_put(kind, dtype_code, update, n, ctypes.byref(o), float(ms)))
 
 

@@ -56,7 +56,7 @@ int tc_box_cols();
 cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8);
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                            int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
-                           const float *scaleA, const float *scaleB);
+                           const float *scaleA, const float *scaleB, int max_ctas = 0);
 cudaError_t launch_stage_rows_fp8(int rows, int k, int kpad, const float *L, int ld, unsigned char *stage, int lds,
                                   float *scale, cudaStream_t s);
 cudaError_t launch_stage_cols_fp8(int k, int kpad, int cols, const float *B, int ld, unsigned char *stage, int lds,
@@ -262,6 +262,7 @@ struct Plan {
     int fmt = 0;      // staging format: 0 BF16, 1 split BF16, 2 FP8 e4m3 (StageDesc)
     bool lookahead = true;
     int panel_ctas = 16;
+    int update_ctas = 0;   // persistent CTAs of the remainder update (0: one per SM)
     long long bound = 2000000000LL;
 };
 
@@ -293,6 +294,7 @@ Plan make_plan(int n, const lu_opts *o) {
     p.bi = std::max(1, std::min(p.bi, p.bo));
     p.lookahead = !(o && o->lookahead < 0);
     p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : 16;
+    p.update_ctas = (o && o->update_ctas > 0) ? o->update_ctas : 0;
     p.bound = lu_spin_bound_ns(o);
     return p;
 }
@@ -307,6 +309,7 @@ const lu_opts *with_tuned(int kind, lu_dtype dt, int n, const lu_opts *o, lu_opt
     if (buf->nb_inner == 0) buf->nb_inner = t.nb_inner;
     if (buf->panel_ctas == 0) buf->panel_ctas = t.panel_ctas;
     if (buf->lookahead == 0) buf->lookahead = t.lookahead;
+    if (buf->update_ctas == 0) buf->update_ctas = t.update_ctas;
     return buf;
 }
 
@@ -365,7 +368,8 @@ cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int
         if (c.pl.tc)
             return launch_gemm_tc(c.pl.fmt == 1 ? 3 : (c.pl.fmt == 2 ? 8 : 1), m, nn, c.kpad, c.mapA[k_par], 0, c.mapB,
                                   c0 - r0, reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda,
-                                  c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status, c.pl.bound, s, c.scA[k_par], c.scB);
+                                  c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status, c.pl.bound, s, c.scA[k_par], c.scB,
+                                  s == c.st->P ? 0 : c.pl.update_ctas);
     }
     return launch_gemm_simt<T>(m, nn, w, c.A + r0 + (size_t)kb * c.lda, c.lda, c.A + kb + (size_t)c0 * c.lda, c.lda,
                                c.A + r0 + (size_t)c0 * c.lda, c.lda, s);
@@ -541,7 +545,7 @@ extern "C" {
 
 static bool opts_valid(lu_dtype dt, const lu_opts *opts) {
     if (!opts) return true;
-    if (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 ||
+    if (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 || opts->update_ctas < 0 ||
         (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
          opts->update != LU_UPDATE_FP8))
         return false;
@@ -566,6 +570,7 @@ int lu_plan_info(lu_dtype dt, int n, const lu_opts *opts, lu_opts *plan) {
     plan->lookahead = p.lookahead ? 1 : -1;
     plan->update = opts ? opts->update : LU_UPDATE_NATIVE;
     plan->spin_ns = p.bound;
+    plan->update_ctas = p.update_ctas;
     return plan_fits(p, n, elem) ? LU_OK : LU_ERR_UNSUPPORTED;
 }
 

@@ -538,7 +538,7 @@ static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorM
 // C must be 16-byte aligned with ldc a multiple of 4 (tc_c_aligned).
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                            int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
-                           const float *scaleA, const float *scaleB) {
+                           const float *scaleA, const float *scaleB, int max_ctas) {
     if (m <= 0 || n <= 0 || K <= 0) return cudaSuccess;
     if (nprod != 1 && nprod != 3 && nprod != 8) return cudaErrorInvalidValue;
     const int bk = nprod == 8 ? kTcBK8 : kTcBK;
@@ -556,7 +556,9 @@ cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &ma
         if (e != cudaSuccess) return e;
     }
     const int ntiles = lu_ceil_div(m, kTcBM) * lu_ceil_div(n, kTcBN);
-    const int grid = ntiles < sms ? ntiles : sms;
+    // persistent CTAs: one per SM, or max_ctas (> 0) to leave SMs to other work
+    const int cap = max_ctas > 0 && max_ctas < sms ? max_ctas : sms;
+    const int grid = ntiles < cap ? ntiles : cap;
     cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
     if (ez != cudaSuccess) return ez;
     if (nprod == 1) return launch_tc_mode<1>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s);

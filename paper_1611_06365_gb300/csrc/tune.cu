@@ -60,14 +60,22 @@ bool valid_update(lu_dtype dt, int update) {
     return dt == LU_F32 && (update == LU_UPDATE_BF16 || update == LU_UPDATE_BF16X3 || update == LU_UPDATE_FP8);
 }
 
-lu_opts make_opts(int nb, int nb_inner, int panel_ctas, int lookahead, int update) {
+lu_opts make_opts(int nb, int nb_inner, int panel_ctas, int lookahead, int update, int update_ctas = 0) {
     lu_opts o = {};
     o.nb = nb;
     o.nb_inner = nb_inner;
     o.panel_ctas = panel_ctas;
     o.lookahead = lookahead;
     o.update = update;
+    o.update_ctas = update_ctas;
     return o;
+}
+
+bool opts_in_range(int kind, const lu_opts &o) {
+    if (o.nb < 0 || o.nb_inner < 0 || o.panel_ctas < 0 || o.panel_ctas > 16 || o.lookahead < -1 || o.lookahead > 1 ||
+        o.update_ctas < 0 || o.update_ctas > 4096)
+        return false;
+    return kind != 1 || o.nb == 0 || o.nb == 1 || o.nb == 16 || o.nb == 32;
 }
 
 struct Timer {
@@ -96,11 +104,8 @@ int lu_tune_put(int kind, lu_dtype dt, int update, int n, const lu_opts *o, doub
     if (dt != LU_F64 && dt != LU_F32) return -2;
     if (!valid_update(dt, update)) return -3;
     if (n < 0) return -4;
-    if (!o || o->nb < 0 || o->nb_inner < 0 || o->panel_ctas < 0 || o->panel_ctas > 16 || o->lookahead < -1 ||
-        o->lookahead > 1)
-        return -5;
-    if (kind == 1 && o->nb != 0 && o->nb != 1 && o->nb != 16 && o->nb != 32) return -5;
-    lu_opts c = make_opts(o->nb, o->nb_inner, o->panel_ctas, o->lookahead, update);
+    if (!o || !opts_in_range(kind, *o)) return -5;
+    lu_opts c = make_opts(o->nb, o->nb_inner, o->panel_ctas, o->lookahead, update, o->update_ctas);
     std::lock_guard<std::mutex> lk(g_tmu);
     g_table[Key{kind, (int)dt, update, n}] = Entry{c, ms};
     return LU_OK;
@@ -121,11 +126,11 @@ int lu_tune_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return -1;
     std::lock_guard<std::mutex> lk(g_tmu);
-    fprintf(f, "# liblu tuning table v1\n# kind dtype update n nb nb_inner panel_ctas lookahead ms\n");
+    fprintf(f, "# liblu tuning table v1\n# kind dtype update n nb nb_inner panel_ctas lookahead update_ctas ms\n");
     for (const auto &kv : g_table) {
         const lu_opts &o = kv.second.o;
-        fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                std::get<3>(kv.first), o.nb, o.nb_inner, o.panel_ctas, o.lookahead, kv.second.ms);
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                std::get<3>(kv.first), o.nb, o.nb_inner, o.panel_ctas, o.lookahead, o.update_ctas, kv.second.ms);
     }
     const int bad = ferror(f);
     fclose(f);
@@ -150,9 +155,9 @@ int lu_tune_load(const char *path) {
         if (*p == '#' || *p == '\n' || *p == '\r' || *p == '\0') continue;
         Row r{};
         char tail = 0;
-        const int got = sscanf(p, "%d %d %d %d %d %d %d %d %lf %c", &r.kind, &r.dt, &r.update, &r.n, &r.o.nb,
-                               &r.o.nb_inner, &r.o.panel_ctas, &r.o.lookahead, &r.ms, &tail);
-        if (got != 9) {
+        const int got = sscanf(p, "%d %d %d %d %d %d %d %d %d %lf %c", &r.kind, &r.dt, &r.update, &r.n, &r.o.nb,
+                               &r.o.nb_inner, &r.o.panel_ctas, &r.o.lookahead, &r.o.update_ctas, &r.ms, &tail);
+        if (got != 10) {
             ok = false;
             break;
         }
@@ -164,8 +169,7 @@ int lu_tune_load(const char *path) {
     for (const Row &r : rows) {
         const lu_dtype dt = (lu_dtype)r.dt;
         if ((r.kind != 0 && r.kind != 1) || (r.dt != LU_F64 && r.dt != LU_F32) || !valid_update(dt, r.update) || r.n < 0 ||
-            r.o.nb < 0 || r.o.nb_inner < 0 || r.o.panel_ctas < 0 || r.o.panel_ctas > 16 || r.o.lookahead < -1 ||
-            r.o.lookahead > 1 || (r.kind == 1 && r.o.nb != 0 && r.o.nb != 1 && r.o.nb != 16 && r.o.nb != 32))
+            !opts_in_range(r.kind, r.o))
             return -2;
     }
     for (const Row &r : rows) lu_tune_put(r.kind, (lu_dtype)r.dt, r.update, r.n, &r.o, r.ms);
@@ -254,6 +258,10 @@ int lu_autotune(lu_dtype dt, int n, int update, double budget_ms, lu_tune_result
             if ((rc = consider(make_opts(best.nb, 0, pc, best.lookahead, update))) != LU_OK) break;
         if (rc != LU_OK) break;
         if (n <= 2048 && (rc = consider(make_opts(best.nb, 0, best.panel_ctas, -1, update))) != LU_OK) break;
+        // tensor-core updates: leave some SMs to the panel chain (a smaller RU2 grid)
+        if (update != LU_UPDATE_NATIVE &&
+            (rc = consider(make_opts(best.nb, 0, best.panel_ctas, best.lookahead, update, 112))) != LU_OK)
+            break;
     } while (false);
     g_bypass = false;
     if (A0) cudaFreeAsync(A0, s);

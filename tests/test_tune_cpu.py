@@ -24,7 +24,7 @@ def test_put_get_clear(L):
     lu.lu_tune_put(lu.TUNE_BATCHED, lu.LU_F32, 256, nb=32, ms=5.0)
     assert lu.lu_tune_count() == 3
     got = lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F64, 4096)
-    assert got == {"nb": 16, "nb_inner": 0, "panel_ctas": 8, "lookahead": 0, "update": 0}
+    assert got == {"nb": 16, "nb_inner": 0, "panel_ctas": 8, "lookahead": 0, "update": 0, "update_ctas": 0}
     # the key includes the update kind and the exact order
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096) is None
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096, update=lu.LU_UPDATE_BF16X3)["nb"] == 128
@@ -55,7 +55,7 @@ def test_put_rejects(L, kind, dt, n, kw, code):
 
 def test_save_load_round_trip(L, tmp_path):
     lu.lu_tune_put(lu.TUNE_FACTOR, lu.LU_F64, 16384, nb=32, panel_ctas=16, lookahead=1, ms=2650.25)
-    lu.lu_tune_put(lu.TUNE_FACTOR, lu.LU_F32, 8192, nb=64, update=lu.LU_UPDATE_FP8, ms=40.0)
+    lu.lu_tune_put(lu.TUNE_FACTOR, lu.LU_F32, 8192, nb=64, update=lu.LU_UPDATE_FP8, update_ctas=120, ms=40.0)
     lu.lu_tune_put(lu.TUNE_BATCHED, lu.LU_F64, 256, nb=16, ms=41.5)
     p = tmp_path / "tune.txt"
     assert lu.lu_tune_save(p) == 3
@@ -70,16 +70,17 @@ def test_save_load_round_trip(L, tmp_path):
 
 
 @pytest.mark.parametrize("line", [
-    "0 0 0 512 32 0 16 1",                 # a field missing
-    "0 0 0 512 32 0 16 1 2.0 extra",       # a field too many
-    "0 0 1 512 32 0 16 1 2.0",             # BF16 update on FP64
-    "1 1 0 256 24 0 0 0 1.0",              # batched width 24
-    "0 0 0 512 32 0 99 1 2.0",             # panel team 99
-    "zero 0 0 512 32 0 16 1 2.0",
+    "0 0 0 512 32 0 16 1 0",               # a field missing
+    "0 0 0 512 32 0 16 1 0 2.0 extra",     # a field too many
+    "0 0 1 512 32 0 16 1 0 2.0",           # BF16 update on FP64
+    "1 1 0 256 24 0 0 0 0 1.0",            # batched width 24
+    "0 0 0 512 32 0 99 1 0 2.0",           # panel team 99
+    "0 1 1 512 64 0 16 1 -3 2.0",          # negative update grid
+    "zero 0 0 512 32 0 16 1 0 2.0",
 ])
 def test_load_refuses_whole_file(L, tmp_path, line):
     p = tmp_path / "bad.txt"
-    p.write_text("# header\n0 0 0 1024 16 0 16 1 5.0\n" + line + "\n")
+    p.write_text("# header\n0 0 0 1024 16 0 16 1 0 5.0\n" + line + "\n")
     with pytest.raises(lu.LuError) as e:
         lu.lu_tune_load(p)
     assert e.value.code == -2

@@ -77,7 +77,7 @@ def test_autotune_records_the_winner(oracle_mod, clean_table, dtype, update, n):
     Ad, pd, infod = _factor(A0, update=update)
     o = r["opts"]
     Ae, pe, infoe = _factor(A0, nb=o["nb"], nb_inner=o["nb_inner"], panel_ctas=o["panel_ctas"],
-                            lookahead=o["lookahead"], update=update)
+                            lookahead=o["lookahead"], update=update, update_ctas=o["update_ctas"])
     torch.cuda.synchronize()
     assert int(infod.item()) == 0 and torch.equal(pd, pe) and torch.equal(Ad.view(torch.uint8), Ae.view(torch.uint8))
     if dtype == "f64":
@@ -108,3 +108,18 @@ def test_autotune_batched(clean_table, dtype):
     # orders above 256 have only the unblocked kernel
     r2 = lu.lu_autotune_batched(code, torch.tensor([300, 17], dtype=torch.int32, device=dev()), 300)
     assert r2["candidates"] == 1 and r2["opts"]["nb"] == 1
+
+
+@pytest.mark.parametrize("update", [1, 2, 3])
+def test_update_grid_cap_keeps_bits(update):
+    """Capping the remainder update's persistent grid (the SM split between panel
+    and update) changes which CTA computes a tile, not its arithmetic."""
+    import torch
+
+    n = 1536
+    A0 = li.uniform_colmajor_torch(n, n, 4400 + update, dev(), torch.float32)
+    ref = _factor(A0, nb=64, update=update)
+    for cap in (1, 37, 96):
+        got = _factor(A0, nb=64, update=update, update_ctas=cap)
+        torch.cuda.synchronize()
+        assert torch.equal(got[1], ref[1]) and torch.equal(got[0].view(torch.uint8), ref[0].view(torch.uint8)), cap
