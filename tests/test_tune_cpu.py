@@ -110,12 +110,13 @@ def test_autotune_argument_errors(L):
 
 def test_plan_info_follows_table(L):
     rc, p = lu.lu_plan_info(lu.LU_F64, 4096)
-    assert rc == 0 and p["nb"] == 32 and p["lookahead"] == 1 and p["panel_ctas"] == 16
-    lu.lu_tune_put(lu.TUNE_FACTOR, lu.LU_F64, 4096, nb=64, panel_ctas=8)
+    assert rc == 0 and p["nb"] == 32 and p["lookahead"] == 1 and p["panel_ctas"] == 8
+    assert lu.lu_plan_info(lu.LU_F64, 16384)[1]["nb"] == 64
+    lu.lu_tune_put(lu.TUNE_FACTOR, lu.LU_F64, 4096, nb=64, panel_ctas=4)
     rc, p = lu.lu_plan_info(lu.LU_F64, 4096)
-    assert rc == 0 and p["nb"] == 64 and p["panel_ctas"] == 8
+    assert rc == 0 and p["nb"] == 64 and p["panel_ctas"] == 4
     rc, p = lu.lu_plan_info(lu.LU_F64, 4096, nb=16)          # explicit fields win
-    assert rc == 0 and p["nb"] == 16 and p["panel_ctas"] == 8
+    assert rc == 0 and p["nb"] == 16 and p["panel_ctas"] == 4
     rc, p = lu.lu_plan_info(lu.LU_F64, 4097)
     assert p["nb"] == 32
 
