@@ -520,6 +520,43 @@ def time_to_solution(args, dev):
             "speedup_vs_fp64": rep64.t_total_ms / rep.t_total_ms if rep.t_total_ms > 0 else None}
 
 
+def fp8_large(args, dev):
+    """Mixed solves with the FP8 e4m3 update at order --mixed-n (65536: FP64 A 32 GiB, FP32
+    factors 16 GiB), nrhs = 16, A = U diag(s) V^T with 256 Householder reflectors per side;
+    one JSON line per kappa with the ladder's report, the backward error recomputed here and
+    the forward error against X_true (column 0 = ones, the others uniform [-1, 1))."""
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    n, nrhs = args.mixed_n, 16
+    for ci, kappa in enumerate(float(k) for k in args.kappas.split(",")):
+        seed = 20161106 + 1000 * 5 + ci
+        t0 = time.perf_counter()
+        A = li.kappa_matrix_torch(n, kappa, seed, MIXED_REFLECTORS, dev)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        Xt = torch.from_numpy(li.uniform(n, nrhs, seed + 1)).to(dev)
+        Xt[:, 0] = 1.0
+        Xt = Xt.t().contiguous()                       # (nrhs, n): row q = right-hand side q
+        B = (A.t() @ Xt.t()).t().contiguous()          # B = A X_true
+        X = torch.zeros_like(B)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rep = lu.lu_solve_mixed(A, B, X, update=lu.LU_UPDATE_FP8)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t1
+        R = B - (A.t() @ X.t()).t()
+        eta = float((R.abs().amax(1) / (A.abs().sum(0).max() * X.abs().amax(1) + B.abs().amax(1))).max())
+        fwd = float((X - Xt).abs().max() / Xt.abs().max())
+        print(json.dumps({"case": "fp8_large", "n": n, "nrhs": nrhs, "kappa": kappa, "seed": seed,
+                          "reflectors_per_side": MIXED_REFLECTORS, "gen_s": gen_s, "wall_s": wall, "eta": eta,
+                          "forward_error": fwd, "report": rep.as_dict()}), flush=True)
+        del A, B, X, Xt, R
+        torch.cuda.empty_cache()
+
+
 def run_case(args):
     """Single-kernel cases for profiling (one launch of the kernel of interest)."""
     import torch
@@ -552,6 +589,9 @@ def run_case(args):
         ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
         lu.lu_factor(A, ipiv, info, update=lu.LU_UPDATE_BF16X3)
+    elif args.case == "fp8_large":
+        fp8_large(args, dev)
+        return
     elif args.case in ("batched_f64", "batched_f32"):
         # the batched workload (10 000 orders in [16, 256]): one factorization launch
         import numpy as np
@@ -598,9 +638,12 @@ def main():
                     help="device time the autotuner may spend per order")
     ap.add_argument("--tune-file", dest="tune_file", default=None,
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
-    ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32"],
+    ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
+                                       "fp8_large"],
                     default=None,
-                    help="run one profiling case instead of the benchmark")
+                    help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
+                         "FP8-update solves, one JSON line per kappa)")
+    ap.add_argument("--kappas", default="1e3,1e6,1e12", help="condition numbers of the fp8_large case")
     args = ap.parse_args()
     if args.case:
         run_case(args)
