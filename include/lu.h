@@ -72,9 +72,13 @@ enum {
 
 /* Tuning knobs.  Pass NULL for the built-in choice; a zero field means "auto". */
 typedef struct {
-    int nb;            /* outer panel width b_o (section 3.1 "algorithmic block size") */
+    int nb;            /* outer panel width b_o (the algorithmic block size of section 3.1);
+                          0 = LU_F64: 32 up to n = 8192, 64 beyond; LU_F32: 128 (SIMT
+                          update) or 64 (tensor-core updates, 128 from n = 24576) */
     int nb_inner;      /* inner panel width b_i (section 4.2, outer vs inner LU) */
-    int panel_ctas;    /* CTAs in the panel cluster, 1..16 (team PF size, section 3.2) */
+    int panel_ctas;    /* CTAs in the panel cluster, 1..16 (team PF size, section 3.2);
+                          0 = 8 for LU_F64, 16 for LU_F32; a panel whose rows do not fit
+                          that many CTAs' register tiles takes more */
     int lookahead;     /* 0 (auto) or 1: static look-ahead with worker sharing;
                           -1: plain blocked RL without look-ahead */
     int update;        /* LU_UPDATE_* (LU_F32 only) */
