@@ -330,10 +330,13 @@ def run_ours(args):
     }
     if rank == 0 and not args.skip_cpu:
         dt, threads = oracle_sample(args.cpu_n, SEED)
+        # the n = 512 factor + solve of the latency line, on the same host cores (best of 5)
+        dt512 = min(oracle_sample(512, 20161106 + 1000 * 1)[0] for _ in range(5))
         line["cpu_baseline"] = {"value": flops_lu(args.cpu_n) / dt / 1e9, "unit": "GFLOP/s", "cores": threads,
                                 "kind": "oracle",
                                 "sample": f"oracle getrf+getrs on a uniform [-1,1) matrix of order {args.cpu_n} "
-                                          f"(same generator), {dt:.1f} s"}
+                                          f"(same generator), {dt:.1f} s",
+                                "n512_us": dt512 * 1e6}
     if rank == 0 and args.tune_file and "loaded" not in tuned:
         lu.lu_tune_save(args.tune_file)
     if rank == 0:
