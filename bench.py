@@ -592,6 +592,16 @@ def run_case(args):
         ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
         lu.lu_factor(A, ipiv, info, update=lu.LU_UPDATE_BF16X3)
+    elif args.case == "solve_f32":
+        # FP32 factors of order 16384 (split-BF16 update), then one solve with one right-hand
+        # side: the refinement step's triangular solves
+        n = 16384
+        A = li.uniform_colmajor_torch(n, n, 5, dev, torch.float32)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        lu.lu_factor(A, ipiv, info, update=lu.LU_UPDATE_BF16X3)
+        b = torch.ones(1, n, dtype=torch.float32, device=dev)
+        lu.lu_solve(A, ipiv, b)
     elif args.case == "fp8_large":
         fp8_large(args, dev)
         return
@@ -642,7 +652,7 @@ def main():
     ap.add_argument("--tune-file", dest="tune_file", default=None,
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
-                                       "fp8_large"],
+                                       "fp8_large", "solve_f32"],
                     default=None,
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")
