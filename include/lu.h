@@ -311,9 +311,10 @@ const char *lu_status_string(int code);
 /*
  * lu_last_device_status -- LU_OK or LU_ERR_TIMEOUT recorded by a bounded
  * device wait since the last reset.  Synchronizes `stream`.  reset != 0 clears
- * it afterwards.
+ * it afterwards.  lu_get_status(stream) is lu_last_device_status(stream, 0).
  */
 int lu_last_device_status(void *stream, int reset);
+int lu_get_status(void *stream);
 
 /*
  * lu_update_timing -- instrumentation of the trailing-update launches (RL3 /

@@ -22,7 +22,7 @@ from . import build as _build_mod
 __all__ = [
     "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8", "LuError", "lib", "build",
     "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
-    "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status",
+    "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status", "lu_get_status",
     "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches",
     "lu_autotune", "lu_autotune_batched", "lu_tune_get", "lu_tune_put", "lu_tune_save", "lu_tune_load", "lu_tune_count",
     "lu_tune_clear", "lu_plan_info", "TUNE_FACTOR", "TUNE_BATCHED", "to_colmajor", "from_colmajor", "MixedReport",
@@ -97,6 +97,8 @@ def lib():
         L.lu_status_string.argtypes = [i]
         L.lu_status_string.restype = ctypes.c_char_p
         L.lu_last_device_status.argtypes = [vp, i]
+        L.lu_get_status.argtypes = [vp]
+        L.lu_get_status.restype = i
         L.lu_version.restype = ctypes.c_char_p
         L.lu_solve_noalloc.argtypes = [i, i, i, vp, i, ip, vp, i, ip, vp]
         L.lu_solve_noalloc.restype = i
@@ -254,6 +256,11 @@ def lu_status_string(code: int) -> str:
 
 def lu_last_device_status(stream=None, reset=False) -> int:
     return lib().lu_last_device_status(_stream(stream), int(bool(reset)))
+
+
+def lu_get_status(stream=None) -> int:
+    """LU_OK or LU_ERR_TIMEOUT recorded by a bounded device wait (synchronizes the stream)."""
+    return lib().lu_get_status(_stream(stream))
 
 
 def lu_update_timing(enable: bool) -> int:

@@ -835,6 +835,8 @@ int lu_last_device_status(void *stream, int reset) {
     return v;
 }
 
+int lu_get_status(void *stream) { return lu_last_device_status(stream, 0); }
+
 int lu_update_timing(int enable) {
     std::lock_guard<std::mutex> lk(g_tmu);
     g_timing = enable != 0;

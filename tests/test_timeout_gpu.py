@@ -23,6 +23,7 @@ def test_withheld_block_times_out_and_device_stays_usable(oracle_mod):
     assert rc == lu.LU_ERR_TIMEOUT
     assert t0.elapsed_time(t1) >= 4.0             # the wait really ran to its bound
     assert lu.lu_last_device_status() == 0        # the library-wide status is untouched
+    assert lu.lu_get_status() == lu.LU_OK
     # the context is intact: a factorization and a solve still give the oracle's answer
     n = 300
     A = li.uniform(n, n, seed=77)
