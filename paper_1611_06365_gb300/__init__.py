@@ -20,7 +20,7 @@ import os
 from . import build as _build_mod
 
 __all__ = [
-    "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8", "LuError", "lib", "build",
+    "LU_OK", "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8", "LuError", "lib", "build",
     "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status", "lu_get_status",
     "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches",
@@ -30,6 +30,7 @@ __all__ = [
 
 LU_F64, LU_F32 = 0, 1
 LU_UPDATE_NATIVE, LU_UPDATE_BF16, LU_UPDATE_BF16X3, LU_UPDATE_FP8 = 0, 1, 2, 3
+LU_OK = 0
 LU_ERR_CUDA, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED = -100, -101, -102, -103
 LU_ERR_SCRATCH = -104
 TUNE_FACTOR, TUNE_BATCHED = 0, 1   # kinds of tuning-table entries
