@@ -75,13 +75,15 @@ static void *upd_worker(void *p)
 }
 
 /* Pivot choice of step j: first index of the largest |A(i, j)|, i = j..m-1.
- * `gap` (optional) receives (|p1| - |p2|) / |p1| for the two largest
- * magnitudes, used to tell true pivot disagreements from near-ties. */
+ * A NaN has no magnitude and never wins a strict comparison, so it is never
+ * chosen; a column with no other entry keeps p = j.  `gap` (optional)
+ * receives (|p1| - |p2|) / |p1| for the two largest magnitudes, used to tell
+ * true pivot disagreements from near-ties. */
 static int pivot_of_column(const double *A, int lda, int m, int j, double *gap)
 {
     int p = j;
-    double best = fabs(AT(A, lda, j, j)), second = -1.0;
-    for (int i = j + 1; i < m; ++i) {
+    double best = -1.0, second = -1.0;
+    for (int i = j; i < m; ++i) {
         double v = fabs(AT(A, lda, i, j));
         if (v > best) { second = best; best = v; p = i; }
         else if (v > second) second = v;

@@ -259,3 +259,23 @@ def test_batched_equals_single(oracle_mod):
         assert np.allclose(xs[t], 1.0, atol=1e-10)
         if t % 2 == 1:
             assert np.array_equal(ipiv, np.arange(1, len(ipiv) + 1))
+
+
+def test_nan_is_never_a_pivot(oracle_mod):
+    """Partial pivoting takes the entry of largest magnitude; a NaN has none and
+    loses every strict comparison, so it is never chosen, also when it sits on
+    the diagonal; a column that is NaN throughout keeps row j."""
+    A = np.array([[np.nan, 1.0, 2.0],
+                  [0.5, 3.0, 1.0],
+                  [-4.0, 1.0, 0.0]])
+    LU, piv, info = oracle_mod.getrf(A)
+    assert piv[0] == 3                                   # |-4| beats 0.5; the NaN is skipped
+    assert np.all(np.isnan(LU[2, :]))                    # the NaN row: NaN multiplier, NaN updates
+    assert np.all(np.isfinite(LU[:2, :]))                # the other rows stay finite
+    B = np.array([[np.nan, 1.0], [np.nan, 2.0]])
+    _, piv2, _ = oracle_mod.getrf(B)
+    assert piv2[0] == 1                                  # no candidate: row j itself
+    # a NaN below a finite diagonal is skipped as well
+    C = np.array([[1.0, 0.0], [np.nan, 1.0]])
+    _, piv3, _ = oracle_mod.getrf(C)
+    assert piv3[0] == 1
