@@ -18,10 +18,16 @@
 //   4. every warp picks the winner from the slots in its own shared memory
 //      (largest magnitude, smallest row on ties); the thread holding row p
 //      takes the old row j, the thread holding row j takes the pivot row, and
-//      every thread scales its rows of column j by IEEE division and applies
-//      the rank-1 update in registers.  The column index is a compile-time
-//      constant in that update (one specialised code block per column), so the
-//      tile never leaves the register file.
+//      every thread scales its rows of column j by the correctly rounded
+//      quotient (FP32: IEEE division; FP64: Markstein's correction from the
+//      reciprocal the candidate's warp computed and pushed with the row) and
+//      applies the rank-1 update in registers.  The column index is a
+//      compile-time constant in that update (one specialised code block per
+//      column), so the tile never leaves the register file.
+//
+// A panel of at most 512 rows (one per thread) whose tile fits one CTA runs
+// on a single CTA: its CTA-wide candidate is the pivot, and steps 2 and 3 are
+// skipped.
 //
 // After each inner panel (when b_o > b_i), still inside the same launch:
 // its interchanges are applied to the panel's other columns (one row map,
