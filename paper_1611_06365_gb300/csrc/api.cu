@@ -22,6 +22,11 @@
 // factored by the inner/outer scheme of section 4.2 (Figure 6): inner panels
 // of width b_i on the cluster, each followed by its interchanges, TRSM and
 // update restricted to the outer panel.
+//
+// Plans: b_o, b_i, the panel team and the RU2 grid come from lu_opts, else
+// from the autotuner's table (tune.cu), else from the built-in choice
+// (make_plan); every panel of a plan is checked to fit a cluster before
+// anything is enqueued.
 #include "common.cuh"
 #include <cuda.h>
 #include <cuda_bf16.h>
