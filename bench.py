@@ -578,13 +578,13 @@ def run_case(args):
         C = li.uniform_colmajor_torch(m, n, 3, dev, torch.float32)
         lu.lu_trailing_update(lu.LU_UPDATE_BF16X3, A, B, C, m, n, k)
     elif args.case == "fp64_factor":
-        # FP64 factorization, n = 8192 (512 MiB), with the plan the autotuner picks for the
-        # n = 16384 workload on GB300 (b_o = 64, an 8-CTA panel team)
+        # FP64 factorization, n = 8192 (512 MiB), by default with the plan the autotuner
+        # picks for the n = 16384 workload on GB300 (b_o = 64, an 8-CTA panel team)
         n = 8192
         A = li.uniform_colmajor_torch(n, n, 5, dev, torch.float64)
         ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
-        lu.lu_factor(A, ipiv, info, nb=64, panel_ctas=8)
+        lu.lu_factor(A, ipiv, info, nb=args.nb or 64, panel_ctas=args.panel_ctas or 8)
     elif args.case == "mixed_factor":
         # FP32 factorization with the split-BF16 update, n = 8192
         n = 8192
@@ -657,6 +657,9 @@ def main():
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")
     ap.add_argument("--kappas", default="1e3,1e6,1e12", help="condition numbers of the fp8_large case")
+    ap.add_argument("--nb", type=int, default=0, help="outer panel width of the fp64_factor case (0: 64)")
+    ap.add_argument("--panel-ctas", dest="panel_ctas", type=int, default=0,
+                    help="panel team of the fp64_factor case (0: 8)")
     args = ap.parse_args()
     if args.case:
         run_case(args)
