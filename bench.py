@@ -568,7 +568,8 @@ def run_case(args):
     import paper_1611_06365_gb300 as lu
 
     dev = torch.device("cuda", 0)
-    lu.build()
+    if args.case != "torch_context":   # the library-context case runs torch only
+        lu.build()
     if args.case == "tc_update":
         # split-BF16 trailing update, C 8192 x 8192 FP32 (256 MiB, larger than L2), K = 256
         m = n = 8192
@@ -602,6 +603,26 @@ def run_case(args):
         lu.lu_factor(A, ipiv, info, update=lu.LU_UPDATE_BF16X3)
         b = torch.ones(1, n, dtype=torch.float32, device=dev)
         lu.lu_solve(A, ipiv, b)
+    elif args.case == "torch_context":
+        # library context (not a target): torch.linalg.lu_factor / solve on the same inputs
+        for n, tdt in ((512, torch.float64), (16384, torch.float64), (16384, torch.float32)):
+            A = li.uniform_colmajor_torch(n, n, 20161106 + 1000 * 2, dev, torch.float64).t().contiguous().to(tdt)
+            b = A @ torch.ones(n, 1, dtype=tdt, device=dev)
+            for name, fn in (("lu_factor", lambda: torch.linalg.lu_factor(A)),
+                             ("solve", lambda: torch.linalg.solve(A, b))):
+                fn()
+                torch.cuda.synchronize()
+                reps = 5 if n <= 4096 else 2
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                print(json.dumps({"case": "torch_context", "routine": f"torch.linalg.{name}", "n": n,
+                                  "dtype": str(tdt).replace("torch.", ""), "ms": ms,
+                                  "gflops": flops_lu(n) / (ms / 1e3) / 1e9}), flush=True)
     elif args.case == "fp8_large":
         fp8_large(args, dev)
         return
@@ -652,7 +673,7 @@ def main():
     ap.add_argument("--tune-file", dest="tune_file", default=None,
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
-                                       "fp8_large", "solve_f32"],
+                                       "fp8_large", "solve_f32", "torch_context"],
                     default=None,
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")
