@@ -651,7 +651,7 @@ def run_case(args):
     print(json.dumps({"case": args.case, "ok": True}))
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -681,7 +681,11 @@ def main():
     ap.add_argument("--nb", type=int, default=0, help="outer panel width of the fp64_factor case (0: 64)")
     ap.add_argument("--panel-ctas", dest="panel_ctas", type=int, default=0,
                     help="panel team of the fp64_factor case (0: 8)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = make_parser().parse_args()
     if args.case:
         run_case(args)
         return
