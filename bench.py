@@ -3,9 +3,14 @@
 mixed-precision time to backward error 1e-14 beside the FP64 one.
 
 A step is one pass of the hot path over one synthetic matrix: restore A
-(n = 16384, entries uniform [-1, 1), FP64, 2 GiB, larger than L2), lu_factor
-(panel, row interchanges, TRSM, trailing update, look-ahead) and lu_solve of
-b = A * ones.  The metric value is LU GFLOP/s = (2/3 n^3) / (time per step).
+(n = 32768, the largest order of the FP64 sweep, entries uniform [-1, 1),
+FP64, 8 GiB, larger than L2), lu_factor (panel, row interchanges, TRSM,
+trailing update, look-ahead) and lu_solve of b = A * ones.  The metric value
+is LU GFLOP/s = (2/3 n^3) / (time per step).  The line also carries the pivot
+agreement with the oracle's stored pivots, the mixed-precision time to
+backward error 1e-14 at n = 16384 for kappa in {1e2, 1e5, 1e8} and 1 or 8
+right-hand sides beside the FP64 path's, the batched workload and the n = 512
+latency.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,14 +35,49 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "LU GFLOP/s (2/3n^3) and time to 1e-14 backward error: mixed vs FP64, 1 GB300"
-N_MAIN = 16384
-SEED = 20161106 + 1000 * 2          # family 2 (blocked FP64 LU sweep), case 0
+N_MAIN = 32768
+FP64_FAMILY = 20161106 + 1000 * 2   # family 2 (blocked FP64 LU sweep)
+FP64_CASE = {4096: 1, 8192: 2, 16384: 0, 32768: 3}   # seed = FP64_FAMILY + case, as in the tests
+SEED = FP64_FAMILY + 0              # the CPU legs' sample matrices
 MIXED_N = 16384
-MIXED_KAPPA = 1e5
-MIXED_REFLECTORS = 256
+MIXED_KAPPAS = (1e2, 1e5, 1e8)
+MIXED_NRHS = (1, 8)
+MIXED_FAMILY = 20161106 + 1000 * 3  # family 3 (mixed-precision solve)
+MIXED_REFLECTORS = 256              # the order-65536 FP8 case (the full product takes too long there)
 SM_COUNT = 152
 FP64_PEAK_TFLOPS = 2 * 2 * SM_COUNT * 2.07e9 / 1e12   # 2 DFMA (4 flop) / clk / SM at 2070 MHz = 1.259
 FP32_PEAK_TFLOPS = 128 * 2 * SM_COUNT * 2.07e9 / 1e12  # 128 FFMA (256 flop) / clk / SM at 2070 MHz = 80.5
+PEAKS_JSON = os.path.join(ROOT, "profiles", "peaks_alu_gb300.json")
+
+
+def fp64_seed(n):
+    return FP64_FAMILY + FP64_CASE.get(n, 0)
+
+
+def _alu_peaks():
+    """Measured FP64 / FP32 ALU peaks (bench --case peaks, committed under profiles/)."""
+    try:
+        with open(PEAKS_JSON) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def fp64_peak():
+    """(TFLOP/s, note): the larger of the measured DFMA and DMMA rates, else the derived figure."""
+    pk = _alu_peaks()
+    vals = [pk.get(k, {}).get("tflops") for k in ("dfma", "dmma")]
+    vals = [v for v in vals if v]
+    if vals:
+        return max(vals), f"measured: max(DFMA, DMMA) probe, {os.path.relpath(PEAKS_JSON, ROOT)}"
+    return FP64_PEAK_TFLOPS, "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (no measured probe on file)"
+
+
+def fp32_peak():
+    pk = _alu_peaks().get("ffma", {}).get("tflops")
+    if pk:
+        return pk, f"measured: FFMA probe, {os.path.relpath(PEAKS_JSON, ROOT)}"
+    return FP32_PEAK_TFLOPS, "derived: 128 FFMA/clk/SM x 152 SMs x 2070 MHz (no measured probe on file)"
 BATCH_COUNT = 10000
 BATCH_SEED = 20161106 + 1000 * 4      # family 4 (batched LU)
 
@@ -198,7 +238,8 @@ def run_ours(args):
     lu.build()
     n = args.n
     # inputs: A (FP64, column-major, 2 GiB at n = 16384) generated on the device
-    A0 = li.uniform_colmajor_torch(n, n, SEED + rank, dev, torch.float64)
+    seed = fp64_seed(n) + rank
+    A0 = li.uniform_colmajor_torch(n, n, seed, dev, torch.float64)
     A = torch.empty_like(A0)
     ones = torch.ones(n, dtype=torch.float64, device=dev)
     b0 = (A0.t() @ ones).view(1, n)            # b = A * ones (column-major A0 holds A^T row-major)
@@ -214,7 +255,12 @@ def run_ours(args):
         tuned["loaded"] = {"file": args.tune_file, "entries": lu.lu_tune_load(args.tune_file)}
         args.no_autotune = True
     if not args.no_autotune:
-        tuned["fp64"] = lu.lu_autotune(lu.LU_F64, n, budget_ms=args.tune_budget_ms)
+        if n <= 16384:
+            tuned["fp64"] = lu.lu_autotune(lu.LU_F64, n, budget_ms=args.tune_budget_ms)
+        else:
+            # one candidate takes ~20 s here: the built-in FP64 plan is the tuner's winner
+            # at n = 16384 (b_o = 64, 8-CTA panel team), also the best of a b_o sweep at 32768
+            tuned["fp64"] = {"opts": lu.lu_plan_info(lu.LU_F64, n)[1], "built_in": True}
 
     def step():
         A.copy_(A0)
@@ -253,13 +299,14 @@ def run_ours(args):
     upd_n, upd_ms, upd_flops, upd_bytes = lu.lu_update_timing_read()
     clk = clocks.stop()
     ms_per_step, value = combine_ranks(e0.elapsed_time(e1), args.steps, flops_lu(n), ws, dev)
+    pivots = pivot_agreement(n, seed, ipiv.cpu().numpy()) if rank == 0 else None
 
     # end-to-end through the C ABI with host buffers (pinned), copies timed
     hA = A0.cpu().pin_memory()
     hb = b0.cpu().pin_memory()
     hx = torch.empty_like(hb).pin_memory()
     hinfo = torch.zeros(1, dtype=torch.int32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 3 if n <= 16384 else 1))
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
@@ -281,12 +328,14 @@ def run_ours(args):
 
     # roofline of the dominant kernel (trailing update, FP64 DFMA)
     achieved = upd_flops / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+    peak64, peak64_note = fp64_peak()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": None,
                 "kernel": "gemm_update_simt<double>", "launches": upd_n,
                 "avg_launch_ms": upd_ms / max(1, upd_n),
                 "flops_per_launch": upd_flops / max(1, upd_n),
-                "peak_note": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz"}
+                "peak_note": peak64_note,
+                "peak_live": live_probe(dev)}
     # measured DRAM bytes per flop of the update at the plan's panel width (the update's
     # depth k): an ncu capture of the same kernel at that k, scaled to the average launch
     _, plan = lu.lu_plan_info(lu.LU_F64, n)
@@ -321,9 +370,11 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"fp64_lu_lookahead_n{n}", "n": n, "lda": n, "nrhs": 1, "seed": SEED,
-                   "entries": "uniform [-1,1)", "l2": "inputs larger than L2 (2 GiB FP64 matrix per step)",
+        "config": {"workload": f"fp64_lu_lookahead_n{n}", "n": n, "lda": n, "nrhs": 1, "seed": seed,
+                   "entries": "uniform [-1,1)",
+                   "l2": f"inputs larger than L2 ({8 * n * n / 2 ** 30:.0f} GiB FP64 matrix restored per step)",
                    "parallelism": f"replicas x{ws}", "eta_fp64": eta,
+                   "pivots_vs_oracle": pivots,
                    "autotuned": tuned or None},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "time_to_solution": tts, "batched": batched, "latency_n512": small,
@@ -343,6 +394,36 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def pivot_agreement(n, seed, ipiv):
+    """The pivot vector of the timed factorization against the oracle's, stored
+    for this (order, seed) by tests/golden/make_oracle_pivots.py (the full oracle
+    takes minutes to an hour at these orders); for orders without a stored
+    vector, None."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_oracle_pivots
+    from _parity import golden_agreement
+
+    gold = make_oracle_pivots.read(n, seed)
+    if gold is None:
+        return None
+    out = golden_agreement(ipiv, gold[0], gold[1], n)
+    out["reference"] = os.path.basename(make_oracle_pivots.golden_path(n, seed))
+    return out
+
+
+def live_probe(dev):
+    """The FP64 peak probes, run now (a fraction of a second each), beside the stored figure."""
+    import paper_1611_06365_gb300 as lu
+
+    out = {}
+    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 16), ("dmma", lu.PROBE_DMMA, 1 << 15)):
+        lu.lu_peak_probe(kind, iters // 16)
+        tf, ms = lu.lu_peak_probe(kind, iters)
+        out[name] = {"tflops": tf, "ms": ms}
+    return out
 
 
 def small_case(dev):
@@ -458,69 +539,101 @@ def batched_case(dev, dtype, steps, tuned=None):
     assert np.all(infos == 0) and err < (1e-6 if dtype == "f64" else 1.0), (dtype, err)
     flops = float(np.sum(2.0 / 3.0 * sizes.astype(np.float64) ** 3 + 2.0 * sizes.astype(np.float64) ** 2))
     lu_ms = step_ms - restore_ms
-    peak = FP64_PEAK_TFLOPS if dtype == "f64" else FP32_PEAK_TFLOPS
+    peak, peak_note = fp64_peak() if dtype == "f64" else fp32_peak()
     achieved = flops / (lu_ms / 1e3) / 1e12
     return {"count": BATCH_COUNT, "n_range": [16, 256], "seed": BATCH_SEED, "graph": True,
             "step_ms": step_ms, "restore_ms": restore_ms, "factor_solve_ms": lu_ms,
             "gflops": flops / (lu_ms / 1e3) / 1e9, "max_abs_err_x_minus_1": err,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "peak_note": "derived: " + ("2 DFMA" if dtype == "f64" else "128 FFMA") +
-                                      "/clk/SM x 152 SMs x 2070 MHz"}}
+                         "frac": achieved / peak, "peak_note": peak_note}}
 
 
 def time_to_solution(args, dev):
-    """Mixed-precision solve vs the FP64 factor+solve, both to eta <= 1e-14."""
+    """Mixed-precision solve vs the FP64 factor + refinement, both to eta <= 1e-14,
+    on the kappa matrices A = U diag(s) V^T (U, V: full products of n seeded
+    Householder reflectors each, one pair shared by the kappas), for every kappa
+    and number of right-hand sides; X_true has column 0 = ones, the others
+    uniform [-1, 1), B = A X_true in FP64."""
     import torch
 
     import lu_inputs as li
     import paper_1611_06365_gb300 as lu
 
     n = args.mixed_n
-    A = li.kappa_matrix_torch(n, MIXED_KAPPA, SEED + 1, MIXED_REFLECTORS, dev)
-    xt = torch.ones(1, n, dtype=torch.float64, device=dev)   # X_true column 0 = ones
-    B = (A.t() @ xt.view(-1)).view(1, n)
-    X = torch.zeros_like(B)
-    lu.lu_solve_mixed(A, B, X)                    # warm-up
-    torch.cuda.synchronize()
-    reps = []
-    for _ in range(2):
-        t0 = time.perf_counter()
-        rep = lu.lu_solve_mixed(A, B, X)
-        torch.cuda.synchronize()
-        reps.append((time.perf_counter() - t0, rep))
-    wall, rep = min(reps, key=lambda r: r[0])
-    # the tensor-core update inside one more run, against the HBM roofline (C in FP32 read
-    # and written once per launch, staged operands read once)
-    lu.lu_update_timing(True)
-    lu.lu_solve_mixed(A, B, X)
-    torch.cuda.synchronize()
-    lu.lu_update_timing(False)
-    u_n, u_ms, u_flops, u_bytes = lu.lu_update_timing_read()
     hbm_peak = _measured_peaks().get("hbm_gbs", 6793.0)
-    tc_roof = None
-    if u_ms > 0:
-        gbs = u_bytes / (u_ms / 1e3) / 1e9
-        tc_roof = {"bound": "hbm", "kernel": "gemm_update_tc<3>", "launches": u_n, "total_ms": u_ms,
-                   "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                   "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"}
-    x = X.view(-1)
-    r = B.view(-1) - A.t() @ x
-    eta = float(r.abs().max() / (A.abs().sum(0).max() * x.abs().max() + B.abs().max()))
-    # the FP64 path to the same target: FP64 factorization, FP64 refinement until eta <= 1e-14
-    X64 = torch.zeros_like(B)
-    rep64 = lu.lu_solve_mixed(A, B, X64, fp64_factor=1)
+    bf16_peak = _measured_peaks().get("bf16_tflops_sustained", 1722.0)
+    t0 = time.perf_counter()
+    Q_u, Vt = li.kappa_factors_torch(n, MIXED_FAMILY + (0 if n == 16384 else 1), n, dev)
     torch.cuda.synchronize()
-    x64 = X64.view(-1)
-    r64 = B.view(-1) - A.t() @ x64
-    eta64 = float(r64.abs().max() / (A.abs().sum(0).max() * x64.abs().max() + B.abs().max()))
-    return {"n": n, "kappa": MIXED_KAPPA, "reflectors_per_side": MIXED_REFLECTORS, "nrhs": 1, "target_eta": 1e-14,
-            "mixed_ms": rep.t_total_ms, "mixed_wall_ms": wall * 1e3, "mixed_factor_ms": rep.t_factor_ms,
-            "mixed_refine_ms": rep.t_refine_ms, "mixed_rung": rep.rung, "mixed_iterations": rep.iterations,
-            "mixed_gmres_iters": rep.gmres_iters, "mixed_eta": eta, "mixed_fell_back": rep.fell_back,
-            "fp64_ms": rep64.t_total_ms, "fp64_iterations": rep64.iterations, "fp64_eta": eta64,
-            "update_roofline": tc_roof,
-            "speedup_vs_fp64": rep64.t_total_ms / rep.t_total_ms if rep.t_total_ms > 0 else None}
+    gen_s = time.perf_counter() - t0
+    plan_bo = None
+    cases = []
+    tc_roof = None
+    for kappa in MIXED_KAPPAS:
+        A = li.kappa_from_factors_torch(Q_u, Vt, kappa)
+        anorm = A.abs().sum(0).max()
+        fp64 = None
+        for nrhs in MIXED_NRHS:
+            Xt = torch.from_numpy(li.uniform(n, nrhs, MIXED_FAMILY + 500 + nrhs)).to(dev)
+            Xt[:, 0] = 1.0
+            Xt = Xt.t().contiguous()                       # (nrhs, n): row q = right-hand side q
+            B = (A.t() @ Xt.t()).t().contiguous()
+            X = torch.zeros_like(B)
+            lu.lu_solve_mixed(A, B, X)                     # warm-up
+            torch.cuda.synchronize()
+            reps = []
+            for _ in range(2):
+                w0 = time.perf_counter()
+                rep = lu.lu_solve_mixed(A, B, X)
+                torch.cuda.synchronize()
+                reps.append((time.perf_counter() - w0, rep))
+            wall, rep = min(reps, key=lambda r: r[0])
+            R = B - (A.t() @ X.t()).t()
+            eta = float((R.abs().amax(1) / (anorm * X.abs().amax(1) + B.abs().amax(1))).max())
+            fwd = float((X - Xt).abs().max() / Xt.abs().max())
+            if plan_bo is None:
+                plan_bo = lu.lu_plan_info(lu.LU_F32, n, update=lu.LU_UPDATE_BF16X3)[1]["nb"]
+            # attainable bound of the factorization: the split-BF16 products (three per pair) at
+            # the sustained BF16 rate, or the FP32 trailing matrix streamed once per panel
+            bound_ms = max(3 * flops_lu(n) / (bf16_peak * 1e12), (8.0 / 3.0) * n ** 3 / plan_bo / (hbm_peak * 1e9)) * 1e3
+            entry = {"kappa": kappa, "nrhs": nrhs, "rung": rep.rung, "iterations": rep.iterations,
+                     "gmres_iters": rep.gmres_iters, "fell_back": rep.fell_back, "eta": eta,
+                     "forward_error": fwd, "forward_error_est": getattr(rep, "forward_error_est", None),
+                     "mixed_ms": rep.t_total_ms, "mixed_wall_ms": wall * 1e3, "factor_ms": rep.t_factor_ms,
+                     "refine_ms": rep.t_refine_ms, "factor_bound_ms": bound_ms,
+                     "factor_frac_of_bound": bound_ms / rep.t_factor_ms if rep.t_factor_ms > 0 else None}
+            if nrhs == 1:
+                # the FP64 path to the same target: FP64 factorization, FP64 refinement
+                X64 = torch.zeros_like(B)
+                rep64 = lu.lu_solve_mixed(A, B, X64, fp64_factor=1)
+                torch.cuda.synchronize()
+                R64 = B - (A.t() @ X64.t()).t()
+                eta64 = float((R64.abs().amax(1) / (anorm * X64.abs().amax(1) + B.abs().amax(1))).max())
+                fp64 = {"fp64_ms": rep64.t_total_ms, "fp64_iterations": rep64.iterations, "fp64_eta": eta64}
+            entry.update(fp64)
+            entry["speedup_vs_fp64"] = fp64["fp64_ms"] / rep.t_total_ms if rep.t_total_ms > 0 else None
+            cases.append(entry)
+            if tc_roof is None:
+                # the tensor-core update inside one more run, against the HBM roofline (C in FP32
+                # read and written once per launch, staged operands read once)
+                lu.lu_update_timing(True)
+                lu.lu_solve_mixed(A, B, X)
+                torch.cuda.synchronize()
+                lu.lu_update_timing(False)
+                u_n, u_ms, u_flops, u_bytes = lu.lu_update_timing_read()
+                if u_ms > 0:
+                    gbs = u_bytes / (u_ms / 1e3) / 1e9
+                    tc_roof = {"bound": "hbm", "kernel": "gemm_update_tc<3>", "launches": u_n, "total_ms": u_ms,
+                               "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                               "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+            del B, X, Xt, R
+        del A
+    del Q_u, Vt
+    torch.cuda.empty_cache()
+    head = next(c for c in cases if c["kappa"] == 1e5 and c["nrhs"] == 1)
+    return {"n": n, "reflectors_per_side": n, "target_eta": 1e-14, "generation_s": gen_s, "plan_nb": plan_bo,
+            "cases": cases, "update_roofline": tc_roof,
+            "mixed_ms": head["mixed_ms"], "fp64_ms": head["fp64_ms"], "speedup_vs_fp64": head["speedup_vs_fp64"]}
 
 
 def fp8_large(args, dev):
@@ -558,6 +671,46 @@ def fp8_large(args, dev):
                           "forward_error": fwd, "report": rep.as_dict()}), flush=True)
         del A, B, X, Xt, R
         torch.cuda.empty_cache()
+
+
+def measure_peaks(dev):
+    """ALU peaks on this GPU: DFMA, DMMA and FFMA throughput probes (lu_peak_probe), each
+    a launch of about a second after a short warm-up, with the SM clocks sampled
+    during the probes; FP8 e4m3 and BF16 library GEMMs (torch) as context points."""
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+
+    out = {"gpu": torch.cuda.get_device_name(dev), "how": "lu_peak_probe: 4 CTAs x 256 threads per SM, "
+           "8 (FMA) or 4 (DMMA) independent chains per thread/warp; CUDA events around one launch"}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 20), ("dmma", lu.PROBE_DMMA, 1 << 19),
+                              ("ffma", lu.PROBE_FFMA, 1 << 24)):
+        lu.lu_peak_probe(kind, iters // 64)
+        tf, ms = lu.lu_peak_probe(kind, iters)
+        out[name] = {"tflops": tf, "ms": ms, "iters": iters}
+    out["clocks"] = clocks.stop()
+    lib_pts = {}
+    try:
+        m = 8192
+        a = torch.randn(m, m, device=dev).to(torch.float8_e4m3fn)
+        b = torch.randn(m, m, device=dev).to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        e1.record()
+        torch.cuda.synchronize()
+        lib_pts["fp8_e4m3_scaled_mm_8192"] = 2.0 * m ** 3 * 10 / (e0.elapsed_time(e1) / 1e3) / 1e12
+    except Exception as exc:   # a library context point only
+        lib_pts["fp8_e4m3_scaled_mm_8192"] = f"unavailable: {type(exc).__name__}"
+    out["library_tflops"] = lib_pts
+    return out
 
 
 def run_case(args):
@@ -626,6 +779,13 @@ def run_case(args):
     elif args.case == "fp8_large":
         fp8_large(args, dev)
         return
+    elif args.case == "peaks":
+        print(json.dumps(measure_peaks(dev)), flush=True)
+        return
+    elif args.case == "c3_grid":
+        # the mixed-precision time-to-solution grid alone, at order --mixed-n
+        print(json.dumps({"case": "c3_grid", "time_to_solution": time_to_solution(args, dev)}), flush=True)
+        return
     elif args.case in ("batched_f64", "batched_f32"):
         # the batched workload (10 000 orders in [16, 256]): one factorization launch
         import numpy as np
@@ -654,7 +814,7 @@ def run_case(args):
 def make_parser():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_MAIN)
@@ -673,7 +833,7 @@ def make_parser():
     ap.add_argument("--tune-file", dest="tune_file", default=None,
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
-                                       "fp8_large", "solve_f32", "torch_context"],
+                                       "fp8_large", "solve_f32", "torch_context", "peaks", "c3_grid"],
                     default=None,
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")

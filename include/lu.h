@@ -35,6 +35,11 @@
  *  - Every device-side wait between CTAs is bounded; when a bound expires the
  *    kernel records LU_ERR_TIMEOUT in a library status word (see
  *    lu_last_device_status) and returns instead of hanging.
+ *  - The library keeps per-device state created on first use (two streams,
+ *    events, the status word, the device address of lu_solve_noalloc's
+ *    scratch array).  cudaDeviceReset destroys the context that state lives
+ *    in: after a reset, unload and reload the library before calling it on
+ *    that device again.
  */
 #ifndef GB300_LU_H
 #define GB300_LU_H
@@ -199,6 +204,9 @@ typedef struct {
     double t_factor_ms;  /* device time of the FP32 factorization */
     double t_refine_ms;  /* device time of refinement (and fallback) */
     double t_total_ms;   /* device time of the whole call */
+    double forward_error_est;  /* estimate of max_q ||x_q - x*_q||_inf / ||x_q||_inf: the size of
+                            the last refinement correction relative to the solution (Demmel et
+                            al., ACM TOMS 32(2), 2006); INFINITY if no correction was made */
 } lu_mixed_report;
 
 /*
@@ -377,6 +385,21 @@ int lu_wait_selftest(long long bound_ns, void *stream);
  * synchronizing the stream; negative on an argument or CUDA error.
  */
 long long lu_div_selftest(lu_dtype dt, long long count, unsigned long long seed, void *stream);
+
+/*
+ * lu_peak_probe -- measured throughput of the arithmetic units the FP64 and
+ * FP32 paths run on, for roofline denominators (instrumentation; the paper
+ * reports its CPU's peak the same way, as flops per cycle times the clock).
+ *   kind 0: FP64 fused multiply-adds on the CUDA cores (DFMA);
+ *        1: FP32 fused multiply-adds (FFMA);
+ *        2: mma.sync m8n8k4 with FP64 operands (DMMA).
+ *   iters: dependent steps per chain (each thread or warp runs 8 or 4
+ *   independent chains; 4 CTAs of 256 threads per SM).  Launches one kernel
+ *   on `stream`, times it with CUDA events and synchronizes.  *tflops (host)
+ *   receives flops / time / 1e12, *ms the kernel time; either may be NULL.
+ *   Returns 0, -1 (bad kind), -2 (iters <= 0) or LU_ERR_CUDA.
+ */
+int lu_peak_probe(int kind, long long iters, double *tflops, double *ms, void *stream);
 
 /* Number of CUDA kernels this library has launched since it was loaded. */
 long long lu_kernel_launches(void);

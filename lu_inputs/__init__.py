@@ -73,11 +73,18 @@ def uniform(m: int, n: int | None = None, seed: int = 0, lo: float = -1.0) -> np
     (2u - 1 needs at most 53 bits).  lo = 0 gives the paper's (0, 1) variant.
     """
     n = m if n is None else n
-    c = np.arange(m * n, dtype=np.uint64)
-    u = unit_uniform(splitmix64(seed, c))
-    v = lo + (1.0 - lo) * u if lo != -1.0 else 2.0 * u - 1.0
-    # counter j*m + i -> column-major fill
-    return v.reshape(n, m).T.copy()
+    # counter j*m + i -> column-major fill, generated a block of columns at a
+    # time to bound the temporaries; large matrices come back Fortran-ordered
+    # (same values, no transposing copy)
+    out = np.empty((n, m), dtype=np.float64)
+    cols = max(1, (1 << 24) // max(m, 1))
+    for j0 in range(0, n, cols):
+        j1 = min(n, j0 + cols)
+        c = np.arange(j0 * m, j1 * m, dtype=np.uint64)
+        u = unit_uniform(splitmix64(seed, c))
+        v = lo + (1.0 - lo) * u if lo != -1.0 else 2.0 * u - 1.0
+        out[j0:j1] = v.reshape(j1 - j0, m)
+    return out.T.copy() if m * n <= (1 << 24) else out.T
 
 
 def uniform_colmajor_torch(m: int, n: int, seed: int, device, dtype=None, ld: int | None = None):
@@ -228,6 +235,27 @@ def kappa_matrix_torch(n: int, kappa: float, seed: int, k: int, device, block: i
     import torch
 
     s = torch.from_numpy(kappa_singular_values(n, kappa)).to(device)
+    Q_u, Vt = kappa_factors_torch(n, seed, k, device, block)
+    A = Q_u @ (s[:, None] * Vt)
+    return A.T.contiguous()  # row j = column j
+
+
+def kappa_from_factors_torch(Q_u, Vt, kappa: float):
+    """A = U diag(s) V^T for the factors of ``kappa_factors_torch`` (one library
+    product per kappa), in the device column-major layout."""
+    import torch
+
+    n = Q_u.shape[0]
+    s = torch.from_numpy(kappa_singular_values(n, kappa)).to(Q_u.device)
+    return (Q_u @ (s[:, None] * Vt)).T.contiguous()
+
+
+def kappa_factors_torch(n: int, seed: int, k: int, device, block: int = 64):
+    """(U, V^T) of ``kappa_matrix``: U = H_1..H_k from the reflectors of
+    ``seed``, V likewise from ``seed + 1``, both explicit FP64 n x n (row-major
+    torch tensors).  Shared by every kappa of one (order, seed)."""
+    import torch
+
     Vu = torch.from_numpy(householder_vectors(n, k, seed)).to(device)
     Vv = torch.from_numpy(householder_vectors(n, k, seed + 1)).to(device)
 
@@ -250,9 +278,9 @@ def kappa_matrix_torch(n: int, kappa: float, seed: int, k: int, device, block: i
         return X
 
     Vt = apply_left(Vv, torch.eye(n, dtype=torch.float64, device=device)).T.contiguous()
-    X = s[:, None] * Vt
-    A = apply_left(Vu, X)
-    return A.T.contiguous()  # row j = column j
+    del Vv
+    Q_u = apply_left(Vu, torch.eye(n, dtype=torch.float64, device=device))
+    return Q_u, Vt
 
 
 def batch_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:

@@ -53,6 +53,8 @@ def _load():
         d, i = ctypes.c_double, ctypes.c_int
         lib.oracle_getrf.argtypes = [i, i, P(d), i, P(i), P(d), i]
         lib.oracle_getrf.restype = i
+        lib.oracle_getrf_forced.argtypes = [i, i, P(d), i, P(i), P(d), i, P(i)]
+        lib.oracle_getrf_forced.restype = i
         lib.oracle_getrs.argtypes = [i, i, P(d), i, P(i), P(d), i]
         lib.oracle_getrs.restype = i
         lib.oracle_apply_pivots.argtypes = [i, i, P(d), i, P(i), i]
@@ -82,16 +84,28 @@ def default_threads() -> int:
     return max(1, len(os.sched_getaffinity(0)))
 
 
-def getrf(A, nthreads: int = 1, want_gaps: bool = False):
-    """Return (LU, ipiv, info[, gaps]) for the m x n matrix A (copied)."""
+def getrf(A, nthreads: int = 1, want_gaps: bool = False, forced=None):
+    """Return (LU, ipiv, info[, gaps]) for the m x n matrix A (copied).
+
+    ``forced`` (optional, length min(m, n)): 1-based pivot rows imposed on
+    the elimination, 0 where the step searches as usual (the near-tie rule:
+    re-run with another implementation's choice at a step whose top-2 gap is
+    within rounding).  ``gaps`` are always the search's own top-2 gaps."""
     lib = _load()
     F = _fortran(A).copy(order="F")
     m, n = F.shape
     k = min(m, n)
     ipiv = np.zeros(max(k, 1), dtype=np.int32)
     gaps = np.zeros(max(k, 1), dtype=np.float64) if want_gaps else None
-    info = lib.oracle_getrf(m, n, _dp(F), max(m, 1), _ip(ipiv),
-                            _dp(gaps) if want_gaps else None, int(nthreads))
+    if forced is None:
+        info = lib.oracle_getrf(m, n, _dp(F), max(m, 1), _ip(ipiv),
+                                _dp(gaps) if want_gaps else None, int(nthreads))
+    else:
+        fz = np.full(max(k, 1), -1, dtype=np.int32)
+        f = np.asarray(forced, dtype=np.int64)[:k]
+        fz[:len(f)] = np.where(f > 0, f - 1, -1)
+        info = lib.oracle_getrf_forced(m, n, _dp(F), max(m, 1), _ip(ipiv),
+                                       _dp(gaps) if want_gaps else None, int(nthreads), _ip(fz))
     if info < 0:
         raise ValueError("oracle_getrf: bad argument")
     out = (F, ipiv[:k], info)

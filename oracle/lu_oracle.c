@@ -92,11 +92,31 @@ static int pivot_of_column(const double *A, int lda, int m, int j, double *gap)
     return p;
 }
 
+/* oracle_getrf_forced: oracle_getrf in which the pivot of step j is row
+ * forced[j] (0-based, j <= forced[j] < m) wherever forced != NULL and
+ * forced[j] >= 0; every other step searches as usual.  It serves the near-tie
+ * rule of the parity tests: when another implementation picks a different
+ * pivot at a step whose top-2 gap is within rounding, the elimination is
+ * re-run with that choice and compared from there on.  gaps[j] still reports
+ * the search's own top-2 gap.  Returns -1 for a bad argument or a forced row
+ * outside j..m-1 (A is then partly eliminated). */
+int oracle_getrf_forced(int m, int n, double *A, int lda, int *ipiv, double *gaps, int nthreads,
+                        const int *forced);
+
 int oracle_getrf(int m, int n, double *A, int lda, int *ipiv, double *gaps, int nthreads)
+{
+    return oracle_getrf_forced(m, n, A, lda, ipiv, gaps, nthreads, NULL);
+}
+
+int oracle_getrf_forced(int m, int n, double *A, int lda, int *ipiv, double *gaps, int nthreads,
+                        const int *forced)
 {
     if (m < 0 || n < 0 || lda < (m > 1 ? m : 1)) return -1;
     int info = 0;
     int kmax = m < n ? m : n;
+    if (forced)
+        for (int j = 0; j < kmax; ++j)
+            if (forced[j] >= m || (forced[j] >= 0 && forced[j] < j)) return -1;
     if (nthreads < 1) nthreads = 1;
     pthread_barrier_t bar;
     pthread_t *th = NULL;
@@ -113,6 +133,7 @@ int oracle_getrf(int m, int n, double *A, int lda, int *ipiv, double *gaps, int 
     }
     for (int j = 0; j < kmax; ++j) {
         int p = pivot_of_column(A, lda, m, j, gaps ? &gaps[j] : NULL);
+        if (forced && forced[j] >= 0) p = forced[j];
         ipiv[j] = p + 1;
         int zero = (AT(A, lda, p, j) == 0.0);
         if (zero) {

@@ -25,7 +25,7 @@ __all__ = [
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status", "lu_get_status",
     "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches",
     "lu_autotune", "lu_autotune_batched", "lu_tune_get", "lu_tune_put", "lu_tune_save", "lu_tune_load", "lu_tune_count",
-    "lu_tune_clear", "lu_plan_info", "TUNE_FACTOR", "TUNE_BATCHED", "to_colmajor", "from_colmajor", "MixedReport",
+    "lu_tune_clear", "lu_plan_info", "lu_peak_probe", "PROBE_DFMA", "PROBE_FFMA", "PROBE_DMMA", "TUNE_FACTOR", "TUNE_BATCHED", "to_colmajor", "from_colmajor", "MixedReport",
 ]
 
 LU_F64, LU_F32 = 0, 1
@@ -34,6 +34,7 @@ LU_OK = 0
 LU_ERR_CUDA, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED = -100, -101, -102, -103
 LU_ERR_SCRATCH = -104
 TUNE_FACTOR, TUNE_BATCHED = 0, 1   # kinds of tuning-table entries
+PROBE_DFMA, PROBE_FFMA, PROBE_DMMA = 0, 1, 2   # lu_peak_probe kinds
 LU_TRACE_KINDS = ("panel", "swap_left", "ru1", "pf1", "pf2", "ru2")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,7 +67,8 @@ class MixedOpts(ctypes.Structure):
 class MixedReport(ctypes.Structure):
     _fields_ = [("rung", ctypes.c_int), ("iterations", ctypes.c_int), ("gmres_iters", ctypes.c_int),
                 ("fell_back", ctypes.c_int), ("info", ctypes.c_int), ("backward_error", ctypes.c_double),
-                ("t_factor_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+                ("t_factor_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
+                ("forward_error_est", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -124,6 +126,9 @@ def lib():
         L.lu_tune_save.argtypes = [ctypes.c_char_p]
         L.lu_tune_load.argtypes = [ctypes.c_char_p]
         L.lu_tune_clear.restype = None
+        L.lu_peak_probe.argtypes = [i, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), vp]
+        L.lu_peak_probe.restype = i
         L.lu_plan_info.argtypes = [i, i, ctypes.POINTER(LuOpts), ctypes.POINTER(LuOpts)]
         L.lu_plan_info.restype = i
         for f in ("lu_autotune", "lu_autotune_batched", "lu_tune_get", "lu_tune_put", "lu_tune_save", "lu_tune_load",
@@ -303,6 +308,13 @@ def lu_wait_selftest(bound_ns: int, stream=None) -> int:
 def lu_div_selftest(dtype_code: int, count: int, seed: int = 1, stream=None) -> int:
     """Pairs on which the substitutions' quotient differs from IEEE division (0 expected)."""
     return lib().lu_div_selftest(dtype_code, int(count), int(seed), _stream(stream))
+
+
+def lu_peak_probe(kind: int, iters: int, stream=None):
+    """(TFLOP/s, ms) of one throughput-probe launch (PROBE_DFMA, PROBE_FFMA or PROBE_DMMA)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check("lu_peak_probe", lib().lu_peak_probe(kind, int(iters), ctypes.byref(tf), ctypes.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 def lu_kernel_launches() -> int:

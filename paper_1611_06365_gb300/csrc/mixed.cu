@@ -111,6 +111,18 @@ __global__ void axpy_scaled_kernel(int n, int nrhs, const float *__restrict__ D3
     }
 }
 
+// out[q] = bits of max_i |s_q D32(i, q)|: the size of the correction axpy_scaled adds
+__global__ void absmax_scaled_f32_kernel(int n, int nrhs, const float *__restrict__ D32, int ldd,
+                                         const unsigned long long *__restrict__ rmax, unsigned long long *__restrict__ out) {
+    const size_t total = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), q = (int)(e / n);
+        double s = __longlong_as_double((long long)rmax[q]);
+        if (!(s > 0.0) || isinf(s)) s = 1.0;
+        atomicMax(&out[q], (unsigned long long)__double_as_longlong(fabs(s * (double)D32[(size_t)i + (size_t)q * ldd])));
+    }
+}
+
 __global__ void axpy_f64_kernel(int n, int nrhs, const double *__restrict__ D, int ldd, double *__restrict__ X, int ldx) {
     const size_t total = (size_t)n * nrhs;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -158,6 +170,15 @@ cudaError_t launch_absmax(int n, int nrhs, const double *V, int ldv, unsigned lo
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long) * nrhs, s);
     if (e != cudaSuccess || n <= 0) return e;
     absmax_kernel<<<grid_for((size_t)n * nrhs), 256, 0, s>>>(n, nrhs, V, ldv, out);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax_scaled_f32(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax,
+                                     unsigned long long *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long) * nrhs, s);
+    if (e != cudaSuccess || n <= 0) return e;
+    absmax_scaled_f32_kernel<<<grid_for((size_t)n * nrhs), 256, 0, s>>>(n, nrhs, D32, ldd, rmax, out);
     lu_count_launch();
     return cudaGetLastError();
 }

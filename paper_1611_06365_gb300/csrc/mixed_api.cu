@@ -14,6 +14,12 @@
 //   eta = max_q ||b_q - A x_q||_inf / (||A||_inf ||x_q||_inf + ||b_q||_inf)
 // at most `tol`.  Stall: eta has not halved over the last two steps, or
 // max_iter steps were taken on the rung.
+// Forward-error estimate: the size of the last correction relative to the
+// solution, max_q ||d_q||_inf / ||x_q||_inf, the estimate refinement gives for
+// free (Demmel, Hida, Kahan, Li, Mukherjee and Riedy, "Error bounds from
+// extra-precise iterative refinement", ACM TOMS 32(2), 2006): once refinement
+// contracts, the error left after the last correction is below that
+// correction's size.
 #include "common.cuh"
 #include <algorithm>
 #include <chrono>
@@ -37,9 +43,11 @@ cudaError_t launch_to_f32_scaled(int n, int nrhs, const double *R, int ldr, cons
 cudaError_t launch_axpy_scaled(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax, double *X, int ldx,
                                cudaStream_t s);
 cudaError_t launch_axpy_f64(int n, int nrhs, const double *D, int ldd, double *X, int ldx, cudaStream_t s);
+cudaError_t launch_absmax_scaled_f32(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax,
+                                     unsigned long long *out, cudaStream_t s);
 int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb, double *X, int ldx, const float *LU32,
              int ld32, const int *perm, double anorm, const double *bnorm, double tol, int max_outer, int restart,
-             int *iters_out, int *inner_out, double *eta_out, cudaStream_t s);
+             int *iters_out, int *inner_out, double *eta_out, double *ferr_out, cudaStream_t s);
 }  // namespace lu
 
 using namespace lu;
@@ -71,6 +79,24 @@ double bits_to_double(unsigned long long b) {
 }
 
 }  // namespace
+
+// max_q ||d_q||_inf / ||x_q||_inf from device norms (synchronizes s)
+static int ferr_now(int nrhs, const unsigned long long *d_dmax, const unsigned long long *d_xmax, double *ferr,
+                    cudaStream_t s) {
+    std::vector<unsigned long long> h(2 * (size_t)nrhs);
+    LU_CUDA_TRY(cudaMemcpyAsync(h.data(), d_dmax, sizeof(unsigned long long) * nrhs, cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaMemcpyAsync(h.data() + nrhs, d_xmax, sizeof(unsigned long long) * nrhs, cudaMemcpyDeviceToHost, s));
+    LU_CUDA_TRY(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    for (int q = 0; q < nrhs; ++q) {
+        const double d = bits_to_double(h[q]), x = bits_to_double(h[nrhs + q]);
+        double f = x > 0.0 ? d / x : (d > 0.0 ? INFINITY : 0.0);
+        if (std::isnan(f)) f = INFINITY;
+        worst = std::max(worst, f);
+    }
+    *ferr = worst;
+    return LU_OK;
+}
 
 // eta for each column from device norms (synchronizes s)
 static int eta_now(int nrhs, const unsigned long long *d_rmax, const unsigned long long *d_xmax, double anorm,
@@ -129,7 +155,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     float *A32 = nullptr, *R32 = nullptr;
     int *ipiv = nullptr, *perm = nullptr, *info = nullptr;
     double *rowsum = nullptr, *R = nullptr, *part = nullptr;
-    unsigned long long *norms = nullptr;   // [0] anorm, [1..nrhs] rmax, [1+nrhs..] xmax, [1+2nrhs..] bmax
+    unsigned long long *norms = nullptr;   // [0] anorm, [1..nrhs] rmax, [1+nrhs..] xmax, [1+2nrhs..] bmax, [1+3nrhs..] dmax
     LU_CUDA_TRY(ws.get(&A32, (size_t)ld32 * n));
     LU_CUDA_TRY(ws.get(&R32, (size_t)n * nrhs));
     LU_CUDA_TRY(ws.get(&ipiv, n));
@@ -138,8 +164,9 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     LU_CUDA_TRY(ws.get(&rowsum, n));
     LU_CUDA_TRY(ws.get(&R, (size_t)n * nrhs));
     LU_CUDA_TRY(ws.get(&part, residual_workspace_doubles(n, nrhs)));
-    LU_CUDA_TRY(ws.get(&norms, 1 + 3 * (size_t)nrhs));
+    LU_CUDA_TRY(ws.get(&norms, 1 + 4 * (size_t)nrhs));
     unsigned long long *d_anorm = norms, *d_rmax = norms + 1, *d_xmax = norms + 1 + nrhs, *d_bmax = norms + 1 + 2 * nrhs;
+    unsigned long long *d_dmax = norms + 1 + 3 * nrhs;
 
     // ||A||_inf and ||b||_inf
     LU_CUDA_TRY(launch_cast_rowsum(n, dA, lda, A32, ld32, rowsum, s));
@@ -172,7 +199,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
                                   cudaMemcpyDeviceToDevice, s));
     LU_CUDA_TRY(cudaMemcpyAsync(d_rmax, d_bmax, sizeof(unsigned long long) * nrhs, cudaMemcpyDeviceToDevice, s));
-    double eta = 1.0;
+    double eta = 1.0, ferr = INFINITY;
     std::vector<double> hist;
     bool done = false;
     if (hinfo == 0 && !fp64_only) {
@@ -180,10 +207,13 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
             rc = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
             if (rc != LU_OK) return rc;
+            LU_CUDA_TRY(launch_absmax_scaled_f32(n, nrhs, R32, n, d_rmax, d_dmax, s));   // size of the correction
             LU_CUDA_TRY(launch_axpy_scaled(n, nrhs, R32, n, d_rmax, dX, ldx, s));
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
             LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
             rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+            if (rc != LU_OK) return rc;
+            rc = ferr_now(nrhs, d_dmax, d_xmax, &ferr, s);
             if (rc != LU_OK) return rc;
             r.iterations++;
             hist.push_back(eta);
@@ -196,9 +226,12 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     if (!done && hinfo == 0 && allow_gmres && !fp64_only) {
         r.rung = 1;
         int outer = 0, inner = 0;
+        double ferr1 = 0.0;
         rc = gmres_ir(n, nrhs, dA, lda, dB, ldb, dX, ldx, A32, ld32, perm, anorm, bnorm.data(), tol, max_iter, restart, &outer,
-                      &inner, &eta, s);
+                      &inner, &eta, &ferr1, s);
         if (rc != LU_OK) return rc;
+        // a column GMRES-IR did not correct keeps its estimate from rung 0 (max: conservative)
+        ferr = r.iterations > 0 ? std::max(ferr, ferr1) : ferr1;
         r.iterations += outer;
         r.gmres_iters += inner;
         done = eta <= tol;
@@ -226,10 +259,13 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
             rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
             if (rc != LU_OK) return rc;
+            LU_CUDA_TRY(launch_absmax(n, nrhs, D, n, d_dmax, s));      // size of the correction
             LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));   // X += D
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
             LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
             rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+            if (rc != LU_OK) return rc;
+            rc = ferr_now(nrhs, d_dmax, d_xmax, &ferr, s);
             if (rc != LU_OK) return rc;
             r.iterations++;
             if (eta <= tol) break;
@@ -245,6 +281,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     r.t_refine_ms = t12;
     r.t_total_ms = (double)t01 + t12;
     r.backward_error = eta;
+    r.forward_error_est = ferr;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);

@@ -31,8 +31,10 @@ def leibniz_det(A):
     return total
 
 
-def rational_gepp(A):
-    """Return (ipiv 1-based, L, U) as lists of Fractions; raises on singular."""
+def rational_gepp(A, forced=None):
+    """Return (ipiv 1-based, L, U) as lists of Fractions; raises on singular.
+
+    ``forced``: optional 1-based pivot rows imposed at some steps (0 = search)."""
     n = len(A)
     M = [[Fraction(x) for x in row] for row in A]
     ipiv = []
@@ -41,6 +43,8 @@ def rational_gepp(A):
         for i in range(j + 1, n):
             if abs(M[i][j]) > abs(M[p][j]):
                 p = i
+        if forced is not None and forced[j] > 0:
+            p = forced[j] - 1
         ipiv.append(p + 1)
         if M[p][j] == 0:
             raise ZeroDivisionError("singular")

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import lu_inputs as li
+from tests._parity import oracle_parity
 from tests.gpu_util import EPS32, EPS64, expected_ipiv, factor_gpu
 
 pytestmark = pytest.mark.gpu
@@ -19,9 +20,10 @@ pytestmark = pytest.mark.gpu
 def _parity_f64(oracle_mod, A, **opts):
     n = A.shape[0]
     LU, ipiv, info, _, _ = factor_gpu(A, "f64", **opts)
-    LUo, pivo, infoo = oracle_mod.getrf(A, nthreads=oracle_mod.default_threads())
+    infoo = oracle_mod.getrf(A)[2]
     assert info == infoo
-    assert np.array_equal(ipiv, pivo), f"first pivot mismatch at {np.argmax(ipiv != pivo)}"
+    # whole pivot vector, near-tie rule (tests/_parity.py)
+    LUo, _ = oracle_parity(oracle_mod, A, ipiv)
     r, a = oracle_mod.lu_residual_fro(A, LU, ipiv)
     assert r / a <= 10 * n * EPS64
     assert np.max(np.abs(LU - LUo)) <= 10 * n * EPS64 * max(1.0, np.max(np.abs(LUo)))

@@ -69,6 +69,17 @@ def test_kappa_torch_matches_numpy():
     assert np.allclose(li.from_device_colmajor(T, n), A, atol=1e-13)
 
 
+def test_kappa_shared_factors_match():
+    """One (U, V^T) pair serves every kappa: the same matrices as building each anew."""
+    torch = pytest.importorskip("torch")
+    n = 64
+    Q_u, Vt = li.kappa_factors_torch(n, seed=11, k=n, device="cpu", block=16)
+    for kappa in (1e2, 1e8):
+        A = li.kappa_matrix(n, kappa, seed=11, k=n)
+        T = li.kappa_from_factors_torch(Q_u, Vt, kappa)
+        assert np.allclose(li.from_device_colmajor(T, n), A, atol=1e-13)
+
+
 def test_batch_sizes_range():
     s = li.batch_sizes(10000, 16, 256, seed=4)
     assert s.min() == 16 and s.max() == 256

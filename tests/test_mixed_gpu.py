@@ -168,7 +168,13 @@ def test_mixed_kappa_ladder(oracle_mod, kappa, rung_max):
     assert eta <= 1e-14, (rep.as_dict(), eta)
     assert rep.rung <= rung_max
     # forward error within kappa * eta (with a safety factor)
-    assert np.max(np.abs(X - xt)) / np.max(np.abs(xt)) <= 100 * kappa * max(eta, 1e-16)
+    fwd = np.max(np.abs(X - xt)) / np.max(np.abs(xt))
+    assert fwd <= 100 * kappa * max(eta, 1e-16)
+    # the report's estimate (size of the last correction): the error left is below it,
+    # up to the attainable accuracy kappa * eps of an FP64 residual
+    est = rep.forward_error_est
+    assert np.isfinite(est) and est > 0.0
+    assert fwd <= 10 * max(est, kappa * np.finfo(float).eps), (fwd, est)
 
 
 @pytest.mark.parametrize("kind,rung_max", [("dominant", 0), ("kappa10", 1), ("kappa1e3", 2)])

@@ -279,3 +279,55 @@ def test_nan_is_never_a_pivot(oracle_mod):
     C = np.array([[1.0, 0.0], [np.nan, 1.0]])
     _, piv3, _ = oracle_mod.getrf(C)
     assert piv3[0] == 1
+
+
+def test_forced_pivot_hand_worked(oracle_mod):
+    """The near-tie rule's re-run: a pivot imposed at one step, the others
+    searched; hand-worked in tests/golden/lu3x3_forced.txt."""
+    g = _read_golden("lu3x3_forced.txt")
+    A = np.array([[float(x) for x in r] for r in g["A"]])
+    forced = [int(x) for x in g["forced"][0]]
+    LU, ipiv, info = oracle_mod.getrf(A, forced=forced)
+    assert info == 0
+    assert list(ipiv) == [int(x) for x in g["ipiv"][0]]
+    L, U = oracle_mod.unpack(LU)
+    # every value here is a dyadic rational reached exactly
+    assert np.array_equal(L, np.array([[float(x) for x in r] for r in g["L"]]))
+    assert np.array_equal(U, np.array([[float(x) for x in r] for r in g["U"]]))
+    det = np.prod(np.diag(U)) * (-1) ** int(np.sum(ipiv != np.arange(1, 4)))
+    assert det == float(g["det"][0][0])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_forced_pivots_match_exact_rational(oracle_mod, seed):
+    """Forced choices at random steps (any row at or below the diagonal), the
+    rest searched: pivots equal exact rational elimination with the same choices."""
+    n = 4 + seed
+    h = li.splitmix64(5000 + seed, np.arange(n * n + n, dtype=np.uint64))
+    Ai = ((h[:n * n] % np.uint64(2001)).astype(np.int64) - 1000).reshape(n, n)
+    forced = [0] * n
+    for j in range(0, n - 1, 2):                       # every other step forced
+        forced[j] = j + 1 + int(h[n * n + j] % np.uint64(n - j))
+    ipiv_x, Lx, Ux = rational_gepp(Ai.tolist(), forced=forced)
+    LU, ipiv, info = oracle_mod.getrf(Ai.astype(float), forced=forced)
+    assert list(ipiv) == ipiv_x
+    L, U = oracle_mod.unpack(LU)
+    Lf = np.array([[float(v) for v in r] for r in Lx])
+    Uf = np.array([[float(v) for v in r] for r in Ux])
+    # forced pivots may give multipliers above 1: bound relative to the exact factors' size
+    scale_l = max(1.0, np.max(np.abs(Lf)))
+    scale_u = max(1.0, np.max(np.abs(Uf))) * scale_l
+    assert np.max(np.abs(L - Lf)) <= 1e-10 * scale_l
+    assert np.max(np.abs(U - Uf)) <= 1e-10 * scale_u
+
+
+def test_forcing_the_searched_pivots_changes_nothing(oracle_mod):
+    A = li.uniform(257, seed=31)
+    LU, ipiv, info, gaps = oracle_mod.getrf(A, want_gaps=True)
+    LUf, ipivf, infof, gapsf = oracle_mod.getrf(A, want_gaps=True, forced=ipiv)
+    assert np.array_equal(ipiv, ipivf) and np.array_equal(LU, LUf) and np.array_equal(gaps, gapsf)
+    # a forced row above the diagonal is refused
+    bad = np.zeros(257, dtype=np.int32)
+    bad[5] = 3
+    with pytest.raises(ValueError):
+        oracle_mod.getrf(A, forced=bad)
