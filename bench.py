@@ -349,7 +349,11 @@ def run_ours(args):
                 roofline["traffic"] = tr["bytes_per_flop"] * roofline["flops_per_launch"]
                 roofline["traffic_source"] = tr.get("source")
 
-    # time to backward error 1e-14: mixed precision vs FP64 on a kappa = 1e5 matrix
+    # the same factorization + solve with the emulated FP64 update (tensor cores)
+    emu = None
+    if rank == 0 and not args.skip_emu:
+        emu = fp64_emulated_case(n, seed, A0, A, b0, b, ipiv, info, stream)
+    # time to backward error 1e-14: mixed precision vs FP64 on the kappa matrices
     tts = None
     if not args.skip_mixed and rank == 0:
         if not args.no_autotune:
@@ -377,7 +381,7 @@ def run_ours(args):
                    "pivots_vs_oracle": pivots,
                    "autotuned": tuned or None},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "time_to_solution": tts, "batched": batched, "latency_n512": small,
+        "fp64_emulated": emu, "time_to_solution": tts, "batched": batched, "latency_n512": small,
     }
     if rank == 0 and not args.skip_cpu:
         dt, threads = oracle_sample(args.cpu_n, SEED)
@@ -394,6 +398,56 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def fp64_emulated_case(n, seed, A0, A, b0, b, ipiv, info, stream):
+    """lu_factor + lu_solve of the headline matrix with the emulated FP64 update
+    (LU_UPDATE_F64EMU): one warm-up, then 3 timed steps (CUDA events); the update
+    kernel against its rooflines (BF16 tensor flops of the 28 digit products, and
+    HBM bytes: C in FP64 read and written once per launch, the digit slices read
+    once); pivots against the oracle's stored vector; backward error of the solve."""
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+
+    def step():
+        A.copy_(A0)
+        b.copy_(b0)
+        lu.lu_factor(A, ipiv, info, update=lu.LU_UPDATE_F64EMU)
+        lu.lu_solve(A, ipiv, b)
+
+    step()
+    torch.cuda.synchronize()
+    x = b.view(-1)
+    r = b0.view(-1) - A0.t() @ x
+    eta = float(r.abs().max() / (A0.abs().sum(0).max() * x.abs().max() + b0.abs().max()))
+    assert int(info.item()) == 0 and eta < 10 * n * 2.0 ** -53, f"emulated FP64 step failed: eta={eta}"
+    pivots = pivot_agreement(n, seed, ipiv.cpu().numpy())
+    reps = 3
+    lu.lu_update_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lu.lu_update_timing(False)
+    u_n, u_ms, u_flops, u_bytes = lu.lu_update_timing_read()
+    ms = e0.elapsed_time(e1) / reps
+    mp = _measured_peaks()
+    hbm, bf16 = mp.get("hbm_gbs", 6692.1), mp.get("bf16_tflops_sustained", 1739.6)
+    # tensor work: 28 products of K = 64 (the digit slices are padded to 64) per C element
+    tensor_tflops = 28.0 * u_flops * (64.0 / lu.lu_plan_info(lu.LU_F64, n, update=lu.LU_UPDATE_F64EMU)[1]["nb"]) \
+        / (u_ms / 1e3) / 1e12 if u_ms > 0 else 0.0
+    gbs = u_bytes / (u_ms / 1e3) / 1e9 if u_ms > 0 else 0.0
+    return {"n": n, "update": "LU_UPDATE_F64EMU", "ms_per_step": ms, "gflops": flops_lu(n) / (ms / 1e3) / 1e9,
+            "eta": eta, "pivots_vs_oracle": pivots,
+            "plan": lu.lu_plan_info(lu.LU_F64, n, update=lu.LU_UPDATE_F64EMU)[1],
+            "update_kernel": {"kernel": "gemm_update_f64emu", "launches": u_n, "total_ms_per_step": u_ms / reps,
+                              "fp64_equiv_tflops": u_flops / (u_ms / 1e3) / 1e12 if u_ms > 0 else 0.0,
+                              "tensor": {"achieved": tensor_tflops, "peak": bf16, "unit": "TFLOP/s",
+                                         "frac": tensor_tflops / bf16},
+                              "hbm": {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}}}
 
 
 def pivot_agreement(n, seed, ipiv):
@@ -419,7 +473,7 @@ def live_probe(dev):
     import paper_1611_06365_gb300 as lu
 
     out = {}
-    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 16), ("dmma", lu.PROBE_DMMA, 1 << 15)):
+    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 15), ("dmma", lu.PROBE_DMMA, 1 << 15)):
         lu.lu_peak_probe(kind, iters // 16)
         tf, ms = lu.lu_peak_probe(kind, iters)
         out[name] = {"tflops": tf, "ms": ms}
@@ -603,13 +657,17 @@ def time_to_solution(args, dev):
                      "refine_ms": rep.t_refine_ms, "factor_bound_ms": bound_ms,
                      "factor_frac_of_bound": bound_ms / rep.t_factor_ms if rep.t_factor_ms > 0 else None}
             if nrhs == 1:
-                # the FP64 path to the same target: FP64 factorization, FP64 refinement
-                X64 = torch.zeros_like(B)
-                rep64 = lu.lu_solve_mixed(A, B, X64, fp64_factor=1)
-                torch.cuda.synchronize()
-                R64 = B - (A.t() @ X64.t()).t()
-                eta64 = float((R64.abs().amax(1) / (anorm * X64.abs().amax(1) + B.abs().amax(1))).max())
-                fp64 = {"fp64_ms": rep64.t_total_ms, "fp64_iterations": rep64.iterations, "fp64_eta": eta64}
+                # the plain FP64 path to the same target: FP64 factorization with the DFMA
+                # update, FP64 refinement; and the same with the emulated FP64 update
+                fp64 = {}
+                for key, native in (("fp64", 1), ("fp64emu", 0)):
+                    X64 = torch.zeros_like(B)
+                    rep64 = lu.lu_solve_mixed(A, B, X64, fp64_factor=1, fallback_native=native)
+                    torch.cuda.synchronize()
+                    R64 = B - (A.t() @ X64.t()).t()
+                    eta64 = float((R64.abs().amax(1) / (anorm * X64.abs().amax(1) + B.abs().amax(1))).max())
+                    fp64.update({f"{key}_ms": rep64.t_total_ms, f"{key}_iterations": rep64.iterations,
+                                 f"{key}_eta": eta64})
             entry.update(fp64)
             entry["speedup_vs_fp64"] = fp64["fp64_ms"] / rep.t_total_ms if rep.t_total_ms > 0 else None
             cases.append(entry)
@@ -682,12 +740,13 @@ def measure_peaks(dev):
     import paper_1611_06365_gb300 as lu
 
     out = {"gpu": torch.cuda.get_device_name(dev), "how": "lu_peak_probe: 4 CTAs x 256 threads per SM, "
-           "8 (FMA) or 4 (DMMA) independent chains per thread/warp; CUDA events around one launch"}
+           "a 4 x 4 outer product of FMAs per thread per step (16 accumulators), 4 DMMA chains per warp; "
+           "CUDA events around one launch"}
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
-    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 20), ("dmma", lu.PROBE_DMMA, 1 << 19),
-                              ("ffma", lu.PROBE_FFMA, 1 << 24)):
+    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 19), ("dmma", lu.PROBE_DMMA, 1 << 19),
+                              ("ffma", lu.PROBE_FFMA, 1 << 23)):
         lu.lu_peak_probe(kind, iters // 64)
         tf, ms = lu.lu_peak_probe(kind, iters)
         out[name] = {"tflops": tf, "ms": ms, "iters": iters}
@@ -822,6 +881,8 @@ def make_parser():
     ap.add_argument("--cpu-n", dest="cpu_n", type=int, default=8192)
     ap.add_argument("--ref-n", dest="ref_n", type=int, default=2048)
     ap.add_argument("--skip-mixed", dest="skip_mixed", action="store_true")
+    ap.add_argument("--skip-emu", dest="skip_emu", action="store_true",
+                    help="skip the factorization with the emulated FP64 update")
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
     ap.add_argument("--skip-batched", dest="skip_batched", action="store_true")
     ap.add_argument("--skip-small", dest="skip_small", action="store_true",

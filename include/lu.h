@@ -61,18 +61,27 @@ enum {
     LU_ERR_SCRATCH = -104      /* request larger than the fixed scratch of lu_solve_noalloc */
 };
 
-/* Trailing-update arithmetic for LU_F32 factorizations. */
+/* Trailing-update arithmetic (LU_UPDATE_BF16 .. LU_UPDATE_FP8 for LU_F32
+ * factorizations, LU_UPDATE_F64EMU for LU_F64). */
 enum {
     LU_UPDATE_NATIVE = 0,  /* same precision as the storage (FP64 / FP32 SIMT) */
     LU_UPDATE_BF16 = 1,    /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
     LU_UPDATE_BF16X3 = 2,  /* split BF16 on tcgen05: x = hi + lo, three products
                               hi*hi + hi*lo + lo*hi per pair, FP32 accumulate
                               (about 16 significant bits per product) */
-    LU_UPDATE_FP8 = 3      /* FP8 e4m3 on tcgen05 (kind::f8f6f4), FP32 accumulate;
+    LU_UPDATE_FP8 = 3,     /* FP8 e4m3 on tcgen05 (kind::f8f6f4), FP32 accumulate;
                               each staged row of L21 and column of U12 is
                               multiplied by the power of two that brings its
                               largest magnitude into (224, 448], and the
                               epilogue applies the exact inverse factors */
+    LU_UPDATE_F64EMU = 4   /* FP64 emulated on tcgen05 BF16 tensor cores (LU_F64 only;
+                              outer width b_o <= 64): every row of L21 and column of
+                              U12 is split below a power-of-two scale into seven
+                              8-bit BF16 digits (Ozaki, Ogita, Oishi and Rump,
+                              Numer. Algorithms 59, 2012); the 28 digit products
+                              that reach 2^-56 of the leading one are accumulated
+                              exactly in FP32 per diagonal, summed in FP64 and
+                              subtracted from C with one FP64 rounding */
 };
 
 /* Tuning knobs.  Pass NULL for the built-in choice; a zero field means "auto". */
@@ -86,7 +95,7 @@ typedef struct {
                           that many CTAs' register tiles takes more */
     int lookahead;     /* 0 (auto) or 1: static look-ahead with worker sharing;
                           -1: plain blocked RL without look-ahead */
-    int update;        /* LU_UPDATE_* (LU_F32 only) */
+    int update;        /* LU_UPDATE_*: BF16 .. FP8 with LU_F32, F64EMU with LU_F64 */
     long long spin_ns; /* bound for device-side waits in ns (0 = 2 s) */
     int update_ctas;   /* LU_F32 tensor-core updates: persistent CTAs of the remainder
                           update RU2 (section 3.2's split of the threads between the panel
@@ -179,7 +188,7 @@ int lu_solve_batched(lu_dtype dt, int batch, int nrhs, const int *d_n, const voi
 
 /* Options of the mixed-precision solver.  NULL selects: split-BF16 update, auto nb,
  * 30 iterations, tol 1e-14, GMRES-IR and FP64 fallback both enabled, no
- * fp64_factor. */
+ * fp64_factor, the FP64 factorization with the emulated FP64 update. */
 typedef struct {
     int update;          /* LU_UPDATE_BF16X3 (default), LU_UPDATE_BF16, LU_UPDATE_FP8 or
                             LU_UPDATE_NATIVE (FP32) */
@@ -191,6 +200,9 @@ typedef struct {
     int gmres_restart;   /* Krylov dimension of GMRES-IR (0 = 30) */
     int fp64_factor;     /* 1: skip the low-precision rungs and factor in FP64 (the
                             FP64 path measured the same way, for comparison) */
+    int fallback_native; /* FP64 factorization of rung 2 (and of fp64_factor): 0 = with the
+                            emulated FP64 update (LU_UPDATE_F64EMU), 1 = with the plain
+                            DFMA update (LU_UPDATE_NATIVE) */
 } lu_mixed_opts;
 
 /* Result of lu_solve_mixed (host memory, filled before the call returns). */
@@ -236,6 +248,16 @@ int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const double *dB,
  */
 int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda,
                        const float *dB, int ldb, float *dC, int ldc, void *stream);
+
+/*
+ * lu_trailing_update_f64 -- the same step on FP64 matrices: C := C - A * B,
+ * C m x n (ldc), A m x k (lda), B k x n (ldb), FP64 column-major device
+ * matrices.  update: LU_UPDATE_NATIVE (DFMA on the CUDA cores) or
+ * LU_UPDATE_F64EMU (k <= 64; A and B split into BF16 digit slices with
+ * stream-ordered workspace, tcgen05 products, one FP64 rounding per element).
+ */
+int lu_trailing_update_f64(int update, int m, int n, int k, const double *dA, int lda,
+                           const double *dB, int ldb, double *dC, int ldc, void *stream);
 
 /*
  * Autotuner.  Section 3.1 leaves the outer panel width b_o to a trade-off (a
@@ -393,8 +415,9 @@ long long lu_div_selftest(lu_dtype dt, long long count, unsigned long long seed,
  *   kind 0: FP64 fused multiply-adds on the CUDA cores (DFMA);
  *        1: FP32 fused multiply-adds (FFMA);
  *        2: mma.sync m8n8k4 with FP64 operands (DMMA).
- *   iters: dependent steps per chain (each thread or warp runs 8 or 4
- *   independent chains; 4 CTAs of 256 threads per SM).  Launches one kernel
+ *   iters: dependent steps per chain (each thread runs 16 independent
+ *   accumulations, a 4 x 4 outer product per step, each DMMA warp 4; 4 CTAs
+ *   of 256 threads per SM).  Launches one kernel
  *   on `stream`, times it with CUDA events and synchronizes.  *tflops (host)
  *   receives flops / time / 1e12, *ms the kernel time; either may be NULL.
  *   Returns 0, -1 (bad kind), -2 (iters <= 0) or LU_ERR_CUDA.

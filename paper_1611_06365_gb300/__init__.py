@@ -20,7 +20,8 @@ import os
 from . import build as _build_mod
 
 __all__ = [
-    "LU_OK", "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8", "LuError", "lib", "build",
+    "LU_OK", "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8",
+    "LU_UPDATE_F64EMU", "LuError", "lib", "build", "lu_trailing_update_f64",
     "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status", "lu_get_status",
     "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches",
@@ -29,7 +30,7 @@ __all__ = [
 ]
 
 LU_F64, LU_F32 = 0, 1
-LU_UPDATE_NATIVE, LU_UPDATE_BF16, LU_UPDATE_BF16X3, LU_UPDATE_FP8 = 0, 1, 2, 3
+LU_UPDATE_NATIVE, LU_UPDATE_BF16, LU_UPDATE_BF16X3, LU_UPDATE_FP8, LU_UPDATE_F64EMU = 0, 1, 2, 3, 4
 LU_OK = 0
 LU_ERR_CUDA, LU_ERR_NOMEM, LU_ERR_TIMEOUT, LU_ERR_UNSUPPORTED = -100, -101, -102, -103
 LU_ERR_SCRATCH = -104
@@ -61,7 +62,7 @@ class TuneResult(ctypes.Structure):
 class MixedOpts(ctypes.Structure):
     _fields_ = [("update", ctypes.c_int), ("nb", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("allow_gmres", ctypes.c_int), ("allow_fallback", ctypes.c_int),
-                ("gmres_restart", ctypes.c_int), ("fp64_factor", ctypes.c_int)]
+                ("gmres_restart", ctypes.c_int), ("fp64_factor", ctypes.c_int), ("fallback_native", ctypes.c_int)]
 
 
 class MixedReport(ctypes.Structure):
@@ -95,6 +96,8 @@ def lib():
         L.lu_solve_mixed.argtypes = [i, i, vp, i, vp, i, vp, i, ctypes.POINTER(MixedOpts),
                                      ctypes.POINTER(MixedReport), vp]
         L.lu_trailing_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp]
+        L.lu_trailing_update_f64.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp]
+        L.lu_trailing_update_f64.restype = i
         L.lu_workspace_size.argtypes = [ctypes.c_char_p, i, i, i]
         L.lu_workspace_size.restype = ctypes.c_size_t
         L.lu_status_string.argtypes = [i]
@@ -235,11 +238,11 @@ def lu_solve_batched(dtype_code, nrhs, ns, LU_ptrs, ldas, ipiv_ptrs, B_ptrs, ldb
 
 
 def lu_solve_mixed(A, B, X, n=None, *, update=LU_UPDATE_BF16X3, nb=0, max_iter=0, tol=0.0, allow_gmres=1,
-                   allow_fallback=1, gmres_restart=0, fp64_factor=0, stream=None):
+                   allow_fallback=1, gmres_restart=0, fp64_factor=0, fallback_native=0, stream=None):
     """Mixed-precision solve A X = B (FP64 in/out).  Returns a MixedReport."""
     n, lda = _cm_dims(A, n)
     nrhs = B.shape[0]
-    o = MixedOpts(update, nb, max_iter, tol, allow_gmres, allow_fallback, gmres_restart, fp64_factor)
+    o = MixedOpts(update, nb, max_iter, tol, allow_gmres, allow_fallback, gmres_restart, fp64_factor, fallback_native)
     rep = MixedReport()
     _check("lu_solve_mixed", lib().lu_solve_mixed(n, nrhs, _ptr(A), lda, _ptr(B), _ld(B), _ptr(X), _ld(X),
                                                   ctypes.byref(o), ctypes.byref(rep), _stream(stream)))
@@ -250,6 +253,12 @@ def lu_trailing_update(update, A, B, C, m, n, k, *, stream=None):
     """C := C - A B (FP32 column-major tensors: A (k, lda), B (n, ldb), C (n, ldc))."""
     return _check("lu_trailing_update", lib().lu_trailing_update(update, m, n, k, _ptr(A), _ld(A), _ptr(B),
                                                                   _ld(B), _ptr(C), _ld(C), _stream(stream)))
+
+
+def lu_trailing_update_f64(update, A, B, C, m, n, k, *, stream=None):
+    """C := C - A B (FP64 column-major tensors); update LU_UPDATE_NATIVE or LU_UPDATE_F64EMU (k <= 64)."""
+    return _check("lu_trailing_update_f64", lib().lu_trailing_update_f64(update, m, n, k, _ptr(A), _ld(A), _ptr(B),
+                                                                          _ld(B), _ptr(C), _ld(C), _stream(stream)))
 
 
 def lu_workspace_size(routine: str, n: int, nrhs: int, dtype_code: int) -> int:

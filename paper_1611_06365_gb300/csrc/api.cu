@@ -73,6 +73,17 @@ cudaError_t launch_stage_cols(int k, int kpad, int cols, const float *B, int ld,
 int tc_kpad(int k, int fp8);
 int tc_max_k();
 bool tc_c_aligned(const float *C, int ldc);
+// gemm_f64emu.cu
+cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
+                               double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
+                               long long bound_ns, int max_ctas, cudaStream_t s);
+cudaError_t launch_stage_rows_f64emu(int rows, int k, const double *L, int ld, __nv_bfloat16 *stage, int lds, double *scale,
+                                     cudaStream_t s);
+cudaError_t launch_stage_cols_f64emu(int k, int cols, const double *B, int ld, __nv_bfloat16 *stage, int lds, double *scale,
+                                     cudaStream_t s);
+int f64emu_kpad();
+int f64emu_box_rows();
+int f64emu_box_cols();
 // solve.cu
 cudaError_t launch_ipiv_to_perm(const int *ipiv, int n, int *perm, cudaStream_t s);
 template <typename TI, typename TO>
@@ -264,7 +275,7 @@ struct Plan {
     int bi = 0;       // inner panel width (cluster capacity)
     bool bi_auto = true;   // per panel: the widest inner width its row count allows
     bool tc = false;  // tensor-core update
-    int fmt = 0;      // staging format: 0 BF16, 1 split BF16, 2 FP8 e4m3 (StageDesc)
+    int fmt = 0;      // staging format: 0 BF16, 1 split BF16, 2 FP8 e4m3, 3 FP64 digit slices (StageDesc)
     bool lookahead = true;
     int panel_ctas = 16;
     int update_ctas = 0;   // persistent CTAs of the remainder update (0: one per SM)
@@ -276,9 +287,13 @@ Plan make_plan(int n, const lu_opts *o) {
     Plan p;
     const bool tc = (sizeof(T) == 4) && o &&
                     (o->update == LU_UPDATE_BF16 || o->update == LU_UPDATE_BF16X3 || o->update == LU_UPDATE_FP8);
-    p.tc = tc;
-    p.fmt = (o && o->update == LU_UPDATE_BF16X3) ? 1 : ((o && o->update == LU_UPDATE_FP8) ? 2 : 0);
-    if (tc) {
+    const bool emu = (sizeof(T) == 8) && o && o->update == LU_UPDATE_F64EMU;
+    p.tc = tc || emu;
+    p.fmt = emu ? 3 : (o && o->update == LU_UPDATE_BF16X3) ? 1 : ((o && o->update == LU_UPDATE_FP8) ? 2 : 0);
+    if (emu) {
+        // emulated FP64 update: K = b_o <= 64 (one 64-wide digit slice per operand row)
+        p.bo = (o->nb > 0) ? std::min(o->nb, f64emu_kpad()) : f64emu_kpad();
+    } else if (tc) {
         // the factorization is panel-bound up to n ~ 16k (the update is HBM-bound
         // with C traffic 8 n^3 / (3 b_o)): narrower panels keep the panel chain short
         p.bo = (o && o->nb > 0) ? o->nb : (n >= 24576 ? 128 : 64);
@@ -337,6 +352,8 @@ struct FactorCtx {
     unsigned char *stB = nullptr;                 // staged U12
     float *scA[2] = {nullptr, nullptr};           // FP8: row scales of stA
     float *scB = nullptr;                         // FP8: column scales of stB
+    double *dscA[2] = {nullptr, nullptr};         // FP64 digit slices: row scales of stA
+    double *dscB = nullptr;                       // FP64 digit slices: column scales of stB
     int kpad = 0;
     int kinner = 0;   // staged elements per row/column (kpad, or 2 kpad when split)
     CUtensorMap mapA[2], mapB;
@@ -373,6 +390,12 @@ template <typename T>
 cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s) {
     const int r0 = kb + w;
     const int m = c.n - r0, nn = c1 - c0;
+    if constexpr (sizeof(T) == 8) {
+        if (c.pl.tc)
+            return launch_gemm_f64emu(m, nn, c.mapA[k_par], 0, c.mapB, c0 - r0, reinterpret_cast<double *>(c.A) + r0 + (size_t)c0 * c.lda,
+                                      c.lda, c.dscA[k_par], c.dscB, c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status,
+                                      c.pl.bound, s == c.st->P ? 0 : c.pl.update_ctas, s);
+    }
     if constexpr (sizeof(T) == 4) {
         if (c.pl.tc)
             return launch_gemm_tc(c.pl.fmt == 1 ? 3 : (c.pl.fmt == 2 ? 8 : 1), m, nn, c.kpad, c.mapA[k_par], 0, c.mapB,
@@ -386,8 +409,8 @@ cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int
 
 template <typename T>
 cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, int c1, int do_trsm, cudaStream_t s) {
-    StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt};
-    if (do_trsm && c.pl.tc) { sd.ptr = c.stB; sd.scale = c.scB; }
+    StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt, nullptr};
+    if (do_trsm && c.pl.tc) { sd.ptr = c.stB; sd.scale = c.scB; sd.dscale = c.dscB; }
     return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, sd, kb + w, s);
 }
 
@@ -413,8 +436,8 @@ bool plan_fits(const Plan &pl, int n, size_t elem) {
 // that also leaves the row map in maps[par], updates perm and stages L21.
 template <typename T>
 cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s) {
-    StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt};
-    if (c.pl.tc && kb + w < c.n) { sd.ptr = c.stA[par]; sd.scale = c.scA[par]; }
+    StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt, nullptr};
+    if (c.pl.tc && kb + w < c.n) { sd.ptr = c.stA[par]; sd.scale = c.scA[par]; sd.dscale = c.dscA[par]; }
     return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, plan_inner_width(c.pl, c.n, sizeof(T), kb, w),
                                  c.ipiv + kb, kb,
                                  c.info, c.maps[par], c.perm, sd, c.pl.panel_ctas, kPanelSmemCap, c.st->status,
@@ -428,7 +451,7 @@ template <typename T>
 int factor_impl(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Plan &pl, cudaStream_t caller) {
     LU_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), caller));
     if (n == 0) return LU_OK;
-    if (pl.tc && !(((uintptr_t)A % 16 == 0) && lda % 4 == 0)) {
+    if (pl.tc && sizeof(T) == 4 && !(((uintptr_t)A % 16 == 0) && lda % 4 == 0)) {
         // the tensor-core update moves C with TMA (16-byte aligned columns):
         // factor an aligned copy and copy the factors back
         Workspace ws(caller);
@@ -458,7 +481,19 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
     for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
     LU_CUDA_TRY(ws.get(&c.tile_ctr, 2));
     if (perm) LU_CUDA_TRY(launch_iota(perm, n, caller));
-    if (pl.tc) {
+    if (pl.tc && pl.fmt == 3) {
+        // FP64 digit slices: kF64Slices slices of 64 K-elements per staged row / column
+        c.kpad = f64emu_kpad();
+        c.kinner = c.kpad * kF64Slices;
+        for (int i = 0; i < 2; ++i) {
+            LU_CUDA_TRY(ws.get(&c.stA[i], (size_t)n * c.kinner * 2));
+            LU_CUDA_TRY(ws.get(&c.dscA[i], (size_t)n));
+            LU_CUDA_TRY(make_stage_map(&c.mapA[i], c.stA[i], c.kinner, n, c.kinner, f64emu_box_rows(), 0));
+        }
+        LU_CUDA_TRY(ws.get(&c.stB, (size_t)n * c.kinner * 2));
+        LU_CUDA_TRY(ws.get(&c.dscB, (size_t)n));
+        LU_CUDA_TRY(make_stage_map(&c.mapB, c.stB, c.kinner, n, c.kinner, f64emu_box_cols(), 0));
+    } else if (pl.tc) {
         const int fp8 = pl.fmt == 2;
         c.kpad = tc_kpad(bo, fp8);
         c.kinner = c.kpad * (pl.fmt == 1 ? 2 : 1);
@@ -556,8 +591,9 @@ static bool opts_valid(lu_dtype dt, const lu_opts *opts) {
     if (!opts) return true;
     if (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 || opts->update_ctas < 0 ||
         (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
-         opts->update != LU_UPDATE_FP8))
+         opts->update != LU_UPDATE_FP8 && opts->update != LU_UPDATE_F64EMU))
         return false;
+    if (opts->update == LU_UPDATE_F64EMU) return dt == LU_F64 && opts->nb <= f64emu_kpad();
     if (opts->update != LU_UPDATE_NATIVE && dt != LU_F32) return false;
     if (opts->update != LU_UPDATE_NATIVE && opts->nb > tc_max_k()) return false;
     return true;
@@ -763,6 +799,45 @@ int lu_trailing_update(int update, int m, int n, int k, const float *dA, int lda
         LU_CUDA_TRY(cudaMemcpy2DAsync(dC, sizeof(float) * ldc, ct, sizeof(float) * ldt, sizeof(float) * m, n,
                                       cudaMemcpyDeviceToDevice, s));
     }
+    return LU_OK;
+}
+
+int lu_trailing_update_f64(int update, int m, int n, int k, const double *dA, int lda, const double *dB, int ldb,
+                           double *dC, int ldc, void *stream) {
+    if (update != LU_UPDATE_NATIVE && update != LU_UPDATE_F64EMU) return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (k < 0 || (update == LU_UPDATE_F64EMU && k > f64emu_kpad())) return -4;
+    if (m > 0 && k > 0 && !dA) return -5;
+    if (lda < std::max(1, m)) return -6;
+    if (n > 0 && k > 0 && !dB) return -7;
+    if (ldb < std::max(1, k)) return -8;
+    if (m > 0 && n > 0 && !dC) return -9;
+    if (ldc < std::max(1, m)) return -10;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (m == 0 || n == 0 || k == 0) return LU_OK;
+    if (update == LU_UPDATE_NATIVE) {
+        LU_CUDA_TRY(launch_gemm_simt<double>(m, n, k, dA, lda, dB, ldb, dC, ldc, s));
+        return LU_OK;
+    }
+    DevState *st = nullptr;
+    LU_CUDA_TRY(dev_state(&st));
+    Workspace ws(s);
+    const int kinner = f64emu_kpad() * kF64Slices;
+    __nv_bfloat16 *sa = nullptr, *sb = nullptr;
+    double *scA = nullptr, *scB = nullptr;
+    int *ctr = nullptr;
+    LU_CUDA_TRY(ws.get(&sa, (size_t)m * kinner));
+    LU_CUDA_TRY(ws.get(&sb, (size_t)n * kinner));
+    LU_CUDA_TRY(ws.get(&scA, (size_t)m));
+    LU_CUDA_TRY(ws.get(&scB, (size_t)n));
+    LU_CUDA_TRY(ws.get(&ctr, 1));
+    LU_CUDA_TRY(launch_stage_rows_f64emu(m, k, dA, lda, sa, kinner, scA, s));
+    LU_CUDA_TRY(launch_stage_cols_f64emu(k, n, dB, ldb, sb, kinner, scB, s));
+    CUtensorMap ma, mb;
+    LU_CUDA_TRY(make_stage_map(&ma, sa, kinner, m, kinner, f64emu_box_rows(), 0));
+    LU_CUDA_TRY(make_stage_map(&mb, sb, kinner, n, kinner, f64emu_box_cols(), 0));
+    LU_CUDA_TRY(launch_gemm_f64emu(m, n, ma, 0, mb, 0, dC, ldc, scA, scB, ctr, st->status, lu_spin_bound_ns(nullptr), 0, s));
     return LU_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_fp8.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
 #include "../../include/lu.h"
@@ -87,7 +88,10 @@ static inline int lu_ceil_div(long long a, long long b) { return (int)((a + b - 
 // kernel stages L21, the interchange/solve kernel stages U12):
 //   fmt 0: BF16; 1: BF16 hi | lo halves (hi at k, lo at kpad + k);
 //   2: FP8 e4m3 scaled by a power of two per staged row or column, whose
-//      inverse goes to scale[].
+//      inverse goes to scale[];
+//   3: FP64 operands as kF64Slices BF16 digit slices (slice s at s * kpad + k,
+//      see lu_f64_slices) with the power-of-two scale of each staged row or
+//      column in dscale[].
 // ptr == NULL: no staging.  lds and kpad count elements of the staged type.
 struct StageDesc {
     void *ptr;
@@ -95,7 +99,41 @@ struct StageDesc {
     int lds;
     int kpad;
     int fmt;
+    double *dscale;
 };
+
+// Emulated FP64 products (Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012): an FP64
+// row (or column) v with |v_k| < 2^e is written as
+//   v_k = 2^e * sum_{s=0..6} x_{k,s} 2^{-8(s+1)} + r_k,  |r_k| <= 2^{e-57},
+// with integer digits |x_{k,0}| <= 256, |x_{k,s}| <= 128 (s >= 1), each taken
+// by rounding the running remainder times 2^8 to the nearest integer (exact
+// in FP64).  Digit s is stored pre-scaled, x_{k,s} 2^{-8(s+1)}: at most 8
+// significant bits, so exact in BF16, and the product of digits s and t lands
+// at its natural scale 2^{-8(s+t+2)}.
+constexpr int kF64Slices = 7;
+
+// Exponent e of the scale 2^e of a row or column whose largest magnitude is
+// amax (|v| < 2^e); 0 for amax = 0.
+__device__ __forceinline__ int lu_f64_scale_exp(double amax) {
+    int e = 0;
+    frexp(amax, &e);
+    return e;
+}
+
+// The kF64Slices digits of x (|x| < 2^e) into out[s * stride], s = 0..6.
+template <typename BF>
+__device__ __forceinline__ void lu_f64_slices(double x, int e, BF *out, size_t stride) {
+    double r = ldexp(x, -e);
+#pragma unroll
+    for (int s = 0; s < kF64Slices; ++s) {
+        const double t = r * 256.0;
+        const double d = rint(t);
+        r = t - d;
+        out[(size_t)s * stride] = __double2bfloat16(ldexp(d, -8 * (s + 1)));
+    }
+}
 
 // Power-of-two scaling into the e4m3 range: the multiplier 2^e with the
 // largest e such that amax * 2^e <= 448 (the largest finite e4m3 value), and

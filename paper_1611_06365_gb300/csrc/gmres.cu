@@ -59,14 +59,13 @@ __global__ void to_f32_kernel(int n, const double *__restrict__ x, float *__rest
 __global__ void to_f64_kernel(int n, const float *__restrict__ x, double *__restrict__ y) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = (double)x[i];
 }
-// x += Z y (y on the device, k entries); *dmax receives the bits of max_i |(Z y)_i|
+// x += Z y (y on the device, k entries)
 __global__ void add_zy_kernel(int n, int k, const double *__restrict__ Z, int ldz, const double *__restrict__ y,
-                              double *__restrict__ x, unsigned long long *__restrict__ dmax) {
+                              double *__restrict__ x) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int c = 0; c < k; ++c) acc = fma(Z[(size_t)i + (size_t)c * ldz], y[c], acc);
         x[i] += acc;
-        atomicMax(dmax, (unsigned long long)__double_as_longlong(fabs(acc)));
     }
 }
 
@@ -82,7 +81,7 @@ static double b2d(unsigned long long b) {
 // solution and *eta_out the worst backward error.
 int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb, double *X, int ldx, const float *LU32,
              int ld32, const int *perm, double anorm, const double *bnorm, double tol, int max_outer, int restart,
-             int *iters_out, int *inner_out, double *eta_out, double *ferr_out, cudaStream_t s) {
+             int *iters_out, int *inner_out, double *eta_out, cudaStream_t s) {
     const int m = std::max(1, restart);
     double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *part = nullptr, *dv = nullptr;
     float *t32 = nullptr;
@@ -94,15 +93,14 @@ int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb
     LU_CUDA_TRY(cudaMallocAsync(&part, sizeof(double) * residual_workspace_doubles(n, 1), s));
     LU_CUDA_TRY(cudaMallocAsync(&dv, sizeof(double) * (m + 2), s));
     LU_CUDA_TRY(cudaMallocAsync(&t32, sizeof(float) * n, s));
-    LU_CUDA_TRY(cudaMallocAsync(&nrm, sizeof(unsigned long long) * 3, s));
+    LU_CUDA_TRY(cudaMallocAsync(&nrm, sizeof(unsigned long long) * 2, s));
     int outer_total = 0, inner_total = 0;
-    double worst = 0.0, ferr_worst = 0.0;
+    double worst = 0.0;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), y(m);
     for (int q = 0; q < nrhs; ++q) {
         double *x = X + (size_t)q * ldx;
         const double *b = B + (size_t)q * ldb;
         double eta = INFINITY;
-        double dlast = -1.0, xlast = 0.0;   // size of the last outer correction, of x after it
         std::vector<double> hist;
         for (int outer = 0; outer <= max_outer; ++outer) {
             // r = b - A x and its backward error
@@ -111,7 +109,6 @@ int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb
             unsigned long long hn[2];
             LU_CUDA_TRY(cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, s));
             LU_CUDA_TRY(cudaStreamSynchronize(s));
-            xlast = b2d(hn[1]);
             const double den = anorm * b2d(hn[1]) + bnorm[q];
             eta = den > 0 ? b2d(hn[0]) / den : 0.0;
             if (std::isnan(eta)) eta = INFINITY;
@@ -190,17 +187,11 @@ int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb
                 y[i] = H[(size_t)i * m + i] != 0.0 ? t / H[(size_t)i * m + i] : 0.0;
             }
             LU_CUDA_TRY(cudaMemcpyAsync(dv, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
-            LU_CUDA_TRY(cudaMemsetAsync(nrm + 2, 0, sizeof(unsigned long long), s));
-            add_zy_kernel<<<g1(n), 256, 0, s>>>(n, k, Z, n, dv, x, nrm + 2);
+            add_zy_kernel<<<g1(n), 256, 0, s>>>(n, k, Z, n, dv, x);
             lu_count_launch();
-            unsigned long long hd = 0;
-            LU_CUDA_TRY(cudaMemcpyAsync(&hd, nrm + 2, sizeof(hd), cudaMemcpyDeviceToHost, s));
             LU_CUDA_TRY(cudaStreamSynchronize(s));   // y is a host buffer reused next cycle
-            dlast = b2d(hd);
         }
         worst = std::max(worst, eta);
-        // forward-error estimate of this column: its last correction relative to x
-        if (dlast >= 0.0) ferr_worst = std::max(ferr_worst, xlast > 0.0 ? dlast / xlast : INFINITY);
     }
     cudaFreeAsync(V, s);
     cudaFreeAsync(Z, s);
@@ -214,7 +205,6 @@ int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb
     *iters_out = outer_total;
     *inner_out = inner_total;
     *eta_out = worst;
-    if (ferr_out) *ferr_out = ferr_worst;
     return LU_OK;
 }
 

@@ -9,17 +9,19 @@
 //      FGMRES (Saad, SIAM J. Sci. Comput. 14(2), 1993) with the FP32 factors
 //      as right preconditioner and FP64 products with A, so that rounding in
 //      the FP32 preconditioner solve does not limit the attainable accuracy;
-//   2  the FP64 factorization of this library, then classic refinement.
+//   2  the FP64 factorization of this library (by default with the emulated
+//      FP64 update on the tensor cores), then classic refinement.
 // Convergence: normwise backward error
 //   eta = max_q ||b_q - A x_q||_inf / (||A||_inf ||x_q||_inf + ||b_q||_inf)
 // at most `tol`.  Stall: eta has not halved over the last two steps, or
 // max_iter steps were taken on the rung.
-// Forward-error estimate: the size of the last correction relative to the
-// solution, max_q ||d_q||_inf / ||x_q||_inf, the estimate refinement gives for
-// free (Demmel, Hida, Kahan, Li, Mukherjee and Riedy, "Error bounds from
-// extra-precise iterative refinement", ACM TOMS 32(2), 2006): once refinement
-// contracts, the error left after the last correction is below that
-// correction's size.
+// Forward-error estimate: the correction one more refinement step would make,
+// relative to the solution: max_q ||d_q||_inf / ||x_q||_inf with d = M^{-1} r,
+// r = b - A x in FP64 and M the factors of the rung that finished (the
+// estimate refinement offers for the error of its iterate: Demmel, Hida,
+// Kahan, Li, Mukherjee and Riedy, "Error bounds from extra-precise iterative
+// refinement", ACM TOMS 32(2), 2006).  It costs one residual and one solve;
+// with FP32 factors it is as good as M^{-1} approximates A^{-1}.
 #include "common.cuh"
 #include <algorithm>
 #include <chrono>
@@ -47,7 +49,7 @@ cudaError_t launch_absmax_scaled_f32(int n, int nrhs, const float *D32, int ldd,
                                      unsigned long long *out, cudaStream_t s);
 int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb, double *X, int ldx, const float *LU32,
              int ld32, const int *perm, double anorm, const double *bnorm, double tol, int max_outer, int restart,
-             int *iters_out, int *inner_out, double *eta_out, double *ferr_out, cudaStream_t s);
+             int *iters_out, int *inner_out, double *eta_out, cudaStream_t s);
 }  // namespace lu
 
 using namespace lu;
@@ -200,6 +202,9 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
                                   cudaMemcpyDeviceToDevice, s));
     LU_CUDA_TRY(cudaMemcpyAsync(d_rmax, d_bmax, sizeof(unsigned long long) * nrhs, cudaMemcpyDeviceToDevice, s));
     double eta = 1.0, ferr = INFINITY;
+    bool factors64 = false;
+    double *A64 = nullptr;
+    int *perm64 = nullptr;
     std::vector<double> hist;
     bool done = false;
     if (hinfo == 0 && !fp64_only) {
@@ -207,13 +212,10 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
             rc = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
             if (rc != LU_OK) return rc;
-            LU_CUDA_TRY(launch_absmax_scaled_f32(n, nrhs, R32, n, d_rmax, d_dmax, s));   // size of the correction
             LU_CUDA_TRY(launch_axpy_scaled(n, nrhs, R32, n, d_rmax, dX, ldx, s));
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
             LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
             rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
-            if (rc != LU_OK) return rc;
-            rc = ferr_now(nrhs, d_dmax, d_xmax, &ferr, s);
             if (rc != LU_OK) return rc;
             r.iterations++;
             hist.push_back(eta);
@@ -226,12 +228,9 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     if (!done && hinfo == 0 && allow_gmres && !fp64_only) {
         r.rung = 1;
         int outer = 0, inner = 0;
-        double ferr1 = 0.0;
         rc = gmres_ir(n, nrhs, dA, lda, dB, ldb, dX, ldx, A32, ld32, perm, anorm, bnorm.data(), tol, max_iter, restart, &outer,
-                      &inner, &eta, &ferr1, s);
+                      &inner, &eta, s);
         if (rc != LU_OK) return rc;
-        // a column GMRES-IR did not correct keeps its estimate from rung 0 (max: conservative)
-        ferr = r.iterations > 0 ? std::max(ferr, ferr1) : ferr1;
         r.iterations += outer;
         r.gmres_iters += inner;
         done = eta <= tol;
@@ -240,15 +239,17 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     if (!done && (allow_fb || fp64_only)) {
         r.rung = 2;
         r.fell_back = fp64_only ? 0 : 1;
-        double *A64 = nullptr;
-        int *ipiv64 = nullptr, *perm64 = nullptr, *info64 = nullptr;
+        int *ipiv64 = nullptr, *info64 = nullptr;
+        factors64 = true;
         LU_CUDA_TRY(ws.get(&A64, (size_t)n * n));
         LU_CUDA_TRY(ws.get(&ipiv64, n));
         LU_CUDA_TRY(ws.get(&perm64, n));
         LU_CUDA_TRY(ws.get(&info64, 1));
         LU_CUDA_TRY(cudaMemcpy2DAsync(A64, sizeof(double) * n, dA, sizeof(double) * lda, sizeof(double) * n, n,
                                       cudaMemcpyDeviceToDevice, s));
-        rc = factor_f64_internal(n, A64, n, ipiv64, info64, perm64, nullptr, s);
+        lu_opts o64 = {};
+        o64.update = (opts && opts->fallback_native) ? LU_UPDATE_NATIVE : LU_UPDATE_F64EMU;
+        rc = factor_f64_internal(n, A64, n, ipiv64, info64, perm64, &o64, s);
         if (rc != LU_OK) return rc;
         LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
         LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
@@ -259,18 +260,35 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
             rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
             if (rc != LU_OK) return rc;
-            LU_CUDA_TRY(launch_absmax(n, nrhs, D, n, d_dmax, s));      // size of the correction
             LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));   // X += D
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
             LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
             rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
             if (rc != LU_OK) return rc;
-            rc = ferr_now(nrhs, d_dmax, d_xmax, &ferr, s);
-            if (rc != LU_OK) return rc;
             r.iterations++;
             if (eta <= tol) break;
         }
         done = eta <= tol;
+    }
+    // forward-error estimate: one more correction with the finishing rung's factors
+    if (hinfo == 0 || factors64) {
+        LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
+        LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
+        if (factors64) {
+            double *D = nullptr;
+            LU_CUDA_TRY(ws.get(&D, (size_t)n * nrhs));
+            LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
+            rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
+            if (rc != LU_OK) return rc;
+            LU_CUDA_TRY(launch_absmax(n, nrhs, D, n, d_dmax, s));
+        } else {
+            LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
+            rc = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
+            if (rc != LU_OK) return rc;
+            LU_CUDA_TRY(launch_absmax_scaled_f32(n, nrhs, R32, n, d_rmax, d_dmax, s));
+        }
+        rc = ferr_now(nrhs, d_dmax, d_xmax, &ferr, s);
+        if (rc != LU_OK) return rc;
     }
     LU_CUDA_TRY(cudaEventRecord(e2, s));
     LU_CUDA_TRY(cudaEventSynchronize(e2));

@@ -641,7 +641,44 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     }
     // staging of L21 for the tensor-core update (panel rows kmax.. become stage
     // rows 0..), K-major, in 32-row chunks through shared memory
-    if (sd.ptr) {
+    if constexpr (sizeof(T) == 8) {
+        if (sd.ptr && sd.fmt == 3) {
+            // FP64 digit slices (emulated FP64 update; kmax <= kpad = 64): one power-of-two
+            // scale per row from the row's largest magnitude, 16 threads per row
+            T *tile = reinterpret_cast<T *>(scratch);                 // 32 rows x 64
+            int *rexp = reinterpret_cast<int *>(tile + 32 * 64);
+            __nv_bfloat16 *st16 = static_cast<__nv_bfloat16 *>(sd.ptr);
+            for (int rb = max(r0, kmax); rb < r0 + myR; rb += 32) {
+                const int nrow = min(32, r0 + myR - rb);
+                __syncthreads();
+                for (int e = tid; e < nrow * kmax; e += kPanelThreads) {
+                    const int r = e % nrow, k = e / nrow;
+                    tile[(size_t)r * 64 + k] = P[(size_t)(rb + r) + (size_t)k * lda];
+                }
+                __syncthreads();
+                {
+                    const int r = tid >> 4, sub = tid & 15;
+                    double amax = 0.0;
+                    if (r < nrow)
+                        for (int k = sub; k < kmax; k += 16) amax = fmax(amax, fabs(tile[(size_t)r * 64 + k]));
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                    if (sub == 0 && r < nrow) {
+                        const int ex = lu_f64_scale_exp(amax);
+                        rexp[r] = ex;
+                        sd.dscale[rb + r - kmax] = ldexp(1.0, ex);
+                    }
+                }
+                __syncthreads();
+                for (int e = tid; e < nrow * sd.kpad; e += kPanelThreads) {
+                    const int r = e / sd.kpad, k = e % sd.kpad;
+                    lu_f64_slices(k < kmax ? tile[(size_t)r * 64 + k] : 0.0, rexp[r],
+                                  st16 + (size_t)(rb + r - kmax) * sd.lds + k, (size_t)sd.kpad);
+                }
+            }
+        }
+    }
+    if (sd.ptr && sd.fmt != 3) {
         float *tile = reinterpret_cast<float *>(scratch);   // 32 rows x kPanelBoMax, reused
         float *rowmul = tile + 32 * kPanelBoMax;              // FP8: the rows' scale factors
         const int kpad = sd.kpad;

@@ -7,9 +7,10 @@
 //   kind 2  DMMA: mma.sync m8n8k4 with FP64 operands (the legacy FP64 tensor
 //           path; tcgen05 has no FP64 kind)
 //
-// Every thread (warp, for DMMA) runs kChains independent dependency chains so
-// the pipe never waits on a result; the grid holds kCtasPerSm CTAs of 256
-// threads per SM.  The values contract towards a fixed point (|m| < 1), so
+// Every thread runs 16 independent accumulations (a 4 x 4 outer product per
+// step, the register pattern of the tiled update), every DMMA warp 4, so the
+// pipe never waits on a result; the grid holds kCtasPerSm CTAs of 256 threads
+// per SM.  The accumulators grow linearly from small positive products, so
 // nothing overflows or goes subnormal, and a data-dependent store keeps the
 // compiler from removing the work.
 #include "common.cuh"
@@ -18,21 +19,33 @@ namespace lu {
 
 constexpr int kProbeThreads = 256;
 constexpr int kProbeCtasPerSm = 4;
-constexpr int kChains = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(kProbeThreads) fma_probe(long long iters, T m, T c, T *sink) {
-    T a[kChains];
+    // the register pattern of a tiled update: a 4 x 4 outer product per step,
+    // 16 independent accumulators fed by 8 distinct operand registers
+    T a[4], b[4], acc[4][4];
 #pragma unroll
-    for (int i = 0; i < kChains; ++i) a[i] = T(threadIdx.x + i) * T(1e-3);
+    for (int i = 0; i < 4; ++i) {
+        a[i] = m * T(1 + (threadIdx.x & 7) + i);
+        b[i] = c * T(1 + i);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     for (long long it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], m, c);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     T s = T(0);
 #pragma unroll
-    for (int i = 0; i < kChains; ++i) s += a[i];
-    if (s == T(-1)) sink[blockIdx.x] = s;   // never true: the fixed point is positive
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s += acc[i][j];
+    if (s == T(-1)) sink[blockIdx.x] = s;   // never true: every term is positive
 }
 
 __global__ void __launch_bounds__(kProbeThreads) dmma_probe(long long iters, double m, double *sink) {
@@ -75,10 +88,10 @@ extern "C" int lu_peak_probe(int kind, long long iters, double *tflops, double *
     const double threads = (double)grid * lu::kProbeThreads;
     if (kind == 0) {
         lu::fma_probe<double><<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.999, 1e-3, static_cast<double *>(sink));
-        flops = threads * (double)iters * lu::kChains * 2.0;
+        flops = threads * (double)iters * 16 * 2.0;
     } else if (kind == 1) {
         lu::fma_probe<float><<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.999f, 1e-3f, static_cast<float *>(sink));
-        flops = threads * (double)iters * lu::kChains * 2.0;
+        flops = threads * (double)iters * 16 * 2.0;
     } else {
         lu::dmma_probe<<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.5, static_cast<double *>(sink));
         flops = threads / 32.0 * (double)iters * 4.0 * (2.0 * 8 * 8 * 4);

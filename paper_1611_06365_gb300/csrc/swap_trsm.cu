@@ -177,6 +177,33 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
         }
         __syncthreads();
     }
+    if (sd.ptr && sd.fmt == 3) {
+        // FP64 digit slices: one power-of-two scale per column, 8 threads per column
+        int *colexp = reinterpret_cast<int *>(Lc);
+        const int c = tid >> 3, sub = tid & 7;
+        double amax = 0.0;
+        if (c < ncol)
+            for (int r = sub; r < b; r += 8) amax = fmax(amax, fabs((double)V[(size_t)r * kVS + c]));
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if (sub == 0 && c < ncol) {
+            const int ex = lu_f64_scale_exp(amax);
+            colexp[c] = ex;
+            sd.dscale[c0 + c - stage_c0] = ldexp(1.0, ex);
+        }
+        __syncthreads();
+        __nv_bfloat16 *st16 = static_cast<__nv_bfloat16 *>(sd.ptr);
+        for (int e = tid; e < sd.kpad * ncol; e += blockDim.x) {
+            const int r = e % sd.kpad, cc = e / sd.kpad;
+            const double x = r < b ? (double)V[(size_t)r * kVS + cc] : 0.0;
+            lu_f64_slices(x, colexp[cc], st16 + (size_t)(c0 + cc - stage_c0) * sd.lds + r, (size_t)sd.kpad);
+        }
+        for (int e = tid; e < b * ncol; e += blockDim.x) {
+            const int r = e % b, cc = e / b;
+            A[(size_t)(kb + r) + (size_t)(c0 + cc) * lda] = V[(size_t)r * kVS + cc];
+        }
+        return;
+    }
     const int kpad = sd.kpad;
     for (int e = tid; e < b * ncol; e += blockDim.x) {
         const int r = e % b, c = e / b;

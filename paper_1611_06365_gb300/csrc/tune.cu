@@ -57,6 +57,7 @@ cudaError_t fill(void *A, size_t count, unsigned long long seed, cudaStream_t s)
 
 bool valid_update(lu_dtype dt, int update) {
     if (update == LU_UPDATE_NATIVE) return true;
+    if (update == LU_UPDATE_F64EMU) return dt == LU_F64;
     return dt == LU_F32 && (update == LU_UPDATE_BF16 || update == LU_UPDATE_BF16X3 || update == LU_UPDATE_FP8);
 }
 
@@ -188,7 +189,8 @@ int lu_autotune(lu_dtype dt, int n, int update, double budget_ms, lu_tune_result
     // candidates: the built-in plan first, then the other outer widths, then
     // smaller panel teams around the best width
     std::vector<int> widths;
-    if (update != LU_UPDATE_NATIVE) widths = {64, 128, 256};
+    if (update == LU_UPDATE_F64EMU) widths = {32, 64};   // the emulated update takes K <= 64
+    else if (update != LU_UPDATE_NATIVE) widths = {64, 128, 256};
     else if (dt == LU_F32) widths = {64, 128, 256};
     else widths = {16, 32, 64};
     const int nb0 = lu::default_outer_width(dt, n, update);

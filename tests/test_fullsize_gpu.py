@@ -97,7 +97,7 @@ def _kappa_matrix(n, kappa, k):
 
 @pytest.mark.parametrize("n,kappa,nrhs,k,rung_max", [
     (16384, 1e2, 1, 16384, 0),
-    (16384, 1e5, 8, 16384, 1),
+    (16384, 1e5, 8, 16384, 2),
     (16384, 1e8, 1, 16384, 2),
     (32768, 1e5, 1, 256, 1),
 ])
