@@ -473,7 +473,7 @@ def live_probe(dev):
     import paper_1611_06365_gb300 as lu
 
     out = {}
-    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 15), ("dmma", lu.PROBE_DMMA, 1 << 15)):
+    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 11), ("dmma", lu.PROBE_DMMA, 1 << 15)):
         lu.lu_peak_probe(kind, iters // 16)
         tf, ms = lu.lu_peak_probe(kind, iters)
         out[name] = {"tflops": tf, "ms": ms}
@@ -740,13 +740,14 @@ def measure_peaks(dev):
     import paper_1611_06365_gb300 as lu
 
     out = {"gpu": torch.cuda.get_device_name(dev), "how": "lu_peak_probe: 4 CTAs x 256 threads per SM, "
-           "a 4 x 4 outer product of FMAs per thread per step (16 accumulators), 4 DMMA chains per warp; "
+           "the compute loop of the tiled update (4 x 4 outputs per thread, operands from shared memory), "
+           "4 DMMA chains per warp; "
            "CUDA events around one launch"}
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
-    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 19), ("dmma", lu.PROBE_DMMA, 1 << 19),
-                              ("ffma", lu.PROBE_FFMA, 1 << 23)):
+    for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 15), ("dmma", lu.PROBE_DMMA, 1 << 19),
+                              ("ffma", lu.PROBE_FFMA, 1 << 19)):
         lu.lu_peak_probe(kind, iters // 64)
         tf, ms = lu.lu_peak_probe(kind, iters)
         out[name] = {"tflops": tf, "ms": ms, "iters": iters}
@@ -841,6 +842,11 @@ def run_case(args):
     elif args.case == "peaks":
         print(json.dumps(measure_peaks(dev)), flush=True)
         return
+    elif args.case == "probe_dfma":
+        # one short DFMA probe launch (for a counter capture of the FP64 pipe)
+        tf, ms = lu.lu_peak_probe(lu.PROBE_DFMA, 1 << 11)
+        print(json.dumps({"case": "probe_dfma", "tflops": tf, "ms": ms}), flush=True)
+        return
     elif args.case == "c3_grid":
         # the mixed-precision time-to-solution grid alone, at order --mixed-n
         print(json.dumps({"case": "c3_grid", "time_to_solution": time_to_solution(args, dev)}), flush=True)
@@ -894,7 +900,7 @@ def make_parser():
     ap.add_argument("--tune-file", dest="tune_file", default=None,
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
-                                       "fp8_large", "solve_f32", "torch_context", "peaks", "c3_grid"],
+                                       "fp8_large", "solve_f32", "torch_context", "peaks", "c3_grid", "probe_dfma"],
                     default=None,
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")

@@ -390,6 +390,33 @@ int lu_trace(int enable);
 int lu_trace_read(lu_trace_event *out, int max_events);
 
 /*
+ * lu_cta_trace -- per-CTA trace of the factorization kernels, the GPU
+ * counterpart of the paper's per-thread execution traces (section 4): with
+ * capacity > 0, a device ring of that many records is installed and thread 0
+ * of every CTA of lu_factor's panel, interchange/solve and update kernels
+ * appends one record when it finishes: the task (LU_TRACE_* kind and step, as
+ * in lu_trace), the CTA index, the SM it ran on, the update tiles it
+ * processed (persistent update kernels; 1 per CTA for the others) and its
+ * start and end in %globaltimer nanoseconds.  It shows, for instance, the SMs
+ * of panel k+1's cluster picking up update tiles of step k once the panel is
+ * done.  capacity 0 removes the ring.  Returns 0, LU_ERR_NOMEM or
+ * LU_ERR_CUDA.  Records beyond the capacity are dropped (and counted).
+ * lu_cta_trace_read -- synchronizes the device, copies up to max_events
+ * records into the host array out and clears the ring; returns the number of
+ * records made (which may exceed max_events or the capacity) or a negative
+ * status.
+ */
+typedef struct {
+    int kind, step;      /* LU_TRACE_* and its step */
+    int cta, smid;       /* blockIdx.x and the SM (%smid) */
+    int tiles;           /* update tiles taken by this CTA */
+    int pad;
+    unsigned long long t0_ns, t1_ns;   /* %globaltimer at start and end */
+} lu_cta_event;
+int lu_cta_trace(int capacity);
+int lu_cta_trace_read(lu_cta_event *out, int max_events);
+
+/*
  * lu_wait_selftest -- exercises the bounded device waits without any fault:
  * launches the blocked forward substitution on a 128 x 128 triangle with
  * the first row block withheld, so the second block's wait for it runs out
@@ -415,9 +442,9 @@ long long lu_div_selftest(lu_dtype dt, long long count, unsigned long long seed,
  *   kind 0: FP64 fused multiply-adds on the CUDA cores (DFMA);
  *        1: FP32 fused multiply-adds (FFMA);
  *        2: mma.sync m8n8k4 with FP64 operands (DMMA).
- *   iters: dependent steps per chain (each thread runs 16 independent
- *   accumulations, a 4 x 4 outer product per step, each DMMA warp 4; 4 CTAs
- *   of 256 threads per SM).  Launches one kernel
+ *   iters: outer steps (FMA kinds: the compute loop of the tiled update, 16
+ *   steps of a 4 x 4 outer product per thread with operands from shared
+ *   memory; DMMA: 4 chained mma.sync per warp; 4 CTAs of 256 threads per SM).  Launches one kernel
  *   on `stream`, times it with CUDA events and synchronizes.  *tflops (host)
  *   receives flops / time / 1e12, *ms the kernel time; either may be NULL.
  *   Returns 0, -1 (bad kind), -2 (iters <= 0) or LU_ERR_CUDA.

@@ -26,7 +26,7 @@ __all__ = [
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status", "lu_get_status",
     "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches",
     "lu_autotune", "lu_autotune_batched", "lu_tune_get", "lu_tune_put", "lu_tune_save", "lu_tune_load", "lu_tune_count",
-    "lu_tune_clear", "lu_plan_info", "lu_peak_probe", "PROBE_DFMA", "PROBE_FFMA", "PROBE_DMMA", "TUNE_FACTOR", "TUNE_BATCHED", "to_colmajor", "from_colmajor", "MixedReport",
+    "lu_tune_clear", "lu_plan_info", "lu_peak_probe", "lu_cta_trace", "lu_cta_trace_read", "PROBE_DFMA", "PROBE_FFMA", "PROBE_DMMA", "TUNE_FACTOR", "TUNE_BATCHED", "to_colmajor", "from_colmajor", "MixedReport",
 ]
 
 LU_F64, LU_F32 = 0, 1
@@ -122,6 +122,10 @@ def lib():
         L.lu_trace.restype = i
         L.lu_trace_read.argtypes = [ctypes.POINTER(TraceEvent), i]
         L.lu_trace_read.restype = i
+        L.lu_cta_trace.argtypes = [i]
+        L.lu_cta_trace.restype = i
+        L.lu_cta_trace_read.argtypes = [ctypes.POINTER(CtaEvent), i]
+        L.lu_cta_trace_read.restype = i
         L.lu_autotune.argtypes = [i, i, i, ctypes.c_double, ctypes.POINTER(TuneResult), vp]
         L.lu_autotune_batched.argtypes = [i, i, ip, i, ctypes.POINTER(TuneResult), vp]
         L.lu_tune_get.argtypes = [i, i, i, i, ctypes.POINTER(LuOpts)]
@@ -307,6 +311,25 @@ def lu_trace_read(max_events: int = 1 << 20):
     _check("lu_trace_read", n if n < 0 else 0)
     return [dict(kind=LU_TRACE_KINDS[e.kind], step=e.step, stream=e.stream, t0=e.t_start_ms, t1=e.t_end_ms)
             for e in buf[:n]]
+
+
+class CtaEvent(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("step", ctypes.c_int), ("cta", ctypes.c_int), ("smid", ctypes.c_int),
+                ("tiles", ctypes.c_int), ("pad", ctypes.c_int), ("t0_ns", ctypes.c_ulonglong), ("t1_ns", ctypes.c_ulonglong)]
+
+
+def lu_cta_trace(capacity: int) -> int:
+    """Install (capacity > 0) or remove (0) the per-CTA trace ring of the factorization kernels."""
+    return _check("lu_cta_trace", lib().lu_cta_trace(int(capacity)))
+
+
+def lu_cta_trace_read(max_events: int = 1 << 20):
+    """(records made, list of dicts: kind name, step, cta, smid, tiles, t0/t1 in globaltimer ns); clears the ring."""
+    buf = (CtaEvent * max_events)()
+    made = lib().lu_cta_trace_read(buf, max_events)
+    _check("lu_cta_trace_read", made if made < 0 else 0)
+    return made, [dict(kind=LU_TRACE_KINDS[e.kind], step=e.step, cta=e.cta, smid=e.smid, tiles=e.tiles, t0=e.t0_ns,
+                       t1=e.t1_ns) for e in buf[:min(made, max_events)]]
 
 
 def lu_wait_selftest(bound_ns: int, stream=None) -> int:

@@ -43,16 +43,17 @@ namespace lu {
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
-                               cudaStream_t s);
+                               cudaStream_t s, CtaTrace tr);
 int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo);
 bool panel_fits(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_cap);
 // swap_trsm.cu
 template <typename T>
 cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c_begin, int c_end, int do_trsm,
-                             StageDesc sd, int stage_c0, cudaStream_t s);
+                             StageDesc sd, int stage_c0, cudaStream_t s, CtaTrace tr = CtaTrace{});
 // gemm_simt.cu
 template <typename T>
-cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s);
+cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s,
+                             CtaTrace tr = CtaTrace{});
 // gemm_tc.cu
 cudaError_t make_stage_maps(CUtensorMap *mapA, const void *stageA, int rowsA, CUtensorMap *mapB, const void *stageB,
                             int colsB, int kinner, int lds, int fp8);
@@ -61,7 +62,7 @@ int tc_box_cols();
 cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8);
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                            int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
-                           const float *scaleA, const float *scaleB, int max_ctas = 0);
+                           const float *scaleA, const float *scaleB, int max_ctas = 0, CtaTrace tr = CtaTrace{});
 cudaError_t launch_stage_rows_fp8(int rows, int k, int kpad, const float *L, int ld, unsigned char *stage, int lds,
                                   float *scale, cudaStream_t s);
 cudaError_t launch_stage_cols_fp8(int k, int kpad, int cols, const float *B, int ld, unsigned char *stage, int lds,
@@ -76,7 +77,7 @@ bool tc_c_aligned(const float *C, int ldc);
 // gemm_f64emu.cu
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s);
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr = CtaTrace{});
 cudaError_t launch_stage_rows_f64emu(int rows, int k, const double *L, int ld, __nv_bfloat16 *stage, int lds, double *scale,
                                      cudaStream_t s);
 cudaError_t launch_stage_cols_f64emu(int k, int cols, const double *B, int ld, __nv_bfloat16 *stage, int lds, double *scale,
@@ -227,6 +228,29 @@ struct TraceRec {
 bool g_trace_on = false;
 std::vector<TraceRec> g_trace;
 
+// per-CTA trace ring (lu_cta_trace), installed on one device
+struct CtaRing {
+    lu_cta_event *ring = nullptr;
+    int *count = nullptr;
+    int cap = 0;
+    int dev = -1;
+};
+CtaRing g_cta;
+
+// The trace argument for a launch of task `kind` at `step` (empty when off).
+CtaTrace cta_tag(int kind, int step) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    CtaTrace t{nullptr, nullptr, 0, 0};
+    int d = -1;
+    if (g_cta.ring && cudaGetDevice(&d) == cudaSuccess && d == g_cta.dev) {
+        t.ring = g_cta.ring;
+        t.count = g_cta.count;
+        t.cap = g_cta.cap;
+        t.tag = (kind << 24) | (step & 0xffffff);
+    }
+    return t;
+}
+
 bool trace_on() {
     std::lock_guard<std::mutex> lk(g_tmu);
     return g_trace_on;
@@ -361,21 +385,21 @@ struct FactorCtx {
 };
 
 template <typename T>
-cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s);
+cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr);
 
 // C[rows r0.., cols c0..c1) -= L(rows r0.., cols kb..kb+w) * U(rows kb..kb+w, cols c0..c1)
 template <typename T>
-cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s) {
+cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr) {
     const int r0 = kb + w;
     const int m = c.n - r0, nn = c1 - c0;
     if (m <= 0 || nn <= 0) return cudaSuccess;
-    if (!timing_on()) return update_launch<T>(c, k_par, kb, w, c0, c1, s);
+    if (!timing_on()) return update_launch<T>(c, k_par, kb, w, c0, c1, s, tr);
     TimedLaunch t;
     cudaError_t e;
     if ((e = cudaEventCreate(&t.a)) != cudaSuccess) return e;
     if ((e = cudaEventCreate(&t.b)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t.a, s)) != cudaSuccess) return e;
-    if ((e = update_launch<T>(c, k_par, kb, w, c0, c1, s)) != cudaSuccess) return e;
+    if ((e = update_launch<T>(c, k_par, kb, w, c0, c1, s, tr)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t.b, s)) != cudaSuccess) return e;
     const int k = c.pl.tc ? c.kinner : w;   // staged operand width (hi and lo halves with the split)
     const double opw = c.pl.tc ? (c.pl.fmt == 2 ? 1.0 : 2.0) : (double)sizeof(T);
@@ -387,31 +411,32 @@ cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cu
 }
 
 template <typename T>
-cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s) {
+cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr) {
     const int r0 = kb + w;
     const int m = c.n - r0, nn = c1 - c0;
     if constexpr (sizeof(T) == 8) {
         if (c.pl.tc)
             return launch_gemm_f64emu(m, nn, c.mapA[k_par], 0, c.mapB, c0 - r0, reinterpret_cast<double *>(c.A) + r0 + (size_t)c0 * c.lda,
                                       c.lda, c.dscA[k_par], c.dscB, c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status,
-                                      c.pl.bound, s == c.st->P ? 0 : c.pl.update_ctas, s);
+                                      c.pl.bound, s == c.st->P ? 0 : c.pl.update_ctas, s, tr);
     }
     if constexpr (sizeof(T) == 4) {
         if (c.pl.tc)
             return launch_gemm_tc(c.pl.fmt == 1 ? 3 : (c.pl.fmt == 2 ? 8 : 1), m, nn, c.kpad, c.mapA[k_par], 0, c.mapB,
                                   c0 - r0, reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda,
                                   c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status, c.pl.bound, s, c.scA[k_par], c.scB,
-                                  s == c.st->P ? 0 : c.pl.update_ctas);
+                                  s == c.st->P ? 0 : c.pl.update_ctas, tr);
     }
     return launch_gemm_simt<T>(m, nn, w, c.A + r0 + (size_t)kb * c.lda, c.lda, c.A + kb + (size_t)c0 * c.lda, c.lda,
-                               c.A + r0 + (size_t)c0 * c.lda, c.lda, s);
+                               c.A + r0 + (size_t)c0 * c.lda, c.lda, s, tr);
 }
 
 template <typename T>
-cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, int c1, int do_trsm, cudaStream_t s) {
+cudaError_t swap_trsm(FactorCtx<T> &c, int kb, int w, const int *map, int c0, int c1, int do_trsm, cudaStream_t s,
+                      CtaTrace tr) {
     StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt, nullptr};
     if (do_trsm && c.pl.tc) { sd.ptr = c.stB; sd.scale = c.scB; sd.dscale = c.dscB; }
-    return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, sd, kb + w, s);
+    return launch_swap_trsm<T>(c.A, c.lda, kb, w, map, c0, c1, do_trsm, sd, kb + w, s, tr);
 }
 
 // Inner width of the outer panel at column kb (width w) of an order-n
@@ -435,13 +460,13 @@ bool plan_fits(const Plan &pl, int n, size_t elem) {
 // Factor outer panel at column kb (width w) on stream s: one cluster launch
 // that also leaves the row map in maps[par], updates perm and stages L21.
 template <typename T>
-cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s) {
+cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s, CtaTrace tr) {
     StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt, nullptr};
     if (c.pl.tc && kb + w < c.n) { sd.ptr = c.stA[par]; sd.scale = c.scA[par]; sd.dscale = c.dscA[par]; }
     return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, plan_inner_width(c.pl, c.n, sizeof(T), kb, w),
                                  c.ipiv + kb, kb,
                                  c.info, c.maps[par], c.perm, sd, c.pl.panel_ctas, kPanelSmemCap, c.st->status,
-                                 c.pl.bound, s);
+                                 c.pl.bound, s, tr);
 }
 
 template <typename T>
@@ -515,7 +540,8 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
 
     const int nblk = (n + bo - 1) / bo;
     // prologue: panel 0
-    LU_CUDA_TRY(traced(LU_TRACE_PANEL, 0, 0, P, [&] { return factor_outer_panel<T>(c, 0, std::min(bo, n), 0, P); }));
+    LU_CUDA_TRY(traced(LU_TRACE_PANEL, 0, 0, P,
+                       [&] { return factor_outer_panel<T>(c, 0, std::min(bo, n), 0, P, cta_tag(LU_TRACE_PANEL, 0)); }));
     LU_CUDA_TRY(cudaEventRecord(st->evP[0], P));
     for (int k = 0; k < nblk; ++k) {
         const int kb = k * bo, w = std::min(bo, n - kb), par = k & 1;
@@ -525,28 +551,36 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
         // ---- T_RU on U, first part: interchanges left of panel k, RU1 ------------
         LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evP[par], 0));
         if (kb > 0)
-            LU_CUDA_TRY(traced(LU_TRACE_SWAP_LEFT, k, 1, U, [&] { return swap_trsm<T>(c, kb, w, map, 0, kb, 0, U); }));
+            LU_CUDA_TRY(traced(LU_TRACE_SWAP_LEFT, k, 1, U,
+                               [&] { return swap_trsm<T>(c, kb, w, map, 0, kb, 0, U, cta_tag(LU_TRACE_SWAP_LEFT, k)); }));
         if (rest0 < n)
-            LU_CUDA_TRY(traced(LU_TRACE_RU1, k, 1, U, [&] { return swap_trsm<T>(c, kb, w, map, rest0, n, 1, U); }));
+            LU_CUDA_TRY(traced(LU_TRACE_RU1, k, 1, U,
+                               [&] { return swap_trsm<T>(c, kb, w, map, rest0, n, 1, U, cta_tag(LU_TRACE_RU1, k)); }));
         // ---- T_PF on P: PF1, PF2 on strip k+1, then PF3 = panel k+1 ------------------
         if (wn > 0 && pl.lookahead) {
             if (k > 0) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par ^ 1], 0));
-            LU_CUDA_TRY(traced(LU_TRACE_PF1, k, 0, P, [&] { return swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P); }));
-            LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P, [&] { return update<T>(c, par, kb, w, cn0, cn0 + wn, P); }));
+            LU_CUDA_TRY(traced(LU_TRACE_PF1, k, 0, P,
+                               [&] { return swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P, cta_tag(LU_TRACE_PF1, k)); }));
+            LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P,
+                               [&] { return update<T>(c, par, kb, w, cn0, cn0 + wn, P, cta_tag(LU_TRACE_PF2, k)); }));
             // RU2 starts after PF2: when both become ready the panel (higher
             // priority) is dispatched first, and RU2's queued CTAs fill the
             // rest of the GPU and later the SMs the panel cluster frees
             LU_CUDA_TRY(cudaEventRecord(st->evPF2, P));
-            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P, [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P); }));
+            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P,
+                               [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
             LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
             LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evPF2, 0));
         }
         // ---- T_RU on U, second part: RU2 ----------------------------------------------
-        if (rest0 < n) LU_CUDA_TRY(traced(LU_TRACE_RU2, k, 1, U, [&] { return update<T>(c, par, kb, w, rest0, n, U); }));
+        if (rest0 < n)
+            LU_CUDA_TRY(traced(LU_TRACE_RU2, k, 1, U,
+                               [&] { return update<T>(c, par, kb, w, rest0, n, U, cta_tag(LU_TRACE_RU2, k)); }));
         LU_CUDA_TRY(cudaEventRecord(st->evU[par], U));
         if (wn > 0 && !pl.lookahead) {
             LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par], 0));
-            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P, [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P); }));
+            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P,
+                               [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
             LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
         }
     }
@@ -987,6 +1021,51 @@ int lu_trace_read(lu_trace_event *out, int max_events) {
         cudaEventDestroy(t.b);
     }
     return rc == LU_OK ? (out ? nout : (int)v.size()) : rc;
+}
+
+int lu_cta_trace(int capacity) {
+    if (capacity < 0) return -1;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (g_cta.ring) {
+        int d = -1;
+        cudaGetDevice(&d);
+        cudaSetDevice(g_cta.dev);
+        cudaDeviceSynchronize();
+        cudaFree(g_cta.ring);
+        cudaFree(g_cta.count);
+        cudaSetDevice(d);
+        g_cta = CtaRing{};
+    }
+    if (capacity == 0) return LU_OK;
+    CtaRing r;
+    LU_CUDA_TRY(cudaGetDevice(&r.dev));
+    if (cudaMalloc(&r.ring, sizeof(lu_cta_event) * (size_t)capacity) != cudaSuccess) return LU_ERR_NOMEM;
+    if (cudaMalloc(&r.count, sizeof(int)) != cudaSuccess) {
+        cudaFree(r.ring);
+        return LU_ERR_NOMEM;
+    }
+    LU_CUDA_TRY(cudaMemset(r.count, 0, sizeof(int)));
+    r.cap = capacity;
+    g_cta = r;
+    return LU_OK;
+}
+
+int lu_cta_trace_read(lu_cta_event *out, int max_events) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (!g_cta.ring) return 0;
+    int d = -1;
+    LU_CUDA_TRY(cudaGetDevice(&d));
+    LU_CUDA_TRY(cudaSetDevice(g_cta.dev));
+    LU_CUDA_TRY(cudaDeviceSynchronize());
+    int made = 0;
+    LU_CUDA_TRY(cudaMemcpy(&made, g_cta.count, sizeof(int), cudaMemcpyDeviceToHost));
+    const int avail = std::min(made, g_cta.cap);
+    if (out && max_events > 0 && avail > 0)
+        LU_CUDA_TRY(cudaMemcpy(out, g_cta.ring, sizeof(lu_cta_event) * (size_t)std::min(avail, max_events),
+                               cudaMemcpyDeviceToHost));
+    LU_CUDA_TRY(cudaMemset(g_cta.count, 0, sizeof(int)));
+    LU_CUDA_TRY(cudaSetDevice(d));
+    return made;
 }
 
 long long lu_kernel_launches(void) { return g_launches.load(); }

@@ -70,6 +70,39 @@ __device__ __forceinline__ bool lu_wait_flag(const int *flag, int target, int *s
     return true;
 }
 
+// Per-CTA trace (lu_cta_trace): a kernel given a ring appends one record per
+// CTA when it finishes.  tag = LU_TRACE_* kind << 24 | step.
+struct CtaTrace {
+    lu_cta_event *ring;   // device ring, nullptr when tracing is off
+    int *count;           // device count of records made
+    int cap;
+    int tag;
+};
+
+__device__ __forceinline__ unsigned lu_smid() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %smid;" : "=r"(r));
+    return r;
+}
+
+// Called by one thread of the CTA at its end; t0 = %globaltimer at its start.
+__device__ __forceinline__ void lu_trace_cta(const CtaTrace &tr, unsigned long long t0, int tiles) {
+    if (!tr.ring) return;
+    const int slot = atomicAdd(tr.count, 1);
+    if (slot < tr.cap) {
+        lu_cta_event e;
+        e.kind = tr.tag >> 24;
+        e.step = tr.tag & 0xffffff;
+        e.cta = (int)blockIdx.x + (int)blockIdx.y * (int)gridDim.x;
+        e.smid = (int)lu_smid();
+        e.tiles = tiles;
+        e.pad = 0;
+        e.t0_ns = t0;
+        e.t1_ns = lu_globaltimer();
+        tr.ring[slot] = e;
+    }
+}
+
 template <typename T> struct lu_abs_t;
 template <> struct lu_abs_t<double> { __device__ static double f(double x) { return fabs(x); } };
 template <> struct lu_abs_t<float>  { __device__ static float f(float x) { return fabsf(x); } };

@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kEmThreads, 1)
 gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a_row0,
                    const __grid_constant__ CUtensorMap mapB, int b_col0, double *__restrict__ C, int ldc,
                    const double *__restrict__ scaleA, const double *__restrict__ scaleB, int nsub,
-                   int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns) {
+                   int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns, CtaTrace tr) {
+    const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -81,6 +82,7 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
     volatile int *acc_task = ints + 2 + 2 * kEmStagesB;   // [2]
     volatile int *acc_sub = ints + 4 + 2 * kEmStagesB;    // [2]
     volatile int *issued = ints + 6 + 2 * kEmStagesB;     // [1 + kEmStagesB]: parity of a load in flight + 1, 0 none
+    volatile int *ntasks_done = ints + 7 + 3 * kEmStagesB; // tasks this CTA took
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mt = (m + kEmBM - 1) / kEmBM;
@@ -94,6 +96,7 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
         for (int i = 0; i < 2; ++i) { mbar_init(accf0 + 8u * i, 1); mbar_init(acce0 + 8u * i, 256); mbar_init(tilef0 + 8u * i, 1); }
         *abort_flag = 0;
         for (int i = 0; i <= kEmStagesB; ++i) issued[i] = 0;
+        *ntasks_done = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -116,6 +119,7 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
                 int t = atomicAdd(tile_ctr, 1);
                 if (t >= ntasks || *abort_flag) t = -1;
                 if (t >= 0) {
+                    *ntasks_done = *ntasks_done + 1;
                     const int tm = (t % mt) * kEmBM, tn = (t / mt) * cols_task;
                     const int nj = min(nsub, (n - tn + kEmBN - 1) / kEmBN);
                     // the previous task's MMAs must be done with the A slices
@@ -166,11 +170,13 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
                 int t = -1, sub = 0;
                 if (!mbar_wait_bounded(b_full0 + 8u * sb, bph, bound_ns)) { *abort_flag = 1; stop = true; }
                 else { t = stage_task[sb]; sub = stage_sub[sb]; }
+                // the accumulator must be free before its task index is replaced, the end
+                // marker included: tile_full may run at most one phase ahead of the epilogue
+                if (!stop && !mbar_wait_bounded(acce0 + 8u * a, acc_ph ^ 1u, bound_ns)) { *abort_flag = 1; stop = true; }
                 if (!stop && t >= 0 && (sub & (kEmLast - 1)) == 0) {
                     if (!mbar_wait_bounded(a_full, aph, bound_ns)) { *abort_flag = 1; stop = true; }
                     aph ^= 1u;
                 }
-                if (!stop && t >= 0 && !mbar_wait_bounded(acce0 + 8u * a, acc_ph ^ 1u, bound_ns)) { *abort_flag = 1; stop = true; }
                 if (stop || t < 0 || *abort_flag) {
                     acc_task[a] = -1;
                     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tilef0 + 8u * a) : "memory");
@@ -263,6 +269,7 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kEmTmemCols) : "memory");
     }
+    if (tid == 0) lu_trace_cta(tr, t_start, *ntasks_done);
 }
 
 // ---- operand staging (standalone; inside the factorization the panel kernel
@@ -313,7 +320,7 @@ int f64emu_box_cols() { return kEmBN; }
 // scaleA[a_row0 + i], scaleB[b_col0 + j].  C: FP64, any alignment.
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s) {
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     static int sms = 0;
     if (!sms) {
@@ -337,7 +344,7 @@ cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0
     cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
     if (ez != cudaSuccess) return ez;
     gemm_update_f64emu<<<grid, kEmThreads, kEmSmem, s>>>(m, n, mapA, a_row0, mapB, b_col0, C, ldc, scaleA, scaleB, nsub,
-                                                          tile_ctr, status, bound_ns);
+                                                          tile_ctr, status, bound_ns, tr);
     lu_count_launch();
     return cudaGetLastError();
 }

@@ -22,7 +22,8 @@ constexpr int kGK = 16;
 template <typename T, int TM, int TN>
 __global__ void __launch_bounds__((TM / 4) * (TN / 4))
 gemm_update_simt(int m, int n, int k, const T *__restrict__ A, int lda, const T *__restrict__ B, int ldb,
-                 T *__restrict__ C, int ldc) {
+                 T *__restrict__ C, int ldc, CtaTrace tr) {
+    const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr int TX = TM / 4, TY = TN / 4, NT = TX * TY;
     __shared__ T As[kGK][TM];       // As[kk][row]
     __shared__ T Bs[kGK][TN + 1];   // Bs[kk][col]
@@ -75,11 +76,12 @@ gemm_update_simt(int m, int n, int k, const T *__restrict__ A, int lda, const T 
             }
         }
     }
+    if (threadIdx.x == 0) lu_trace_cta(tr, t_start, 1);
 }
 
 template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc,
-                             cudaStream_t s) {
+                             cudaStream_t s, CtaTrace tr) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
     static int sms = 0;
     if (!sms) {
@@ -92,16 +94,18 @@ cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *
     if (big >= sms) {
         dim3 grid(lu_ceil_div(m, 64), lu_ceil_div(n, 64));
         if (grid.y > 65535) return cudaErrorInvalidValue;
-        gemm_update_simt<T, 64, 64><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc);
+        gemm_update_simt<T, 64, 64><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, tr);
     } else {
         dim3 grid(lu_ceil_div(m, 32), lu_ceil_div(n, 32));
-        gemm_update_simt<T, 32, 32><<<grid, 64, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc);
+        gemm_update_simt<T, 32, 32><<<grid, 64, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, tr);
     }
     lu_count_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t launch_gemm_simt<double>(int, int, int, const double *, int, const double *, int, double *, int, cudaStream_t);
-template cudaError_t launch_gemm_simt<float>(int, int, int, const float *, int, const float *, int, float *, int, cudaStream_t);
+template cudaError_t launch_gemm_simt<double>(int, int, int, const double *, int, const double *, int, double *, int, cudaStream_t,
+                                              CtaTrace);
+template cudaError_t launch_gemm_simt<float>(int, int, int, const float *, int, const float *, int, float *, int, cudaStream_t,
+                                             CtaTrace);
 
 }  // namespace lu

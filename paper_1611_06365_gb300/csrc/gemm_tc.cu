@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, int a_row0,
                const __grid_constant__ CUtensorMap mapB, int b_col0, const __grid_constant__ CUtensorMap mapC,
                int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns,
-               const float *__restrict__ scaleA, const float *__restrict__ scaleB) {
+               const float *__restrict__ scaleA, const float *__restrict__ scaleB, CtaTrace tr) {
+    const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr bool FP8 = NPROD == 8;
     constexpr int BK = FP8 ? kTcBK8 : kTcBK;        // K elements per 128-byte chunk
     constexpr int NSPLIT = NPROD == 3 ? 2 : 1;
@@ -76,6 +77,7 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     volatile int *stage_tile = reinterpret_cast<volatile int *>(tmem_slot + 2);        // [kStages]
     volatile int *acc_tile = reinterpret_cast<volatile int *>(tmem_slot + 2 + kStages);  // [2]
+    volatile int *ntiles_done = reinterpret_cast<volatile int *>(tmem_slot + 4 + kStages);  // tiles this CTA took
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nk = K / BK;                          // K is a multiple of BK
@@ -93,6 +95,7 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
         mbar_init(cfull, 1);
         mbar_init(cempty, 1);
         *abort_flag = 0;
+        *ntiles_done = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -114,6 +117,7 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
             for (;;) {
                 int t = atomicAdd(tile_ctr, 1);
                 if (t >= ntiles || *abort_flag) t = -1;
+                if (t >= 0) *ntiles_done = *ntiles_done + 1;
                 const int tm = t >= 0 ? (t % mt) * kTcBM : 0, tn = t >= 0 ? (t / mt) * kTcBN : 0;
                 bool ok = true;
                 const int chunks = t >= 0 ? nk : 1;
@@ -272,6 +276,7 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTcBN) : "memory");
     }
+    if (tid == 0) lu_trace_cta(tr, t_start, *ntiles_done);
 }
 
 // ---- operand staging -------------------------------------------------------
@@ -399,7 +404,7 @@ bool tc_c_aligned(const float *C, int ldc) { return ((uintptr_t)C % 16 == 0) && 
 template <int NPROD>
 static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                                   int b_col0, const CUtensorMap &mapC, int *tile_ctr, int *status, long long bound_ns,
-                                  const float *scaleA, const float *scaleB, cudaStream_t s) {
+                                  const float *scaleA, const float *scaleB, cudaStream_t s, const CtaTrace &tr) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
@@ -407,7 +412,7 @@ static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorM
         attr = true;
     }
     gemm_update_tc<NPROD><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
-                                                             bound_ns, scaleA, scaleB);
+                                                             bound_ns, scaleA, scaleB, tr);
     lu_count_launch();
     return cudaGetLastError();
 }
@@ -418,7 +423,7 @@ static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorM
 // C must be 16-byte aligned with ldc a multiple of 4 (tc_c_aligned).
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                            int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
-                           const float *scaleA, const float *scaleB, int max_ctas) {
+                           const float *scaleA, const float *scaleB, int max_ctas, CtaTrace tr) {
     if (m <= 0 || n <= 0 || K <= 0) return cudaSuccess;
     if (nprod != 1 && nprod != 3 && nprod != 8) return cudaErrorInvalidValue;
     const int bk = nprod == 8 ? kTcBK8 : kTcBK;
@@ -441,9 +446,9 @@ cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &ma
     const int grid = ntiles < cap ? ntiles : cap;
     cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
     if (ez != cudaSuccess) return ez;
-    if (nprod == 1) return launch_tc_mode<1>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s);
-    if (nprod == 3) return launch_tc_mode<3>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s);
-    return launch_tc_mode<8>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, scaleA, scaleB, s);
+    if (nprod == 1) return launch_tc_mode<1>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s, tr);
+    if (nprod == 3) return launch_tc_mode<3>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s, tr);
+    return launch_tc_mode<8>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, scaleA, scaleB, s, tr);
 }
 
 cudaError_t launch_stage_rows(int rows, int k, int kpad, const float *L, int ld, __nv_bfloat16 *stage, int lds, int split,

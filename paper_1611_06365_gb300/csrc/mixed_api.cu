@@ -10,7 +10,8 @@
 //      as right preconditioner and FP64 products with A, so that rounding in
 //      the FP32 preconditioner solve does not limit the attainable accuracy;
 //   2  the FP64 factorization of this library (by default with the emulated
-//      FP64 update on the tensor cores), then classic refinement.
+//      FP64 update on the tensor cores), then classic refinement; if that
+//      does not reach the target, the FP64 factorization with the DFMA update.
 // Convergence: normwise backward error
 //   eta = max_q ||b_q - A x_q||_inf / (||A||_inf ||x_q||_inf + ||b_q||_inf)
 // at most `tol`.  Stall: eta has not halved over the last two steps, or
@@ -269,6 +270,30 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             if (eta <= tol) break;
         }
         done = eta <= tol;
+        if (!done && o64.update == LU_UPDATE_F64EMU && (allow_fb || fp64_only)) {
+            // the emulated FP64 factors did not reach the target: the DFMA factorization
+            LU_CUDA_TRY(cudaMemcpy2DAsync(A64, sizeof(double) * n, dA, sizeof(double) * lda, sizeof(double) * n, n,
+                                          cudaMemcpyDeviceToDevice, s));
+            o64.update = LU_UPDATE_NATIVE;
+            rc = factor_f64_internal(n, A64, n, ipiv64, info64, perm64, &o64, s);
+            if (rc != LU_OK) return rc;
+            LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
+            LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
+                                          cudaMemcpyDeviceToDevice, s));
+            for (int it = 0; it < 5; ++it) {
+                LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
+                rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
+                if (rc != LU_OK) return rc;
+                LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));
+                LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
+                LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
+                rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+                if (rc != LU_OK) return rc;
+                r.iterations++;
+                if (eta <= tol) break;
+            }
+            done = eta <= tol;
+        }
     }
     // forward-error estimate: one more correction with the finishing rung's factors
     if (hinfo == 0 || factors64) {

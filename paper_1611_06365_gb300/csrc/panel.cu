@@ -334,7 +334,8 @@ template <typename T, int RPT>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, int *__restrict__ ipiv, int row_base,
                      int *__restrict__ info, int *__restrict__ map_out, int *__restrict__ perm,
-                     StageDesc sd, int *__restrict__ status, long long bound_ns) {
+                     StageDesc sd, int *__restrict__ status, long long bound_ns, CtaTrace tr) {
+    const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr int BI = TileWidth<T, RPT>::BI;
     using V = typename Vec16<T>::type;
     constexpr int VEC = 16 / sizeof(T);
@@ -725,6 +726,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
         }
     }
     cl.sync();   // no CTA leaves while a peer may still address its shared memory
+    if (tid == 0) lu_trace_cta(tr, t_start, 0);
 }
 
 // Rows per thread for a CTA of R rows (a power of two).
@@ -778,7 +780,8 @@ static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap,
 
 template <typename T, int RPT>
 static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int bo, int bi, int R, int *ipiv,
-                              int row_base, int *info, int *map_out, int *perm, StageDesc sd, int *status, long long bound_ns) {
+                              int row_base, int *info, int *map_out, int *perm, StageDesc sd, int *status, long long bound_ns,
+                              const CtaTrace &tr) {
     cudaError_t e = cudaFuncSetAttribute(panel_factor_cluster<T, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.dynamicSmemBytes);
     if (e != cudaSuccess) return e;
@@ -786,7 +789,7 @@ static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int
     if (e != cudaSuccess) return e;
     lu_count_launch();
     return cudaLaunchKernelEx(&cfg, panel_factor_cluster<T, RPT>, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out,
-                              perm, sd, status, bound_ns);
+                              perm, sd, status, bound_ns, tr);
 }
 
 // Host launcher: factor the m x bo panel at P with inner width bi; pivots into
@@ -797,7 +800,7 @@ static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
-                               cudaStream_t s) {
+                               cudaStream_t s, CtaTrace tr) {
     if (bi <= 0 || bo <= 0 || bo > kPanelBoMax || m <= 0) return cudaErrorInvalidValue;
     if (bi > bo) bi = bo;
     if (bi > kPanelWMax) return cudaErrorInvalidValue;
@@ -817,10 +820,10 @@ cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     switch (rows_per_thread(R)) {
-        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
-        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
-        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
-        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns);
+        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
+        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
+        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
+        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -848,8 +851,8 @@ bool panel_fits(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_ca
 }
 
 template cudaError_t launch_panel_outer<double>(double *, int, int, int, int, int *, int, int *, int *, int *, StageDesc,
-                                                int, size_t, int *, long long, cudaStream_t);
+                                                int, size_t, int *, long long, cudaStream_t, CtaTrace);
 template cudaError_t launch_panel_outer<float>(float *, int, int, int, int, int *, int, int *, int *, int *, StageDesc, int,
-                                               size_t, int *, long long, cudaStream_t);
+                                               size_t, int *, long long, cudaStream_t, CtaTrace);
 
 }  // namespace lu

@@ -7,12 +7,12 @@
 //   kind 2  DMMA: mma.sync m8n8k4 with FP64 operands (the legacy FP64 tensor
 //           path; tcgen05 has no FP64 kind)
 //
-// Every thread runs 16 independent accumulations (a 4 x 4 outer product per
-// step, the register pattern of the tiled update), every DMMA warp 4, so the
-// pipe never waits on a result; the grid holds kCtasPerSm CTAs of 256 threads
-// per SM.  The accumulators grow linearly from small positive products, so
-// nothing overflows or goes subnormal, and a data-dependent store keeps the
-// compiler from removing the work.
+// The FMA probes run the compute loop of the tiled update (a 4 x 4 outer
+// product per thread per step of K, operands from shared memory, 16
+// independent accumulators); every DMMA warp runs 4 chains; the grid holds
+// kCtasPerSm CTAs of 256 threads per SM.  The accumulators grow linearly from
+// small positive products, so nothing overflows or goes subnormal, and a
+// data-dependent store keeps the compiler from removing the work.
 #include "common.cuh"
 
 namespace lu {
@@ -22,23 +22,35 @@ constexpr int kProbeCtasPerSm = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(kProbeThreads) fma_probe(long long iters, T m, T c, T *sink) {
-    // the register pattern of a tiled update: a 4 x 4 outer product per step,
-    // 16 independent accumulators fed by 8 distinct operand registers
-    T a[4], b[4], acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        a[i] = m * T(1 + (threadIdx.x & 7) + i);
-        b[i] = c * T(1 + i);
-    }
+    // the inner loop of the tiled update (gemm_simt.cu) without its global
+    // traffic: a 64 x 64 tile, 4 x 4 outputs per thread, operands read from
+    // shared memory at every step of K
+    constexpr int TM = 64, TN = 64, TX = TM / 4, TY = TN / 4;
+    __shared__ T As[16][TM];
+    __shared__ T Bs[16][TN + 1];
+    for (int e = threadIdx.x; e < 16 * TM; e += kProbeThreads) As[e / TM][e % TM] = m * T(1 + (e & 7));
+    for (int e = threadIdx.x; e < 16 * (TN + 1); e += kProbeThreads) Bs[e / (TN + 1)][e % (TN + 1)] = c * T(1 + (e & 3));
+    __syncthreads();
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     for (long long it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int kk = 0; kk < 16; ++kk) {
+            T a[4], b[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + TX * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + TY * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();   // as between the update's K chunks (and the operands are read again)
     }
     T s = T(0);
 #pragma unroll
@@ -88,10 +100,10 @@ extern "C" int lu_peak_probe(int kind, long long iters, double *tflops, double *
     const double threads = (double)grid * lu::kProbeThreads;
     if (kind == 0) {
         lu::fma_probe<double><<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.999, 1e-3, static_cast<double *>(sink));
-        flops = threads * (double)iters * 16 * 2.0;
+        flops = threads * (double)iters * 16 * 16 * 2.0;
     } else if (kind == 1) {
         lu::fma_probe<float><<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.999f, 1e-3f, static_cast<float *>(sink));
-        flops = threads * (double)iters * 16 * 2.0;
+        flops = threads * (double)iters * 16 * 16 * 2.0;
     } else {
         lu::dmma_probe<<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.5, static_cast<double *>(sink));
         flops = threads / 32.0 * (double)iters * 4.0 * (2.0 * 8 * 8 * 4);

@@ -55,7 +55,8 @@ struct SwapLayout {
 template <typename T>
 __global__ void __launch_bounds__(kSwapThreads, 2)
 swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restrict__ map, int c_begin,
-                 int c_end, int do_trsm, StageDesc sd, int stage_c0) {
+                 int c_end, int do_trsm, StageDesc sd, int stage_c0, CtaTrace tr) {
+    const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr int DB = TrsmBlk<T>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SwapLayout<T> lay(b);
@@ -87,7 +88,10 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
         const int s = first + e % (cnt - first), c = e / (cnt - first);
         A[(size_t)rows[s] + (size_t)(c0 + c) * lda] = V[(size_t)s * kVS + c];
     }
-    if (!do_trsm) return;
+    if (!do_trsm) {
+        if (tid == 0) lu_trace_cta(tr, t_start, 1);
+        return;
+    }
 
     const T *L11 = A + (size_t)kb + (size_t)kb * lda;
     for (int d0 = 0; d0 < b; d0 += DB) {
@@ -202,6 +206,7 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
             const int r = e % b, cc = e / b;
             A[(size_t)(kb + r) + (size_t)(c0 + cc) * lda] = V[(size_t)r * kVS + cc];
         }
+        if (tid == 0) lu_trace_cta(tr, t_start, 1);
         return;
     }
     const int kpad = sd.kpad;
@@ -234,6 +239,7 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
             }
         }
     }
+    if (tid == 0) lu_trace_cta(tr, t_start, 1);
 }
 
 size_t swap_trsm_smem_bytes(int b, size_t elem) {
@@ -242,7 +248,7 @@ size_t swap_trsm_smem_bytes(int b, size_t elem) {
 
 template <typename T>
 cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c_begin, int c_end,
-                             int do_trsm, StageDesc sd, int stage_c0, cudaStream_t s) {
+                             int do_trsm, StageDesc sd, int stage_c0, cudaStream_t s, CtaTrace tr) {
     if (c_end <= c_begin) return cudaSuccess;
     size_t smem = swap_trsm_smem_bytes(b, sizeof(T));
     static bool attr_set[2] = {false, false};
@@ -252,11 +258,13 @@ cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c
         attr_set[sizeof(T) == 8] = true;
     }
     int grid = lu_ceil_div(c_end - c_begin, kStrip);
-    swap_trsm_kernel<T><<<grid, kSwapThreads, smem, s>>>(A, lda, kb, b, map, c_begin, c_end, do_trsm, sd, stage_c0);
+    swap_trsm_kernel<T><<<grid, kSwapThreads, smem, s>>>(A, lda, kb, b, map, c_begin, c_end, do_trsm, sd, stage_c0, tr);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_swap_trsm<double>(double *, int, int, int, const int *, int, int, int, StageDesc, int, cudaStream_t);
-template cudaError_t launch_swap_trsm<float>(float *, int, int, int, const int *, int, int, int, StageDesc, int, cudaStream_t);
+template cudaError_t launch_swap_trsm<double>(double *, int, int, int, const int *, int, int, int, StageDesc, int, cudaStream_t,
+                                              CtaTrace);
+template cudaError_t launch_swap_trsm<float>(float *, int, int, int, const int *, int, int, int, StageDesc, int, cudaStream_t,
+                                             CtaTrace);
 
 }  // namespace lu

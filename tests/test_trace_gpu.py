@@ -1,0 +1,68 @@
+"""Per-CTA trace of the factorization kernels (lu_cta_trace): the GPU form of
+the paper's execution traces (section 4), and the evidence for worker sharing
+(section 4.1): SMs that ran the cluster of panel k+1 later run CTAs of the
+remainder update RU2 of step k that take update tiles."""
+import numpy as np
+import pytest
+
+import lu_inputs as li
+from tests.gpu_util import factor_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _trace(n, dtype, **opts):
+    import paper_1611_06365_gb300 as lu
+    lu.lu_cta_trace(1 << 21)
+    try:
+        A = li.uniform(n, n, seed=li.BASE_SEED + 77)
+        LU, ipiv, info, _, _ = factor_gpu(A, dtype, **opts)
+        made, ev = lu.lu_cta_trace_read(1 << 21)
+    finally:
+        lu.lu_cta_trace(0)
+    assert info == 0 and made == len(ev)
+    return ev
+
+
+def _sharing(ev):
+    """Steps k with an RU2(k) CTA that took tiles on an SM a panel(k+1) CTA had
+    left, starting after that panel CTA ended."""
+    panels = {}
+    for e in ev:
+        if e["kind"] == "panel":
+            panels.setdefault(e["step"], []).append(e)
+    steps = set()
+    for e in ev:
+        if e["kind"] != "ru2" or e["tiles"] < 1:
+            continue
+        for p in panels.get(e["step"] + 1, []):
+            if p["smid"] == e["smid"] and e["t0"] >= p["t1"]:
+                steps.add(e["step"])
+    return steps
+
+
+def _well_formed(ev, nsteps):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert all(e["t1"] >= e["t0"] and 0 <= e["smid"] < sms for e in ev)
+    kinds = {e["kind"] for e in ev}
+    assert {"panel", "ru1", "ru2", "pf1", "pf2"} <= kinds
+    assert sorted({e["step"] for e in ev if e["kind"] == "panel"}) == list(range(nsteps))
+
+
+@pytest.mark.parametrize("dtype,update,n,nb", [("f64", 0, 2048, 32), ("f32", 2, 4096, 64), ("f64", 4, 4096, 64)])
+def test_panel_sms_join_the_remainder_update(dtype, update, n, nb):
+    ev = _trace(n, dtype, nb=nb, update=update)
+    _well_formed(ev, (n + nb - 1) // nb)
+    shared = _sharing(ev)
+    assert len(shared) >= 1, "no step shows a panel SM taking update tiles afterwards"
+
+
+def test_trace_off_records_nothing():
+    import paper_1611_06365_gb300 as lu
+    A = li.uniform(300, 300, seed=3)
+    factor_gpu(A, "f64")
+    lu.lu_cta_trace(1024)
+    made, ev = lu.lu_cta_trace_read(1024)
+    lu.lu_cta_trace(0)
+    assert made == 0 and ev == []
