@@ -94,6 +94,10 @@ typedef struct {
                           0 = 8 for LU_F64, 16 for LU_F32; a panel whose rows do not fit
                           that many CTAs' register tiles takes more */
     int lookahead;     /* 0 (auto) or 1: static look-ahead with worker sharing;
+                          d = 2..4: look-ahead of depth d (the panel branch keeps the
+                          next d column strips current, so panel k+1 no longer waits
+                          for the remainder update of step k-1; section 3.2 notes the
+                          look-ahead can span more than one panel);
                           -1: plain blocked RL without look-ahead */
     int update;        /* LU_UPDATE_*: BF16 .. FP8 with LU_F32, F64EMU with LU_F64 */
     long long spin_ns; /* bound for device-side waits in ns (0 = 2 s) */
@@ -284,12 +288,14 @@ typedef struct {
  * lu_autotune -- times lu_factor(dt, n) for candidate plans on a scratch n x n
  * matrix (entries uniform in [-1, 1), allocated stream-ordered on `stream`,
  * 2 n^2 elements) and records the fastest in the table.  Candidates: the
- * built-in plan; b_o in {16, 32, 64} (FP64) or {64, 128, 256} (FP32 and the
- * tensor-core updates); then panel teams of 8 and 4 CTAs at the best b_o; for
- * n <= 2048 also the plan without look-ahead; for the tensor-core updates also
- * a remainder-update grid of 112 CTAs (update_ctas).  budget_ms > 0 stops adding
- * candidates once that much device time has been spent (at least one is timed).
- * update: LU_UPDATE_* (not NATIVE only with LU_F32).  Synchronizes `stream`.
+ * built-in plan; b_o in {16, 32, 64} (FP64), {32, 64} (emulated FP64) or
+ * {64, 128, 256} (FP32 and its tensor-core updates); then panel teams of 8 and
+ * 4 CTAs at the best b_o; for n <= 2048 also the plan without look-ahead; the
+ * look-ahead of depth 2; for the tensor-core updates also a remainder-update
+ * grid of 112 CTAs (update_ctas).  budget_ms > 0 stops adding candidates once
+ * that much device time has been spent (at least one is timed).
+ * update: LU_UPDATE_* (BF16 .. FP8 with LU_F32, F64EMU with LU_F64).
+ * Synchronizes `stream`.
  * Returns 0, a negative argument index, LU_ERR_NOMEM, LU_ERR_CUDA or
  * LU_ERR_TIMEOUT; res (host) receives the winner.
  */

@@ -136,11 +136,13 @@ namespace {
 
 constexpr int kMaxDev = 64;
 constexpr size_t kPanelSmemCap = 200 * 1024;
+constexpr int kMaxDepth = 4;              // deepest look-ahead (lu_opts.lookahead)
+constexpr int kRing = kMaxDepth + 1;      // panels whose row maps / staging may be in use at once
 
 struct DevState {
     bool init = false;
     cudaStream_t P = nullptr, U = nullptr;
-    cudaEvent_t evP[2] = {nullptr, nullptr}, evU[2] = {nullptr, nullptr};
+    cudaEvent_t evP[kRing] = {}, evU[kRing] = {};
     cudaEvent_t evIn = nullptr, evOutP = nullptr, evOutU = nullptr, evPF2 = nullptr;
     int *status = nullptr;   // device status word
     int sms = 0;
@@ -163,7 +165,7 @@ cudaError_t dev_state(DevState **out) {
         if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return e;
         if ((e = cudaStreamCreateWithPriority(&st.P, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
         if ((e = cudaStreamCreateWithPriority(&st.U, cudaStreamNonBlocking, lo)) != cudaSuccess) return e;
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kRing; ++i) {
             if ((e = cudaEventCreateWithFlags(&st.evP[i], cudaEventDisableTiming)) != cudaSuccess) return e;
             if ((e = cudaEventCreateWithFlags(&st.evU[i], cudaEventDisableTiming)) != cudaSuccess) return e;
         }
@@ -300,7 +302,7 @@ struct Plan {
     bool bi_auto = true;   // per panel: the widest inner width its row count allows
     bool tc = false;  // tensor-core update
     int fmt = 0;      // staging format: 0 BF16, 1 split BF16, 2 FP8 e4m3, 3 FP64 digit slices (StageDesc)
-    bool lookahead = true;
+    int depth = 1;    // look-ahead depth d: strips k+1 .. k+d on the panel branch (0: none)
     int panel_ctas = 16;
     int update_ctas = 0;   // persistent CTAs of the remainder update (0: one per SM)
     long long bound = 2000000000LL;
@@ -338,7 +340,7 @@ Plan make_plan(int n, const lu_opts *o) {
     p.bi_auto = !(o && o->nb_inner > 0);
     p.bi = p.bi_auto ? wfit : std::min(o->nb_inner, wfit);
     p.bi = std::max(1, std::min(p.bi, p.bo));
-    p.lookahead = !(o && o->lookahead < 0);
+    p.depth = (o && o->lookahead < 0) ? 0 : ((o && o->lookahead > 1) ? std::min(o->lookahead, kMaxDepth) : 1);
     // FP64 panels: an 8-CTA team by default (the autotuner's choice at n = 512 ... 16384);
     // the geometry takes more CTAs when the rows do not fit 8
     p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : (sizeof(T) == 8 ? 8 : 16);
@@ -371,16 +373,17 @@ struct FactorCtx {
     int *perm;            // optional
     Plan pl;
     DevState *st;
-    int *maps[2];         // row maps of panels k (parity)
-    unsigned char *stA[2] = {nullptr, nullptr};   // staged L21 of panels k (parity), bytes
+    int ring = 2;         // panels in flight: look-ahead depth + 1 (2 at least)
+    int *maps[kRing] = {};                        // row maps of panels k (slot k % ring)
+    unsigned char *stA[kRing] = {};               // staged L21 of panels k (slot k % ring), bytes
     unsigned char *stB = nullptr;                 // staged U12
-    float *scA[2] = {nullptr, nullptr};           // FP8: row scales of stA
+    float *scA[kRing] = {};                       // FP8: row scales of stA
     float *scB = nullptr;                         // FP8: column scales of stB
-    double *dscA[2] = {nullptr, nullptr};         // FP64 digit slices: row scales of stA
+    double *dscA[kRing] = {};                     // FP64 digit slices: row scales of stA
     double *dscB = nullptr;                       // FP64 digit slices: column scales of stB
     int kpad = 0;
     int kinner = 0;   // staged elements per row/column (kpad, or 2 kpad when split)
-    CUtensorMap mapA[2], mapB;
+    CUtensorMap mapA[kRing], mapB;
     int *tile_ctr = nullptr;   // [0]: panel-branch updates, [1]: remainder-branch updates
 };
 
@@ -503,14 +506,15 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
     const int bo = pl.bo;
     // every panel of the plan must fit a cluster before anything is enqueued
     if (!plan_fits(pl, n, sizeof(T))) return LU_ERR_UNSUPPORTED;
-    for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
+    c.ring = std::max(2, pl.depth + 1);
+    for (int i = 0; i < c.ring; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
     LU_CUDA_TRY(ws.get(&c.tile_ctr, 2));
     if (perm) LU_CUDA_TRY(launch_iota(perm, n, caller));
     if (pl.tc && pl.fmt == 3) {
         // FP64 digit slices: kF64Slices slices of 64 K-elements per staged row / column
         c.kpad = f64emu_kpad();
         c.kinner = c.kpad * kF64Slices;
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < c.ring; ++i) {
             LU_CUDA_TRY(ws.get(&c.stA[i], (size_t)n * c.kinner * 2));
             LU_CUDA_TRY(ws.get(&c.dscA[i], (size_t)n));
             LU_CUDA_TRY(make_stage_map(&c.mapA[i], c.stA[i], c.kinner, n, c.kinner, f64emu_box_rows(), 0));
@@ -523,13 +527,13 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
         c.kpad = tc_kpad(bo, fp8);
         c.kinner = c.kpad * (pl.fmt == 1 ? 2 : 1);
         const size_t esz = fp8 ? 1 : 2;
-        for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.stA[i], (size_t)n * c.kinner * esz));
+        for (int i = 0; i < c.ring; ++i) LU_CUDA_TRY(ws.get(&c.stA[i], (size_t)n * c.kinner * esz));
         LU_CUDA_TRY(ws.get(&c.stB, (size_t)n * c.kinner * esz));
         if (fp8) {
-            for (int i = 0; i < 2; ++i) LU_CUDA_TRY(ws.get(&c.scA[i], (size_t)n));
+            for (int i = 0; i < c.ring; ++i) LU_CUDA_TRY(ws.get(&c.scA[i], (size_t)n));
             LU_CUDA_TRY(ws.get(&c.scB, (size_t)n));
         }
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < c.ring; ++i)
             LU_CUDA_TRY(make_stage_map(&c.mapA[i], c.stA[i], c.kinner, n, c.kinner, tc_box_rows(), fp8));
         LU_CUDA_TRY(make_stage_map(&c.mapB, c.stB, c.kinner, n, c.kinner, tc_box_cols(), fp8));
     }
@@ -539,17 +543,19 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
     LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evIn, 0));
 
     const int nblk = (n + bo - 1) / bo;
+    const int depth = pl.depth, R = c.ring;
     // prologue: panel 0
     LU_CUDA_TRY(traced(LU_TRACE_PANEL, 0, 0, P,
                        [&] { return factor_outer_panel<T>(c, 0, std::min(bo, n), 0, P, cta_tag(LU_TRACE_PANEL, 0)); }));
     LU_CUDA_TRY(cudaEventRecord(st->evP[0], P));
     for (int k = 0; k < nblk; ++k) {
-        const int kb = k * bo, w = std::min(bo, n - kb), par = k & 1;
+        const int kb = k * bo, w = std::min(bo, n - kb), sl = k % R, sl1 = (k + 1) % R, slp = (k + R - 1) % R;
         const int cn0 = kb + w, wn = std::min(bo, n - cn0);
-        const int *map = c.maps[par];
-        const int rest0 = pl.lookahead ? cn0 + wn : cn0;
+        const int *map = c.maps[sl];
+        // look-ahead window: strips k+1 .. k+depth on the panel branch, the rest on RU
+        const int rest0 = std::min(n, cn0 + depth * bo);
         // ---- T_RU on U, first part: interchanges left of panel k, RU1 ------------
-        LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evP[par], 0));
+        LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evP[sl], 0));
         if (kb > 0)
             LU_CUDA_TRY(traced(LU_TRACE_SWAP_LEFT, k, 1, U,
                                [&] { return swap_trsm<T>(c, kb, w, map, 0, kb, 0, U, cta_tag(LU_TRACE_SWAP_LEFT, k)); }));
@@ -557,31 +563,42 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
             LU_CUDA_TRY(traced(LU_TRACE_RU1, k, 1, U,
                                [&] { return swap_trsm<T>(c, kb, w, map, rest0, n, 1, U, cta_tag(LU_TRACE_RU1, k)); }));
         // ---- T_PF on P: PF1, PF2 on strip k+1, then PF3 = panel k+1 ------------------
-        if (wn > 0 && pl.lookahead) {
-            if (k > 0) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par ^ 1], 0));
+        if (wn > 0 && depth > 0) {
+            // strip k+1 was last updated by RU2(k-1) with depth 1, by this branch with depth >= 2
+            if (k > 0 && depth == 1) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[slp], 0));
             LU_CUDA_TRY(traced(LU_TRACE_PF1, k, 0, P,
                                [&] { return swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P, cta_tag(LU_TRACE_PF1, k)); }));
             LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P,
-                               [&] { return update<T>(c, par, kb, w, cn0, cn0 + wn, P, cta_tag(LU_TRACE_PF2, k)); }));
+                               [&] { return update<T>(c, sl, kb, w, cn0, cn0 + wn, P, cta_tag(LU_TRACE_PF2, k)); }));
             // RU2 starts after PF2: when both become ready the panel (higher
             // priority) is dispatched first, and RU2's queued CTAs fill the
             // rest of the GPU and later the SMs the panel cluster frees
             LU_CUDA_TRY(cudaEventRecord(st->evPF2, P));
             LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P,
-                               [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
-            LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
+                               [&] { return factor_outer_panel<T>(c, cn0, wn, sl1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
+            LU_CUDA_TRY(cudaEventRecord(st->evP[sl1], P));
+            // depth >= 2: strips k+2 .. k+depth after the panel, off its chain; the last of
+            // them was in RU2(k-1)'s range
+            const int s0 = cn0 + wn;
+            if (s0 < rest0) {
+                if (k > 0) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[slp], 0));
+                LU_CUDA_TRY(traced(LU_TRACE_PF1, k, 0, P,
+                                   [&] { return swap_trsm<T>(c, kb, w, map, s0, rest0, 1, P, cta_tag(LU_TRACE_PF1, k)); }));
+                LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P,
+                                   [&] { return update<T>(c, sl, kb, w, s0, rest0, P, cta_tag(LU_TRACE_PF2, k)); }));
+            }
             LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evPF2, 0));
         }
         // ---- T_RU on U, second part: RU2 ----------------------------------------------
         if (rest0 < n)
             LU_CUDA_TRY(traced(LU_TRACE_RU2, k, 1, U,
-                               [&] { return update<T>(c, par, kb, w, rest0, n, U, cta_tag(LU_TRACE_RU2, k)); }));
-        LU_CUDA_TRY(cudaEventRecord(st->evU[par], U));
-        if (wn > 0 && !pl.lookahead) {
-            LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[par], 0));
+                               [&] { return update<T>(c, sl, kb, w, rest0, n, U, cta_tag(LU_TRACE_RU2, k)); }));
+        LU_CUDA_TRY(cudaEventRecord(st->evU[sl], U));
+        if (wn > 0 && depth == 0) {
+            LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[sl], 0));
             LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P,
-                               [&] { return factor_outer_panel<T>(c, cn0, wn, par ^ 1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
-            LU_CUDA_TRY(cudaEventRecord(st->evP[par ^ 1], P));
+                               [&] { return factor_outer_panel<T>(c, cn0, wn, sl1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
+            LU_CUDA_TRY(cudaEventRecord(st->evP[sl1], P));
         }
     }
     LU_CUDA_TRY(cudaEventRecord(st->evOutP, P));
@@ -646,7 +663,7 @@ int lu_plan_info(lu_dtype dt, int n, const lu_opts *opts, lu_opts *plan) {
     plan->nb = p.bo;
     plan->nb_inner = plan_inner_width(p, n, elem, 0, std::min(p.bo, n));
     plan->panel_ctas = p.panel_ctas;
-    plan->lookahead = p.lookahead ? 1 : -1;
+    plan->lookahead = p.depth > 0 ? p.depth : -1;
     plan->update = opts ? opts->update : LU_UPDATE_NATIVE;
     plan->spin_ns = p.bound;
     plan->update_ctas = p.update_ctas;

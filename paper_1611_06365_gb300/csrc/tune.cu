@@ -73,7 +73,7 @@ lu_opts make_opts(int nb, int nb_inner, int panel_ctas, int lookahead, int updat
 }
 
 bool opts_in_range(int kind, const lu_opts &o) {
-    if (o.nb < 0 || o.nb_inner < 0 || o.panel_ctas < 0 || o.panel_ctas > 16 || o.lookahead < -1 || o.lookahead > 1 ||
+    if (o.nb < 0 || o.nb_inner < 0 || o.panel_ctas < 0 || o.panel_ctas > 16 || o.lookahead < -1 || o.lookahead > 4 ||
         o.update_ctas < 0 || o.update_ctas > 4096)
         return false;
     return kind != 1 || o.nb == 0 || o.nb == 1 || o.nb == 16 || o.nb == 32;
@@ -260,6 +260,8 @@ int lu_autotune(lu_dtype dt, int n, int update, double budget_ms, lu_tune_result
             if ((rc = consider(make_opts(best.nb, 0, pc, best.lookahead, update))) != LU_OK) break;
         if (rc != LU_OK) break;
         if (n <= 2048 && (rc = consider(make_opts(best.nb, 0, best.panel_ctas, -1, update))) != LU_OK) break;
+        // depth-2 look-ahead (section 3.2's look-ahead over more than one panel)
+        if (best.lookahead >= 0 && (rc = consider(make_opts(best.nb, 0, best.panel_ctas, 2, update))) != LU_OK) break;
         // tensor-core updates: leave some SMs to the panel chain (a smaller RU2 grid)
         if (update != LU_UPDATE_NATIVE &&
             (rc = consider(make_opts(best.nb, 0, best.panel_ctas, best.lookahead, update, 112))) != LU_OK)

@@ -100,7 +100,7 @@ def test_f64emu_schedule_invariance_bits():
     import paper_1611_06365_gb300 as lu
     A = li.uniform(600, 600, seed=19)
     ref, piv_ref, _, _, _ = factor_gpu(A, "f64", update=lu.LU_UPDATE_F64EMU, nb=64, lookahead=-1)
-    for la, ctas in ((1, 8), (1, 2), (-1, 4)):
+    for la, ctas in ((1, 8), (1, 2), (-1, 4), (2, 8), (3, 4)):
         LU, ipiv, _, _, _ = factor_gpu(A, "f64", update=lu.LU_UPDATE_F64EMU, nb=64, lookahead=la, panel_ctas=ctas)
         assert np.array_equal(ipiv, piv_ref) and np.array_equal(LU, ref)
 

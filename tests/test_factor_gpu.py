@@ -154,8 +154,25 @@ def test_f32_tc_update_large_lookahead_invariance(update):
     """The tensor-core path under look-ahead on and off gives identical bits."""
     A = li.uniform(2304, 2304, seed=16)
     ref, pref, _, _, _ = factor_gpu(A, "f32", update=update, lookahead=-1)
-    got, pgot, _, _, _ = factor_gpu(A, "f32", update=update, lookahead=1)
-    assert np.array_equal(pref, pgot) and np.array_equal(ref, got)
+    for depth in (1, 2, 4):
+        got, pgot, _, _, _ = factor_gpu(A, "f32", update=update, lookahead=depth)
+        assert np.array_equal(pref, pgot) and np.array_equal(ref, got), depth
+
+
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_deeper_lookahead_same_bits_and_oracle_pivots(oracle_mod, depth):
+    """Look-ahead of depth d (the panel branch keeps d strips current) reorders
+    the schedule only: the factors are bit-identical to depth 1 and to no
+    look-ahead, and the pivots equal the oracle's; ragged last strips included."""
+    A = li.uniform(1000, 1000, seed=23)
+    ref, piv_ref, _, _, _ = factor_gpu(A, "f64", nb=32, lookahead=-1)
+    got, piv, info, _, _ = factor_gpu(A, "f64", nb=32, lookahead=depth)
+    assert info == 0 and np.array_equal(piv, piv_ref) and np.array_equal(got, ref)
+    oracle_parity(oracle_mod, A, piv)
+    B = li.uniform(777, 777, seed=24)
+    ref, piv_ref, _, _, _ = factor_gpu(B, "f64", nb=48, lookahead=1)
+    got, piv, _, _, _ = factor_gpu(B, "f64", nb=48, lookahead=depth)
+    assert np.array_equal(piv, piv_ref) and np.array_equal(got, ref)
 
 
 def test_empty_matrix():

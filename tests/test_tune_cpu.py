@@ -43,7 +43,8 @@ def test_put_get_clear(L):
     (0, 0, 64, {"update": 1}, -3),                                # tensor-core update on FP64
     (0, 0, -1, {}, -4),                                           # negative order
     (0, 0, 64, {"panel_ctas": 17}, -5),                           # team larger than a cluster
-    (0, 0, 64, {"lookahead": 2}, -5),
+    (0, 0, 64, {"lookahead": 5}, -5),                             # deeper than the deepest look-ahead (4)
+    (0, 1, 64, {"update": 4}, -3),                                # emulated FP64 update on FP32
     (1, 1, 64, {"nb": 8}, -5),                                    # batched widths are 1, 16, 32
 ])
 def test_put_rejects(L, kind, dt, n, kw, code):
@@ -122,7 +123,7 @@ def test_plan_info_follows_table(L):
 
 
 @pytest.mark.parametrize("dt,update,widths", [
-    (0, 0, (0, 16, 32, 64)), (1, 0, (0, 64, 128, 256)), (1, 1, (0, 64, 128, 256)),
+    (0, 0, (0, 16, 32, 64)), (0, 4, (0, 32, 64)), (1, 0, (0, 64, 128, 256)), (1, 1, (0, 64, 128, 256)),
     (1, 2, (0, 64, 128, 256)), (1, 3, (0, 64, 128, 256)),
 ])
 def test_every_tuner_candidate_fits(L, dt, update, widths):
@@ -133,7 +134,7 @@ def test_every_tuner_candidate_fits(L, dt, update, widths):
             if nb > n:
                 continue
             for pc in (0, 8, 4):
-                for la in (0, -1):
+                for la in (0, -1, 2):
                     rc, p = lu.lu_plan_info(dt, n, nb=nb, panel_ctas=pc, lookahead=la, update=update)
                     assert rc == 0, (dt, update, n, nb, pc, la, p)
                     assert p["nb"] == (nb or p["nb"]) and 1 <= p["nb_inner"] <= p["nb"]
