@@ -18,6 +18,11 @@ Functions and the passages they follow:
 * ``backward_error`` normwise Rigal-Gaches backward error; pinned by
               hand-computed cases.
 * ``lu_residual_fro`` / ``lu_residual_probe`` checks of P A = L U.
+* ``potrf`` / ``potrs`` unblocked right-looking Cholesky A = L L^T and its
+              solves (the symmetric positive definite case section 1 names as
+              the next factorization for the same scheme); pinned by a
+              hand-worked 3x3 case, exact dyadic factors, the LU of the same
+              matrix and a brute-force determinant in the tests.
 """
 from __future__ import annotations
 
@@ -64,6 +69,10 @@ def _load():
         lib.oracle_backward_error.restype = d
         lib.oracle_getrf_getrs_batched.argtypes = [i, P(i), P(d), P(ctypes.c_long), P(i),
                                                    P(ctypes.c_long), P(d), P(ctypes.c_long), P(i)]
+        lib.oracle_potrf.argtypes = [i, P(d), i]
+        lib.oracle_potrf.restype = i
+        lib.oracle_potrs.argtypes = [i, i, P(d), i, P(d), i]
+        lib.oracle_potrs.restype = i
         _lib = lib
     return _lib
 
@@ -188,6 +197,29 @@ def getrf_getrs_batched(mats, rhs):
         ipivs.append(piv[voff[t]:voff[t] + n].copy())
         xs.append(Bbuf[voff[t]:voff[t] + n].copy())
     return LUs, ipivs, info[:len(mats)].copy(), xs
+
+
+def potrf(A):
+    """(L, info) of A = L L^T (lower triangle of A used; L's strictly upper part
+    is A's, untouched).  Unblocked right-looking Cholesky."""
+    lib = _load()
+    F = _fortran(A).copy(order="F")
+    n = F.shape[0]
+    info = lib.oracle_potrf(n, _dp(F), max(n, 1))
+    if info < 0:
+        raise ValueError("oracle_potrf: bad argument")
+    return F, info
+
+
+def potrs(L, B):
+    """Solve A X = B with the factor of potrf; B is (n,) or (n, nrhs)."""
+    lib = _load()
+    L = _fortran(L)
+    n = L.shape[0]
+    vec = np.ndim(B) == 1
+    X = _fortran(np.reshape(B, (n, -1))).copy(order="F")
+    lib.oracle_potrs(n, X.shape[1], _dp(L), max(n, 1), _dp(X), max(n, 1))
+    return X[:, 0].copy() if vec else X
 
 
 def unpack(LU):

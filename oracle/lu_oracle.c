@@ -320,3 +320,53 @@ void oracle_getrf_getrs_batched(int count, const int *ns, double *A, const long 
         oracle_getrs(n, 1, A + aoff[t], n, ipiv + poff[t], B + boff[t], n);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Unblocked right-looking Cholesky factorization A = L L^T of a symmetric
+ * positive definite matrix (lower triangle referenced and overwritten; the
+ * strictly upper part is not touched), the factorization the paper names as
+ * the next case for the same scheme (section 1: the ideas carry over to other
+ * dense factorizations).  For each column j:
+ *   l_jj = sqrt(a_jj)                      (a_jj already updated)
+ *   l_ij = a_ij / l_jj,  i > j             (division, not a reciprocal)
+ *   a_ic = a_ic - l_ij * l_cj, j < c <= i  (lower triangle only, two roundings)
+ * Returns 0, or j+1 for the first column whose updated diagonal entry is not
+ * positive (LAPACK potrf's info; the factorization stops there), or -1 for a
+ * bad argument.
+ * ------------------------------------------------------------------------ */
+int oracle_potrf(int n, double *A, int lda)
+{
+    if (n < 0 || lda < (n > 1 ? n : 1)) return -1;
+    for (int j = 0; j < n; ++j) {
+        const double d = AT(A, lda, j, j);
+        if (!(d > 0.0)) return j + 1;
+        const double l = sqrt(d);
+        AT(A, lda, j, j) = l;
+        for (int i = j + 1; i < n; ++i) AT(A, lda, i, j) = AT(A, lda, i, j) / l;
+        for (int c = j + 1; c < n; ++c) {
+            const double lc = AT(A, lda, c, j);
+            for (int i = c; i < n; ++i)
+                AT(A, lda, i, c) = AT(A, lda, i, c) - AT(A, lda, i, j) * lc;
+        }
+    }
+    return 0;
+}
+
+/* Solve A X = B with the Cholesky factor L (lower): L Y = B, then L^T X = Y. */
+int oracle_potrs(int n, int nrhs, const double *L, int lda, double *B, int ldb)
+{
+    if (n < 0 || nrhs < 0 || lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1)) return -1;
+    for (int r = 0; r < nrhs; ++r) {
+        double *b = B + (size_t)r * (size_t)ldb;
+        for (int j = 0; j < n; ++j) {                     /* L y = b */
+            b[j] = b[j] / AT(L, lda, j, j);
+            for (int i = j + 1; i < n; ++i) b[i] = b[i] - AT(L, lda, i, j) * b[j];
+        }
+        for (int j = n - 1; j >= 0; --j) {                /* L^T x = y */
+            double s = b[j];
+            for (int i = j + 1; i < n; ++i) s = s - AT(L, lda, i, j) * b[i];
+            b[j] = s / AT(L, lda, j, j);
+        }
+    }
+    return 0;
+}

@@ -331,3 +331,71 @@ def test_forcing_the_searched_pivots_changes_nothing(oracle_mod):
     bad[5] = 3
     with pytest.raises(ValueError):
         oracle_mod.getrf(A, forced=bad)
+
+
+# --------------------------------------------------------------------------
+# Cholesky (the symmetric positive definite case, A = L L^T)
+# --------------------------------------------------------------------------
+
+def _dyadic_spd(n, seed):
+    """L lower with diagonal entries in {1, 2, 4} and off-diagonal k/8 (|k| <= 7):
+    A = L L^T and every step of the elimination are exact in FP64."""
+    h = li.splitmix64(seed, np.arange(n * n + n, dtype=np.uint64))
+    k = (h[:n * n] % np.uint64(15)).astype(np.int64).reshape(n, n) - 7
+    L = np.tril(k.astype(np.float64) / 8.0, -1)
+    L[np.arange(n), np.arange(n)] = 2.0 ** (h[n * n:] % np.uint64(3)).astype(np.float64)
+    return L @ L.T, L
+
+
+def test_cholesky_3x3_hand_worked(oracle_mod):
+    g = _read_golden("chol3x3.txt")
+    A = np.array([[float(x) for x in r] for r in g["A"]])
+    L, info = oracle_mod.potrf(A)
+    assert info == 0
+    Lx = np.array([[float(x) for x in r] for r in g["L"]])
+    assert np.array_equal(np.tril(L), Lx)                 # every value here is exact
+    assert np.array_equal(np.triu(L, 1), np.triu(A, 1))   # the upper part is not touched
+    assert np.prod(np.diag(L)) ** 2 == float(g["det"][0][0])
+
+
+@pytest.mark.parametrize("n", [1, 5, 33, 150])
+def test_cholesky_dyadic_exact(oracle_mod, n):
+    A, L = _dyadic_spd(n, seed=600 + n)
+    Lo, info = oracle_mod.potrf(A)
+    assert info == 0 and np.array_equal(np.tril(Lo), L)
+    # and the solve: x integer, b = A x exact
+    x = (li.splitmix64(n, np.arange(n, dtype=np.uint64)) % np.uint64(9)).astype(np.float64) - 4.0
+    assert np.array_equal(oracle_mod.potrs(Lo, A @ x), x)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_cholesky_brute_force_determinant(oracle_mod, seed):
+    n = 3 + seed
+    h = li.splitmix64(7000 + seed, np.arange(n * n, dtype=np.uint64))
+    M = ((h % np.uint64(11)).astype(np.int64) - 5).reshape(n, n)
+    Ai = M @ M.T + n * np.eye(n, dtype=np.int64)             # symmetric positive definite, integer
+    L, info = oracle_mod.potrf(Ai.astype(float))
+    assert info == 0
+    det = float(leibniz_det(Ai.tolist()))
+    assert abs(np.prod(np.diag(L)) ** 2 - det) <= 1e-10 * det
+
+
+def test_cholesky_agrees_with_lu_without_interchanges(oracle_mod):
+    """A column diagonally dominant SPD matrix has no interchanges under partial
+    pivoting, and then L_chol = L_lu diag(u_jj)^(1/2)."""
+    n = 120
+    B = li.uniform(n, n, seed=41)
+    A = (B + B.T) / 2 + 2 * n * np.eye(n)
+    LU, ipiv, info = oracle_mod.getrf(A)
+    assert np.array_equal(ipiv, np.arange(1, n + 1))
+    Llu, Ulu = oracle_mod.unpack(LU)
+    L, info = oracle_mod.potrf(A)
+    assert info == 0
+    assert np.max(np.abs(np.tril(L) - Llu * np.sqrt(np.diag(Ulu))[None, :])) <= 1e-12 * np.max(np.abs(L))
+
+
+def test_cholesky_not_positive_definite(oracle_mod):
+    L, info = oracle_mod.potrf(np.array([[1.0, 2.0], [2.0, 1.0]]))     # a22 - l21^2 = 1 - 4 < 0
+    assert info == 2
+    L, info = oracle_mod.potrf(np.array([[0.0, 0.0], [0.0, 1.0]]))
+    assert info == 1
