@@ -740,14 +740,14 @@ def measure_peaks(dev):
     import paper_1611_06365_gb300 as lu
 
     out = {"gpu": torch.cuda.get_device_name(dev), "how": "lu_peak_probe: 4 CTAs x 256 threads per SM, "
-           "the compute loop of the tiled update (4 x 4 outputs per thread, operands from shared memory), "
-           "4 DMMA chains per warp; "
+           "DFMA: the compute loop of the tiled update (4 x 4 outputs per thread, operands from shared memory); "
+           "FFMA: 8 register chains per thread; DMMA: 4 chains per warp; "
            "CUDA events around one launch"}
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
     for name, kind, iters in (("dfma", lu.PROBE_DFMA, 1 << 15), ("dmma", lu.PROBE_DMMA, 1 << 19),
-                              ("ffma", lu.PROBE_FFMA, 1 << 19)):
+                              ("ffma", lu.PROBE_FFMA, 1 << 23)):
         lu.lu_peak_probe(kind, iters // 64)
         tf, ms = lu.lu_peak_probe(kind, iters)
         out[name] = {"tflops": tf, "ms": ms, "iters": iters}
@@ -842,6 +842,24 @@ def run_case(args):
     elif args.case == "peaks":
         print(json.dumps(measure_peaks(dev)), flush=True)
         return
+    elif args.case == "emu_update":
+        # the emulated FP64 update alone: C 8192 x 8192 FP64 (512 MiB, larger than L2), K = 64
+        m = n = 8192
+        A = li.uniform_colmajor_torch(m, 64, 1, dev, torch.float64)
+        B = li.uniform_colmajor_torch(64, n, 2, dev, torch.float64)
+        C = li.uniform_colmajor_torch(m, n, 3, dev, torch.float64)
+        for _ in range(2):
+            lu.lu_trailing_update_f64(lu.LU_UPDATE_F64EMU, A, B, C, m, n, 64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lu.lu_trailing_update_f64(lu.LU_UPDATE_F64EMU, A, B, C, m, n, 64)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"case": "emu_update", "ms": ms, "fp64_equiv_tflops": 2.0 * m * n * 64 / (ms / 1e3) / 1e12,
+                          "c_gbs": 16.0 * m * n / (ms / 1e3) / 1e9}), flush=True)
+        return
     elif args.case == "probe_dfma":
         # one short DFMA probe launch (for a counter capture of the FP64 pipe)
         tf, ms = lu.lu_peak_probe(lu.PROBE_DFMA, 1 << 11)
@@ -900,7 +918,8 @@ def make_parser():
     ap.add_argument("--tune-file", dest="tune_file", default=None,
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
-                                       "fp8_large", "solve_f32", "torch_context", "peaks", "c3_grid", "probe_dfma"],
+                                       "fp8_large", "solve_f32", "torch_context", "peaks", "c3_grid", "probe_dfma",
+                                       "emu_update"],
                     default=None,
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")

@@ -241,6 +241,31 @@ int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const double *dB,
                    void *stream);
 
 /*
+ * lu_cholesky -- A = L L^T of a symmetric positive definite n x n matrix, in
+ * place (lower triangle read and overwritten; the strictly upper part is not
+ * touched).  The factorization section 1 of the paper names as the next case
+ * for the scheme, run on the same look-ahead schedule as lu_factor: per panel
+ * of b_o <= 64 columns, the diagonal block and L21 := A21 L11^{-T} in one
+ * kernel, then A22 -= L21 L21^T (lower triangle only) split into the next
+ * strip (panel branch) and the rest (remainder branch).
+ *   dt      LU_F64 or LU_F32.      dA, lda  as lu_factor.
+ *   d_info  device int (output): 0, or j > 0 when the updated diagonal entry
+ *           of column j (1-based) is not positive (the first such j; the
+ *           factors past it are meaningless, as in LAPACK's potrf).
+ *   opts    NULL or: nb (b_o, 1..64; 0 = 64), lookahead (-1: none), update
+ *           (LU_UPDATE_NATIVE, or LU_UPDATE_F64EMU with LU_F64), spin_ns.
+ */
+int lu_cholesky(lu_dtype dt, int n, void *dA, int lda, int *d_info, const lu_opts *opts, void *stream);
+
+/*
+ * lu_cholesky_solve -- X := A^{-1} B with the factor of lu_cholesky: L Y = B,
+ * L^T X = Y, through the substitutions of lu_solve applied to the unit lower
+ * factor L diag(L)^{-1} and the upper factor diag(L) L^T (formed in a
+ * stream-ordered n x n workspace).  dB device n x nrhs (ldb), overwritten.
+ */
+int lu_cholesky_solve(lu_dtype dt, int n, int nrhs, const void *dL, int lda, void *dB, int ldb, void *stream);
+
+/*
  * lu_trailing_update -- the trailing update step alone (RL3 / RU2 of the
  * paper): C := C - A * B with C m x n FP32 column-major (ldc), A m x k and
  * B k x n.  `update` selects LU_UPDATE_BF16 (operands rounded to BF16,
@@ -448,9 +473,10 @@ long long lu_div_selftest(lu_dtype dt, long long count, unsigned long long seed,
  *   kind 0: FP64 fused multiply-adds on the CUDA cores (DFMA);
  *        1: FP32 fused multiply-adds (FFMA);
  *        2: mma.sync m8n8k4 with FP64 operands (DMMA).
- *   iters: outer steps (FMA kinds: the compute loop of the tiled update, 16
- *   steps of a 4 x 4 outer product per thread with operands from shared
- *   memory; DMMA: 4 chained mma.sync per warp; 4 CTAs of 256 threads per SM).  Launches one kernel
+ *   iters: outer steps (DFMA: the compute loop of the tiled update, 16 steps
+ *   of a 4 x 4 outer product per thread with operands from shared memory;
+ *   FFMA: 8 independent register chains per thread; DMMA: 4 chained mma.sync
+ *   per warp; 4 CTAs of 256 threads per SM).  Launches one kernel
  *   on `stream`, times it with CUDA events and synchronizes.  *tflops (host)
  *   receives flops / time / 1e12, *ms the kernel time; either may be NULL.
  *   Returns 0, -1 (bad kind), -2 (iters <= 0) or LU_ERR_CUDA.

@@ -21,7 +21,7 @@ from . import build as _build_mod
 
 __all__ = [
     "LU_OK", "LU_F64", "LU_F32", "LU_UPDATE_NATIVE", "LU_UPDATE_BF16", "LU_UPDATE_BF16X3", "LU_UPDATE_FP8",
-    "LU_UPDATE_F64EMU", "LuError", "lib", "build", "lu_trailing_update_f64",
+    "LU_UPDATE_F64EMU", "LuError", "lib", "build", "lu_trailing_update_f64", "lu_cholesky", "lu_cholesky_solve",
     "lu_factor", "lu_solve", "lu_solve_noalloc", "lu_solve_noalloc_capacity", "lu_factor_batched", "lu_solve_batched", "lu_solve_mixed",
     "lu_trailing_update", "lu_workspace_size", "lu_status_string", "lu_last_device_status", "lu_get_status",
     "lu_version", "lu_update_timing", "lu_update_timing_read", "lu_trace", "lu_trace_read", "lu_wait_selftest", "lu_div_selftest", "lu_kernel_launches",
@@ -98,6 +98,10 @@ def lib():
         L.lu_trailing_update.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp]
         L.lu_trailing_update_f64.argtypes = [i, i, i, i, vp, i, vp, i, vp, i, vp]
         L.lu_trailing_update_f64.restype = i
+        L.lu_cholesky.argtypes = [i, i, vp, i, ip, ctypes.POINTER(LuOpts), vp]
+        L.lu_cholesky.restype = i
+        L.lu_cholesky_solve.argtypes = [i, i, i, vp, i, vp, i, vp]
+        L.lu_cholesky_solve.restype = i
         L.lu_workspace_size.argtypes = [ctypes.c_char_p, i, i, i]
         L.lu_workspace_size.restype = ctypes.c_size_t
         L.lu_status_string.argtypes = [i]
@@ -199,6 +203,22 @@ def lu_factor(A, ipiv, info, n=None, *, nb=0, nb_inner=0, panel_ctas=0, lookahea
     o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns, update_ctas)
     return _check("lu_factor", lib().lu_factor(_dtype_code(A), n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
                                                 ctypes.byref(o), _stream(stream)))
+
+
+def lu_cholesky(A, info, n=None, *, nb=0, lookahead=0, update=LU_UPDATE_NATIVE, spin_ns=0, stream=None):
+    """A = L L^T in place (lower triangle) of a symmetric positive definite column-major (n, lda) tensor."""
+    n, lda = _cm_dims(A, n)
+    o = LuOpts(nb, 0, 0, lookahead, update, spin_ns, 0)
+    return _check("lu_cholesky", lib().lu_cholesky(_dtype_code(A), n, _ptr(A), lda, _ptr(info), ctypes.byref(o),
+                                                    _stream(stream)))
+
+
+def lu_cholesky_solve(L, B, n=None, nrhs=None, *, stream=None):
+    """B := A^{-1} B with the factor of lu_cholesky.  B: column-major (nrhs, ldb)."""
+    n, lda = _cm_dims(L, n)
+    nrhs = B.shape[0] if nrhs is None else nrhs
+    return _check("lu_cholesky_solve", lib().lu_cholesky_solve(_dtype_code(L), n, nrhs, _ptr(L), lda, _ptr(B), _ld(B),
+                                                                _stream(stream)))
 
 
 def lu_solve(LU, ipiv, B, n=None, nrhs=None, *, stream=None):

@@ -53,7 +53,7 @@ cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c
 // gemm_simt.cu
 template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s,
-                             CtaTrace tr = CtaTrace{});
+                             CtaTrace tr = CtaTrace{}, bool transb = false, int lshift = -1);
 // gemm_tc.cu
 cudaError_t make_stage_maps(CUtensorMap *mapA, const void *stageA, int rowsA, CUtensorMap *mapB, const void *stageB,
                             int colsB, int kinner, int lds, int fp8);
@@ -77,7 +77,8 @@ bool tc_c_aligned(const float *C, int ldc);
 // gemm_f64emu.cu
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr = CtaTrace{});
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr = CtaTrace{},
+                               int lshift = -1);
 cudaError_t launch_stage_rows_f64emu(int rows, int k, const double *L, int ld, __nv_bfloat16 *stage, int lds, double *scale,
                                      cudaStream_t s);
 cudaError_t launch_stage_cols_f64emu(int k, int cols, const double *B, int ld, __nv_bfloat16 *stage, int lds, double *scale,
@@ -1091,8 +1092,10 @@ const char *lu_version(void) { return "liblu 0.1 (sm_103a; cluster panel, tcgen0
 
 }  // extern "C"
 
-// internal entry points used by the mixed-precision driver (mixed_api.cu)
+// internal entry points used by the mixed-precision driver (mixed_api.cu) and
+// the Cholesky factorization (cholesky.cu)
 namespace lu {
+CtaTrace cta_tag_ext(int kind, int step) { return cta_tag(kind, step); }
 int factor_f32_internal(int n, float *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s) {
     lu_opts tuned;
     o = with_tuned(0, LU_F32, n, o, &tuned);

@@ -16,9 +16,11 @@
 // pair (s + t >= 7) is at most 2^-58 per k, all of them together below
 // 2^-49.4, and the sixth accumulator's rounding below 2^-50.7 (worst cases;
 // a K-term DFMA chain may round by K^2 2^-53 = 2^-41 of the same units).
-// The epilogue adds the six accumulators in FP64 (smallest first), applies the
-// two power-of-two scales (exact) and subtracts from C: one FP64 rounding per
-// element, against K for a DFMA chain.  The scales are per row and column,
+// The epilogue adds the six accumulators exactly in a 64-bit integer (units of
+// 2^-56 of the scales' product; the shared accumulator rounded to that unit),
+// converts it to FP64 (one rounding) and subtracts it from C with one fused
+// multiply-add by the two power-of-two scales: two roundings per element,
+// against K for a DFMA chain, and three FP64-pipe operations per element.  The scales are per row and column,
 // so a row whose entries differ widely in magnitude keeps the absolute, not
 // the relative, accuracy of its largest entry (the normwise property of the
 // splitting).
@@ -33,8 +35,8 @@
 //            tcgen05.mma kind::f16 (M = 128, N = 32, K = 16) into one of two
 //            sets of six TMEM accumulators (2 x 6 x 32 columns);
 //   warps 2-9 epilogue: load the sub-tile's C while the MMAs run, read the
-//            accumulators (tcgen05.ld), combine in FP64, store C (two warps
-//            per TMEM lane quarter, 16 columns each).
+//            accumulators (tcgen05.ld), combine them in integer arithmetic,
+//            store C (two warps per TMEM lane quarter, 16 columns each).
 // Every wait is bounded; on expiry the kernel records LU_ERR_TIMEOUT, gives
 // its copies in flight one bounded wait, frees its TMEM and returns.
 #include "common.cuh"
@@ -60,7 +62,7 @@ constexpr int kEmLast = 1 << 16;               // sub-tile flag: last of its tas
 __global__ void __launch_bounds__(kEmThreads, 1)
 gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a_row0,
                    const __grid_constant__ CUtensorMap mapB, int b_col0, double *__restrict__ C, int ldc,
-                   const double *__restrict__ scaleA, const double *__restrict__ scaleB, int nsub,
+                   const double *__restrict__ scaleA, const double *__restrict__ scaleB, int nsub, int lshift,
                    int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns, CtaTrace tr) {
     const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -118,10 +120,19 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             for (;;) {
                 int t = atomicAdd(tile_ctr, 1);
                 if (t >= ntasks || *abort_flag) t = -1;
+                int nj = 0, tm = 0, tn = 0;
+                while (t >= 0) {
+                    tm = (t % mt) * kEmBM;
+                    tn = (t / mt) * cols_task;
+                    nj = min(nsub, (n - tn + kEmBN - 1) / kEmBN);
+                    // lower-triangle updates: only the sub-tiles reaching the kept triangle
+                    if (lshift >= 0) nj = min(nj, tm + kEmBM - 1 - lshift - tn < 0 ? 0 : (tm + kEmBM - 1 - lshift - tn) / kEmBN + 1);
+                    if (nj > 0) break;
+                    t = atomicAdd(tile_ctr, 1);
+                    if (t >= ntasks || *abort_flag) t = -1;
+                }
                 if (t >= 0) {
                     *ntasks_done = *ntasks_done + 1;
-                    const int tm = (t % mt) * kEmBM, tn = (t / mt) * cols_task;
-                    const int nj = min(nsub, (n - tn + kEmBN - 1) / kEmBN);
                     // the previous task's MMAs must be done with the A slices
                     if (!mbar_wait_bounded(a_empty, aph ^ 1u, bound_ns)) { *abort_flag = 1; t = -1; }
                     else {
@@ -230,29 +241,43 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             double *crow = C + (size_t)(rok ? row : 0);
 #pragma unroll
             for (int c = 0; c < 16; ++c) cv[c] = (rok && col0 + c < n) ? crow[(size_t)(col0 + c) * ldc] : 0.0;
-            const double sa = rok ? scaleA[a_row0 + row] : 0.0;
+            // the row's scale times 2^-56, the unit of the integer sum below
+            const double sa56 = rok ? scaleA[a_row0 + row] * 0x1p-56 : 0.0;
             if (!mbar_wait_bounded(accf0 + 8u * a, acc_ph, bound_ns) || *abort_flag) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t accb = tmem + (uint32_t)(a * kEmAcc * kEmBN + h * 16) + ((uint32_t)(q * 32) << 16);
-            // the six accumulators summed in FP64, smallest first
-            double v[16];
+            // The six accumulators combined exactly in a 64-bit integer in units of 2^-56
+            // (on the integer and FP32 pipes; GB300's FP64 pipe is narrow): diagonal g <= 4
+            // holds an integer multiple of 2^{-8(g+2)} below 2^24 of those units, so
+            // acc_g * 2^{8(g+2)} converts exactly and scales by 2^{40-8g}; the shared sixth
+            // accumulator is rounded to the unit (at most 2^-57 of the scales' product).
+            // |sum| < 2^63; one conversion to FP64 and one FMA then give C - A B.
+            long long vi[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) v[c] = 0.0;
+            for (int c = 0; c < 16; ++c) vi[c] = 0;
 #pragma unroll
-            for (int g = kEmAcc - 1; g >= 0; --g) {
+            for (int g = 0; g < kEmAcc; ++g) {
                 float f[16];
                 tmem_ld16(accb + (uint32_t)(g * kEmBN), f);
+                if (g < kEmAcc - 1) {
+                    const float up = __int_as_float((127 + 8 * (g + 2)) << 23);   // 2^{8(g+2)}
+                    const long long mul = 1LL << (40 - 8 * g);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) v[c] += (double)f[c];
+                    for (int c = 0; c < 16; ++c) vi[c] += (long long)__float2int_rz(f[c] * up) * mul;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) vi[c] += __float2ll_rn(f[c] * 0x1p56f);
+                }
             }
 #pragma unroll
-            for (int c = 0; c < 16; ++c) cv[c] -= (sa * __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])) * v[c];
+            for (int c = 0; c < 16; ++c)
+                cv[c] = fma(-(sa56 * __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])), __ll2double_rn(vi[c]), cv[c]);
             // accumulators read: the MMAs of the sub-tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8u * a) : "memory");
 #pragma unroll
             for (int c = 0; c < 16; ++c)
-                if (rok && col0 + c < n) crow[(size_t)(col0 + c) * ldc] = cv[c];
+                if (rok && col0 + c < n && (lshift < 0 || row >= col0 + c + lshift)) crow[(size_t)(col0 + c) * ldc] = cv[c];
         }
     }
     __syncthreads();
@@ -318,9 +343,12 @@ int f64emu_box_cols() { return kEmBN; }
 // digit slices behind the maps (boxes 64 x 128 for A, 64 x 32 for B over
 // staging buffers of 7 * 64 elements per row/column) and their scales
 // scaleA[a_row0 + i], scaleB[b_col0 + j].  C: FP64, any alignment.
+// lshift >= 0: only the elements (i, j) with i >= j + lshift are written and
+// sub-tiles wholly above that diagonal are skipped (the symmetric update of
+// the Cholesky factorization, where B is L21^T staged like A).
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr) {
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     static int sms = 0;
     if (!sms) {
@@ -344,7 +372,7 @@ cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0
     cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
     if (ez != cudaSuccess) return ez;
     gemm_update_f64emu<<<grid, kEmThreads, kEmSmem, s>>>(m, n, mapA, a_row0, mapB, b_col0, C, ldc, scaleA, scaleB, nsub,
-                                                          tile_ctr, status, bound_ns, tr);
+                                                          lshift, tile_ctr, status, bound_ns, tr);
     lu_count_launch();
     return cudaGetLastError();
 }

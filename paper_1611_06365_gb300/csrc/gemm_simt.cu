@@ -13,22 +13,29 @@
 // look-ahead strip of a small matrix) spreads over four times as many SMs.
 // Every element accumulates its k products in increasing k and is then
 // subtracted from C, whatever the tile.  All matrices column-major.
+//
+// The Cholesky factorization uses the same kernel for its symmetric update
+// A22 -= L21 L21^T: B is then read transposed (TB: element (k, j) at
+// B[j + k ldb]) and only the lower triangle is written (lshift >= 0: element
+// (i, j) of C is kept when i >= j + lshift, and tiles wholly above that
+// diagonal return at once).
 #include "common.cuh"
 
 namespace lu {
 
 constexpr int kGK = 16;
 
-template <typename T, int TM, int TN>
+template <typename T, int TM, int TN, bool TB>
 __global__ void __launch_bounds__((TM / 4) * (TN / 4))
 gemm_update_simt(int m, int n, int k, const T *__restrict__ A, int lda, const T *__restrict__ B, int ldb,
-                 T *__restrict__ C, int ldc, CtaTrace tr) {
+                 T *__restrict__ C, int ldc, int lshift, CtaTrace tr) {
     const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr int TX = TM / 4, TY = TN / 4, NT = TX * TY;
     __shared__ T As[kGK][TM];       // As[kk][row]
     __shared__ T Bs[kGK][TN + 1];   // Bs[kk][col]
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int row0 = blockIdx.x * TM, col0 = blockIdx.y * TN;
+    if (lshift >= 0 && row0 + TM - 1 < col0 + lshift) return;   // wholly above the kept triangle
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -42,11 +49,11 @@ gemm_update_simt(int m, int n, int k, const T *__restrict__ A, int lda, const T 
             const int gr = row0 + r, gk = k0 + kk;
             As[kk][r] = (gr < m && gk < k) ? A[(size_t)gr + (size_t)gk * lda] : T(0);
         }
-        // B tile: 16 k x TN cols (coalesced down k)
+        // B tile: 16 k x TN cols (coalesced down k, or along the columns when transposed)
         for (int e = threadIdx.x; e < TN * kGK; e += NT) {
-            const int kk = e % kGK, c = e / kGK;
+            const int kk = TB ? e / TN : e % kGK, c = TB ? e % TN : e / kGK;
             const int gc = col0 + c, gk = k0 + kk;
-            Bs[kk][c] = (gc < n && gk < k) ? B[(size_t)gk + (size_t)gc * ldb] : T(0);
+            Bs[kk][c] = (gc < n && gk < k) ? (TB ? B[(size_t)gc + (size_t)gk * ldb] : B[(size_t)gk + (size_t)gc * ldb]) : T(0);
         }
         __syncthreads();
 #pragma unroll
@@ -70,7 +77,7 @@ gemm_update_simt(int m, int n, int k, const T *__restrict__ A, int lda, const T 
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int gr = row0 + tx + TX * i;
-            if (gr < m) {
+            if (gr < m && (lshift < 0 || gr >= gc + lshift)) {
                 T *c = &C[(size_t)gr + (size_t)gc * ldc];
                 *c = *c - acc[i][j];
             }
@@ -81,7 +88,7 @@ gemm_update_simt(int m, int n, int k, const T *__restrict__ A, int lda, const T 
 
 template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc,
-                             cudaStream_t s, CtaTrace tr) {
+                             cudaStream_t s, CtaTrace tr, bool transb, int lshift) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
     static int sms = 0;
     if (!sms) {
@@ -94,18 +101,24 @@ cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *
     if (big >= sms) {
         dim3 grid(lu_ceil_div(m, 64), lu_ceil_div(n, 64));
         if (grid.y > 65535) return cudaErrorInvalidValue;
-        gemm_update_simt<T, 64, 64><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, tr);
+        if (transb)
+            gemm_update_simt<T, 64, 64, true><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, lshift, tr);
+        else
+            gemm_update_simt<T, 64, 64, false><<<grid, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, lshift, tr);
     } else {
         dim3 grid(lu_ceil_div(m, 32), lu_ceil_div(n, 32));
-        gemm_update_simt<T, 32, 32><<<grid, 64, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, tr);
+        if (transb)
+            gemm_update_simt<T, 32, 32, true><<<grid, 64, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, lshift, tr);
+        else
+            gemm_update_simt<T, 32, 32, false><<<grid, 64, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, lshift, tr);
     }
     lu_count_launch();
     return cudaGetLastError();
 }
 
 template cudaError_t launch_gemm_simt<double>(int, int, int, const double *, int, const double *, int, double *, int, cudaStream_t,
-                                              CtaTrace);
+                                              CtaTrace, bool, int);
 template cudaError_t launch_gemm_simt<float>(int, int, int, const float *, int, const float *, int, float *, int, cudaStream_t,
-                                             CtaTrace);
+                                             CtaTrace, bool, int);
 
 }  // namespace lu

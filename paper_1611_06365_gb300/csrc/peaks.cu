@@ -7,10 +7,11 @@
 //   kind 2  DMMA: mma.sync m8n8k4 with FP64 operands (the legacy FP64 tensor
 //           path; tcgen05 has no FP64 kind)
 //
-// The FMA probes run the compute loop of the tiled update (a 4 x 4 outer
+// The DFMA probe runs the compute loop of the tiled update (a 4 x 4 outer
 // product per thread per step of K, operands from shared memory, 16
-// independent accumulators); every DMMA warp runs 4 chains; the grid holds
-// kCtasPerSm CTAs of 256 threads per SM.  The accumulators grow linearly from
+// independent accumulators), the FFMA probe 8 independent register chains per
+// thread, and every DMMA warp 4 chains; the grid holds kCtasPerSm CTAs of 256
+// threads per SM.  The accumulators grow linearly from
 // small positive products, so nothing overflows or goes subnormal, and a
 // data-dependent store keeps the compiler from removing the work.
 #include "common.cuh"
@@ -60,6 +61,24 @@ __global__ void __launch_bounds__(kProbeThreads) fma_probe(long long iters, T m,
     if (s == T(-1)) sink[blockIdx.x] = s;   // never true: every term is positive
 }
 
+// Independent FMA chains (8 per thread) on operands held in registers: the
+// pattern that reaches the FP32 pipe's rate (the tile loop above is bound by
+// its shared-memory operand loads in FP32, not in FP64).
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) fma_chains(long long iters, T m, T c, T *sink) {
+    T a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = T(threadIdx.x + i) * T(1e-3);
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = fma(a[i], m, c);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += a[i];
+    if (s == T(-1)) sink[blockIdx.x] = s;   // never true: the chains stay positive
+}
+
 __global__ void __launch_bounds__(kProbeThreads) dmma_probe(long long iters, double m, double *sink) {
     double d[4][2];
     const double a = m, b = 1.0 - 1e-3 * (threadIdx.x & 7);
@@ -102,8 +121,8 @@ extern "C" int lu_peak_probe(int kind, long long iters, double *tflops, double *
         lu::fma_probe<double><<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.999, 1e-3, static_cast<double *>(sink));
         flops = threads * (double)iters * 16 * 16 * 2.0;
     } else if (kind == 1) {
-        lu::fma_probe<float><<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.999f, 1e-3f, static_cast<float *>(sink));
-        flops = threads * (double)iters * 16 * 16 * 2.0;
+        lu::fma_chains<float><<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.999f, 1e-3f, static_cast<float *>(sink));
+        flops = threads * (double)iters * 8 * 2.0;
     } else {
         lu::dmma_probe<<<grid, lu::kProbeThreads, 0, s>>>(iters, 0.5, static_cast<double *>(sink));
         flops = threads / 32.0 * (double)iters * 4.0 * (2.0 * 8 * 8 * 4);

@@ -50,8 +50,10 @@ def _well_formed(ev, nsteps):
     assert sorted({e["step"] for e in ev if e["kind"] == "panel"}) == list(range(nsteps))
 
 
-@pytest.mark.parametrize("dtype,update,n,nb", [("f64", 0, 2048, 32), ("f32", 2, 4096, 64), ("f64", 4, 4096, 64)])
+@pytest.mark.parametrize("dtype,update,n,nb", [("f64", 0, 2048, 32), ("f32", 2, 16384, 64), ("f64", 4, 8192, 64)])
 def test_panel_sms_join_the_remainder_update(dtype, update, n, nb):
+    """Worker sharing needs a remainder update that outlasts the panel: the early
+    steps of these orders (RU2 of step k is the larger task there)."""
     ev = _trace(n, dtype, nb=nb, update=update)
     _well_formed(ev, (n + nb - 1) // nb)
     shared = _sharing(ev)
