@@ -650,7 +650,8 @@ def time_to_solution(args, dev):
             # attainable bound of the factorization: the split-BF16 products (three per pair) at
             # the sustained BF16 rate, or the FP32 trailing matrix streamed once per panel
             bound_ms = max(3 * flops_lu(n) / (bf16_peak * 1e12), (8.0 / 3.0) * n ** 3 / plan_bo / (hbm_peak * 1e9)) * 1e3
-            entry = {"kappa": kappa, "nrhs": nrhs, "rung": rep.rung, "iterations": rep.iterations,
+            entry = {"kappa": kappa, "nrhs": nrhs, "rung": rep.rung, "f32_refactor": rep.f32_refactor,
+                     "iterations": rep.iterations,
                      "gmres_iters": rep.gmres_iters, "fell_back": rep.fell_back, "eta": eta,
                      "forward_error": fwd, "forward_error_est": getattr(rep, "forward_error_est", None),
                      "mixed_ms": rep.t_total_ms, "mixed_wall_ms": wall * 1e3, "factor_ms": rep.t_factor_ms,

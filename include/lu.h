@@ -207,6 +207,9 @@ typedef struct {
     int fallback_native; /* FP64 factorization of rung 2 (and of fp64_factor): 0 = with the
                             emulated FP64 update (LU_UPDATE_F64EMU), 1 = with the plain
                             DFMA update (LU_UPDATE_NATIVE) */
+    int f32_refactor;    /* 0: when classic refinement stalls on the factors of a tensor-core
+                            update, refactor once with the FP32 update and refine on before
+                            GMRES-IR; -1: never */
 } lu_mixed_opts;
 
 /* Result of lu_solve_mixed (host memory, filled before the call returns). */
@@ -221,8 +224,11 @@ typedef struct {
     double t_refine_ms;  /* device time of refinement (and fallback) */
     double t_total_ms;   /* device time of the whole call */
     double forward_error_est;  /* estimate of max_q ||x_q - x*_q||_inf / ||x_q||_inf: the size of
-                            the last refinement correction relative to the solution (Demmel et
-                            al., ACM TOMS 32(2), 2006); INFINITY if no correction was made */
+                            one more refinement correction relative to the solution, with the
+                            factors of the rung that finished (Demmel et al., ACM TOMS 32(2),
+                            2006) */
+    int f32_refactor;    /* 1 if the FP32 factorization with the FP32 update was made after
+                            classic refinement stalled on the tensor-core update's factors */
 } lu_mixed_report;
 
 /*

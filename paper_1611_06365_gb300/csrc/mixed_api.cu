@@ -4,6 +4,9 @@
 //
 // Ladder, in order, each rung entered only when the previous one stalls:
 //   0  classic refinement: x += U^{-1} L^{-1} P r with r = b - A x in FP64;
+//      if it stalls on the factors of a tensor-core update (BF16, split BF16,
+//      FP8), the matrix is refactored once with the FP32 update and refined
+//      on from the current x (report.f32_refactor = 1);
 //   1  GMRES-IR (Carson and Higham, SIAM J. Sci. Comput. 39(6), 2017), here
 //      in its flexible form: the correction equation A d = r is solved by
 //      FGMRES (Saad, SIAM J. Sci. Comput. 14(2), 1993) with the FP32 factors
@@ -208,21 +211,45 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     int *perm64 = nullptr;
     std::vector<double> hist;
     bool done = false;
-    if (hinfo == 0 && !fp64_only) {
+    // classic refinement with the FP32 factors in A32, from the current X and R
+    auto classic = [&]() -> int {
+        hist.clear();
         for (int it = 0; it < max_iter; ++it) {
             LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
-            rc = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
-            if (rc != LU_OK) return rc;
+            int rc2 = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
+            if (rc2 != LU_OK) return rc2;
             LU_CUDA_TRY(launch_axpy_scaled(n, nrhs, R32, n, d_rmax, dX, ldx, s));
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
             LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
-            rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
-            if (rc != LU_OK) return rc;
+            rc2 = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+            if (rc2 != LU_OK) return rc2;
             r.iterations++;
             hist.push_back(eta);
             if (eta <= tol) { done = true; break; }
             const size_t h = hist.size();
             if (h >= 3 && !(hist[h - 1] <= 0.5 * hist[h - 3])) break;   // stalled
+        }
+        return LU_OK;
+    };
+    if (hinfo == 0 && !fp64_only) {
+        rc = classic();
+        if (rc != LU_OK) return rc;
+    }
+    // rung 0, second part: factors of the tensor-core update too coarse for this
+    // matrix (refinement stalled) -- refactor with the FP32 update (FP32-accurate
+    // factors) and refine on from the current solution
+    if (!done && !fp64_only && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0)) {
+        r.f32_refactor = 1;
+        LU_CUDA_TRY(launch_cast_rowsum(n, dA, lda, A32, ld32, rowsum, s));
+        lu_opts fo2 = {};
+        fo2.update = LU_UPDATE_NATIVE;
+        rc = factor_f32_internal(n, A32, ld32, ipiv, info, perm, &fo2, s);
+        if (rc != LU_OK) return rc;
+        LU_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LU_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hinfo == 0) {
+            rc = classic();
+            if (rc != LU_OK) return rc;
         }
     }
     // rung 1: GMRES-IR with the FP32 factors as preconditioner

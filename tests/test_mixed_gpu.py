@@ -195,6 +195,22 @@ def test_mixed_fp8_update(oracle_mod, kind, rung_max):
     assert eta <= 1e-14 and rep.rung <= rung_max, (rep.as_dict(), eta)
 
 
+def test_mixed_refactors_in_fp32_when_the_tensor_core_factors_stall(oracle_mod):
+    """Plain BF16 factors (8 significant bits) of a kappa = 1e5 matrix stall
+    classic refinement; the ladder refactors once with the FP32 update and
+    converges on rung 0 without GMRES-IR or the FP64 factorization."""
+    import paper_1611_06365_gb300 as lu
+    n = 1200
+    A = li.kappa_matrix(n, 1e5, seed=li.BASE_SEED + 2300, k=n)
+    B = A @ np.ones((n, 1))
+    X, rep = _mixed(A, B, update=lu.LU_UPDATE_BF16)
+    assert oracle_mod.backward_error(A, X, B) <= 1e-14
+    assert rep.f32_refactor == 1 and rep.rung == 0 and rep.fell_back == 0, rep.as_dict()
+    X2, rep2 = _mixed(A, B, update=lu.LU_UPDATE_BF16, f32_refactor=-1)   # without it: a later rung
+    assert oracle_mod.backward_error(A, X2, B) <= 1e-14
+    assert rep2.f32_refactor == 0 and rep2.rung >= 1
+
+
 def test_mixed_kappa_1e12_falls_back(oracle_mod):
     n = 400
     A = li.kappa_matrix(n, 1e12, seed=li.BASE_SEED + 2200, k=n)
