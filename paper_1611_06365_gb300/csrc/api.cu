@@ -577,7 +577,6 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
             LU_CUDA_TRY(cudaEventRecord(st->evPF2, P));
             LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P,
                                [&] { return factor_outer_panel<T>(c, cn0, wn, sl1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
-            LU_CUDA_TRY(cudaEventRecord(st->evP[sl1], P));
             // depth >= 2: strips k+2 .. k+depth after the panel, off its chain; the last of
             // them was in RU2(k-1)'s range
             const int s0 = cn0 + wn;
@@ -588,6 +587,10 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
                 LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P,
                                    [&] { return update<T>(c, sl, kb, w, s0, rest0, P, cta_tag(LU_TRACE_PF2, k)); }));
             }
+            // the remainder branch of step k+1 starts after this branch's step k: its first
+            // task applies panel k+1's interchanges to the columns left of it, rows of
+            // L21(k) included, which the strip updates above read
+            LU_CUDA_TRY(cudaEventRecord(st->evP[sl1], P));
             LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evPF2, 0));
         }
         // ---- T_RU on U, second part: RU2 ----------------------------------------------

@@ -241,8 +241,11 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             double *crow = C + (size_t)(rok ? row : 0);
 #pragma unroll
             for (int c = 0; c < 16; ++c) cv[c] = (rok && col0 + c < n) ? crow[(size_t)(col0 + c) * ldc] : 0.0;
-            // the row's scale times 2^-56, the unit of the integer sum below
-            const double sa56 = rok ? scaleA[a_row0 + row] * 0x1p-56 : 0.0;
+            // the row's scale 2^{e_i}, as its biased exponent (the scales are powers of two,
+            // so the product with the column's scale and the unit 2^-56 of the integer sum
+            // below is formed by adding exponents, off the FP64 pipe)
+            const double sa = rok ? scaleA[a_row0 + row] : 0.0;
+            const long long ea = (__double_as_longlong(sa) >> 52) & 0x7ff;
             if (!mbar_wait_bounded(accf0 + 8u * a, acc_ph, bound_ns) || *abort_flag) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t accb = tmem + (uint32_t)(a * kEmAcc * kEmBN + h * 16) + ((uint32_t)(q * 32) << 16);
@@ -270,8 +273,16 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                cv[c] = fma(-(sa56 * __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])), __ll2double_rn(vi[c]), cv[c]);
+            for (int c = 0; c < 16; ++c) {
+                const double sb = __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)]);
+                const long long es = ea + ((__double_as_longlong(sb) >> 52) & 0x7ff) - 1023 - 56;
+                // 2^{e_i + e_j - 56} from the exponents while it is a normal number; the warp
+                // takes the multiplication path only when one of its lanes needs it
+                double sc;
+                if (__all_sync(0xffffffffu, !rok || (ea > 0 && es >= 1 && es <= 2046))) sc = __longlong_as_double(es << 52);
+                else sc = sa * sb * 0x1p-56;
+                cv[c] = fma(-sc, __ll2double_rn(vi[c]), cv[c]);
+            }
             // accumulators read: the MMAs of the sub-tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8u * a) : "memory");

@@ -41,6 +41,24 @@ def _sharing(ev):
     return steps
 
 
+def _timeline(ev, steps):
+    """Per early step: panel(k+1) interval, RU2(k) first start / last end (us from
+    the first record), and how many RU2(k) CTAs started after the panel ended."""
+    t00 = min(e["t0"] for e in ev)
+    out = []
+    for k in range(steps):
+        p = [e for e in ev if e["kind"] == "panel" and e["step"] == k + 1]
+        r = [e for e in ev if e["kind"] == "ru2" and e["step"] == k]
+        if not p or not r:
+            continue
+        pend = max(e["t1"] for e in p)
+        late = [e for e in r if e["t0"] >= pend]
+        out.append((k, (min(e["t0"] for e in p) - t00) / 1e3, (pend - t00) / 1e3,
+                    (min(e["t0"] for e in r) - t00) / 1e3, (max(e["t1"] for e in r) - t00) / 1e3,
+                    len(r), len(late), sum(e["tiles"] for e in late)))
+    return out
+
+
 def _well_formed(ev, nsteps):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -57,7 +75,7 @@ def test_panel_sms_join_the_remainder_update(dtype, update, n, nb):
     ev = _trace(n, dtype, nb=nb, update=update)
     _well_formed(ev, (n + nb - 1) // nb)
     shared = _sharing(ev)
-    assert len(shared) >= 1, "no step shows a panel SM taking update tiles afterwards"
+    assert len(shared) >= 1, ("no step shows a panel SM taking update tiles afterwards", _timeline(ev, 4))
 
 
 def test_trace_off_records_nothing():
