@@ -101,9 +101,15 @@ typedef struct {
                           -1: plain blocked RL without look-ahead */
     int update;        /* LU_UPDATE_*: BF16 .. FP8 with LU_F32, F64EMU with LU_F64 */
     long long spin_ns; /* bound for device-side waits in ns (0 = 2 s) */
-    int update_ctas;   /* LU_F32 tensor-core updates: persistent CTAs of the remainder
-                          update RU2 (section 3.2's split of the threads between the panel
-                          and the update); 0 = one per SM */
+    int update_ctas;   /* tensor-core updates (LU_F32 BF16 .. FP8, LU_F64 F64EMU): persistent
+                          CTAs of the remainder update RU2 (section 3.2's split of the threads
+                          between the panel and the update); 0 = one per SM */
+    int sm_share;      /* tensor-core updates with look-ahead: 0 (default) or 1 = worker
+                          sharing (section 4.1) between the panel and the persistent RU2:
+                          RU2's CTAs on the SMs of one panel-cluster placement stop taking
+                          tiles while panel k+1 waits for them, and a grid of as many CTAs
+                          joins RU2's tile queue when the panel ends; -1 = off (RU2 keeps
+                          its SMs until its queue is empty) */
 } lu_opts;
 
 /*

@@ -43,8 +43,11 @@ namespace lu {
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
-                               cudaStream_t s, CtaTrace tr);
+                               cudaStream_t s, CtaTrace tr, int *yreq);
 int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo);
+int panel_cluster_ctas(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_cap);
+cudaError_t launch_cluster_sm_probe(int C, unsigned *mask, cudaStream_t s);
+cudaError_t launch_share_raise(int *req, cudaStream_t s);
 bool panel_fits(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_cap);
 // swap_trsm.cu
 template <typename T>
@@ -62,7 +65,8 @@ int tc_box_cols();
 cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8);
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                            int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
-                           const float *scaleA, const float *scaleB, int max_ctas = 0, CtaTrace tr = CtaTrace{});
+                           const float *scaleA, const float *scaleB, int max_ctas = 0, CtaTrace tr = CtaTrace{},
+                           SmShare sh = SmShare{});
 cudaError_t launch_stage_rows_fp8(int rows, int k, int kpad, const float *L, int ld, unsigned char *stage, int lds,
                                   float *scale, cudaStream_t s);
 cudaError_t launch_stage_cols_fp8(int k, int kpad, int cols, const float *B, int ld, unsigned char *stage, int lds,
@@ -78,7 +82,7 @@ bool tc_c_aligned(const float *C, int ldc);
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
                                long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr = CtaTrace{},
-                               int lshift = -1);
+                               int lshift = -1, SmShare sh = SmShare{});
 cudaError_t launch_stage_rows_f64emu(int rows, int k, const double *L, int ld, __nv_bfloat16 *stage, int lds, double *scale,
                                      cudaStream_t s);
 cudaError_t launch_stage_cols_f64emu(int k, int cols, const double *B, int ld, __nv_bfloat16 *stage, int lds, double *scale,
@@ -140,12 +144,19 @@ constexpr size_t kPanelSmemCap = 200 * 1024;
 constexpr int kMaxDepth = 4;              // deepest look-ahead (lu_opts.lookahead)
 constexpr int kRing = kMaxDepth + 1;      // panels whose row maps / staging may be in use at once
 
+constexpr int kMaskWords = kShareMaskBits / 32 + 1;   // SM bits, then an overflow word
+
 struct DevState {
     bool init = false;
     cudaStream_t P = nullptr, U = nullptr;
+    cudaStream_t J = nullptr;   // joining grids of the remainder update (worker sharing)
     cudaEvent_t evP[kRing] = {}, evU[kRing] = {};
     cudaEvent_t evIn = nullptr, evOutP = nullptr, evOutU = nullptr, evPF2 = nullptr;
+    cudaEvent_t evPanelEnd = nullptr, evGo = nullptr, evJ = nullptr;
     int *status = nullptr;   // device status word
+    int *share_req = nullptr;        // SmShare request word
+    unsigned *share_mask = nullptr;  // [17][kMaskWords]: SMs of one cluster placement of C CTAs
+    signed char share_state[17] = {};   // per C: 0 not probed, 1 probed, -1 probe refused
     int sms = 0;
 };
 
@@ -166,6 +177,7 @@ cudaError_t dev_state(DevState **out) {
         if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return e;
         if ((e = cudaStreamCreateWithPriority(&st.P, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
         if ((e = cudaStreamCreateWithPriority(&st.U, cudaStreamNonBlocking, lo)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithPriority(&st.J, cudaStreamNonBlocking, lo)) != cudaSuccess) return e;
         for (int i = 0; i < kRing; ++i) {
             if ((e = cudaEventCreateWithFlags(&st.evP[i], cudaEventDisableTiming)) != cudaSuccess) return e;
             if ((e = cudaEventCreateWithFlags(&st.evU[i], cudaEventDisableTiming)) != cudaSuccess) return e;
@@ -174,8 +186,15 @@ cudaError_t dev_state(DevState **out) {
         if ((e = cudaEventCreateWithFlags(&st.evOutP, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&st.evOutU, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&st.evPF2, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&st.evPanelEnd, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&st.evGo, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&st.evJ, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&st.status, sizeof(int))) != cudaSuccess) return e;
         if ((e = cudaMemset(st.status, 0, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&st.share_req, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMemset(st.share_req, 0, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&st.share_mask, 17 * kMaskWords * sizeof(unsigned))) != cudaSuccess) return e;
+        if ((e = cudaMemset(st.share_mask, 0, 17 * kMaskWords * sizeof(unsigned))) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, d)) != cudaSuccess) return e;
         st.init = true;
     }
@@ -306,6 +325,7 @@ struct Plan {
     int depth = 1;    // look-ahead depth d: strips k+1 .. k+d on the panel branch (0: none)
     int panel_ctas = 16;
     int update_ctas = 0;   // persistent CTAs of the remainder update (0: one per SM)
+    bool share = true;     // worker sharing with the persistent tensor-core update (SmShare)
     long long bound = 2000000000LL;
 };
 
@@ -346,6 +366,7 @@ Plan make_plan(int n, const lu_opts *o) {
     // the geometry takes more CTAs when the rows do not fit 8
     p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : (sizeof(T) == 8 ? 8 : 16);
     p.update_ctas = (o && o->update_ctas > 0) ? o->update_ctas : 0;
+    p.share = !(o && o->sm_share < 0);
     p.bound = lu_spin_bound_ns(o);
     return p;
 }
@@ -389,21 +410,24 @@ struct FactorCtx {
 };
 
 template <typename T>
-cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr);
+cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr,
+                          SmShare sh);
 
 // C[rows r0.., cols c0..c1) -= L(rows r0.., cols kb..kb+w) * U(rows kb..kb+w, cols c0..c1)
+// sh: worker sharing of a persistent tensor-core update (SmShare; ignored by the SIMT update)
 template <typename T>
-cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr) {
+cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr,
+                   SmShare sh = SmShare{}) {
     const int r0 = kb + w;
     const int m = c.n - r0, nn = c1 - c0;
     if (m <= 0 || nn <= 0) return cudaSuccess;
-    if (!timing_on()) return update_launch<T>(c, k_par, kb, w, c0, c1, s, tr);
+    if (!timing_on() || sh.mode == 1) return update_launch<T>(c, k_par, kb, w, c0, c1, s, tr, sh);
     TimedLaunch t;
     cudaError_t e;
     if ((e = cudaEventCreate(&t.a)) != cudaSuccess) return e;
     if ((e = cudaEventCreate(&t.b)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t.a, s)) != cudaSuccess) return e;
-    if ((e = update_launch<T>(c, k_par, kb, w, c0, c1, s, tr)) != cudaSuccess) return e;
+    if ((e = update_launch<T>(c, k_par, kb, w, c0, c1, s, tr, sh)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(t.b, s)) != cudaSuccess) return e;
     const int k = c.pl.tc ? c.kinner : w;   // staged operand width (hi and lo halves with the split)
     const double opw = c.pl.tc ? (c.pl.fmt == 2 ? 1.0 : 2.0) : (double)sizeof(T);
@@ -415,21 +439,24 @@ cudaError_t update(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cu
 }
 
 template <typename T>
-cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr) {
+cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int c1, cudaStream_t s, CtaTrace tr,
+                          SmShare sh) {
     const int r0 = kb + w;
     const int m = c.n - r0, nn = c1 - c0;
+    // task counters: [0] the panel branch's updates, [1] the remainder update and its joiners
+    const bool ru = s != c.st->P;
     if constexpr (sizeof(T) == 8) {
         if (c.pl.tc)
             return launch_gemm_f64emu(m, nn, c.mapA[k_par], 0, c.mapB, c0 - r0, reinterpret_cast<double *>(c.A) + r0 + (size_t)c0 * c.lda,
-                                      c.lda, c.dscA[k_par], c.dscB, c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status,
-                                      c.pl.bound, s == c.st->P ? 0 : c.pl.update_ctas, s, tr);
+                                      c.lda, c.dscA[k_par], c.dscB, c.tile_ctr + (ru ? 1 : 0), c.st->status,
+                                      c.pl.bound, ru ? c.pl.update_ctas : 0, s, tr, -1, sh);
     }
     if constexpr (sizeof(T) == 4) {
         if (c.pl.tc)
             return launch_gemm_tc(c.pl.fmt == 1 ? 3 : (c.pl.fmt == 2 ? 8 : 1), m, nn, c.kpad, c.mapA[k_par], 0, c.mapB,
                                   c0 - r0, reinterpret_cast<float *>(c.A) + r0 + (size_t)c0 * c.lda, c.lda,
-                                  c.tile_ctr + (s == c.st->P ? 0 : 1), c.st->status, c.pl.bound, s, c.scA[k_par], c.scB,
-                                  s == c.st->P ? 0 : c.pl.update_ctas, tr);
+                                  c.tile_ctr + (ru ? 1 : 0), c.st->status, c.pl.bound, s, c.scA[k_par], c.scB,
+                                  ru ? c.pl.update_ctas : 0, tr, sh);
     }
     return launch_gemm_simt<T>(m, nn, w, c.A + r0 + (size_t)kb * c.lda, c.lda, c.A + kb + (size_t)c0 * c.lda, c.lda,
                                c.A + r0 + (size_t)c0 * c.lda, c.lda, s, tr);
@@ -464,13 +491,34 @@ bool plan_fits(const Plan &pl, int n, size_t elem) {
 // Factor outer panel at column kb (width w) on stream s: one cluster launch
 // that also leaves the row map in maps[par], updates perm and stages L21.
 template <typename T>
-cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s, CtaTrace tr) {
+cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s, CtaTrace tr, int *yreq = nullptr) {
     StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt, nullptr};
     if (c.pl.tc && kb + w < c.n) { sd.ptr = c.stA[par]; sd.scale = c.scA[par]; sd.dscale = c.dscA[par]; }
     return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, plan_inner_width(c.pl, c.n, sizeof(T), kb, w),
                                  c.ipiv + kb, kb,
                                  c.info, c.maps[par], c.perm, sd, c.pl.panel_ctas, kPanelSmemCap, c.st->status,
-                                 c.pl.bound, s, tr);
+                                 c.pl.bound, s, tr, yreq);
+}
+
+// The SMs of one placement of a C-CTA panel cluster (SmShare), found by a probe
+// cluster on stream s the first time C is asked for; nullptr where the probe
+// launch was refused.
+const unsigned *share_mask_for(DevState *st, int C, cudaStream_t s) {
+    if (C < 1 || C > 16 || st->sms > (int)kShareMaskBits) return nullptr;
+    unsigned *mask = st->share_mask + (size_t)C * kMaskWords;
+    if (st->share_state[C] == 0) {
+        st->share_state[C] = -1;
+        if (cudaMemsetAsync(mask, 0, kMaskWords * sizeof(unsigned), s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (launch_cluster_sm_probe(C, mask, s) != cudaSuccess) {
+            cudaGetLastError();   // cluster size refused: no sharing at this size
+            return nullptr;
+        }
+        st->share_state[C] = 1;
+    }
+    return st->share_state[C] > 0 ? mask : nullptr;
 }
 
 template <typename T>
@@ -555,6 +603,15 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
         const int *map = c.maps[sl];
         // look-ahead window: strips k+1 .. k+depth on the panel branch, the rest on RU
         const int rest0 = std::min(n, cn0 + depth * bo);
+        // worker sharing with a persistent remainder update (SmShare): the SMs of one
+        // placement of panel k+1's cluster
+        const unsigned *smask = nullptr;
+        int cctas = 0;
+        if (pl.tc && pl.share && depth > 0 && wn > 0 && rest0 < n) {
+            cctas = panel_cluster_ctas(n - cn0, sizeof(T), wn, plan_inner_width(pl, n, sizeof(T), cn0, wn), pl.panel_ctas,
+                                       kPanelSmemCap);
+            smask = share_mask_for(st, cctas, P);
+        }
         // ---- T_RU on U, first part: interchanges left of panel k, RU1 ------------
         LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evP[sl], 0));
         if (kb > 0)
@@ -575,8 +632,14 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
             // priority) is dispatched first, and RU2's queued CTAs fill the
             // rest of the GPU and later the SMs the panel cluster frees
             LU_CUDA_TRY(cudaEventRecord(st->evPF2, P));
-            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P,
-                               [&] { return factor_outer_panel<T>(c, cn0, wn, sl1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
+            // with a persistent RU2 that may already hold every SM: ask one cluster
+            // placement back; the panel withdraws the request once it runs
+            if (smask) LU_CUDA_TRY(launch_share_raise(st->share_req, P));
+            LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P, [&] {
+                return factor_outer_panel<T>(c, cn0, wn, sl1, P, cta_tag(LU_TRACE_PANEL, k + 1),
+                                             smask ? st->share_req : nullptr);
+            }));
+            if (smask) LU_CUDA_TRY(cudaEventRecord(st->evPanelEnd, P));
             // depth >= 2: strips k+2 .. k+depth after the panel, off its chain; the last of
             // them was in RU2(k-1)'s range
             const int s0 = cn0 + wn;
@@ -594,9 +657,25 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
             LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evPF2, 0));
         }
         // ---- T_RU on U, second part: RU2 ----------------------------------------------
-        if (rest0 < n)
+        if (rest0 < n && smask) {
+            // RU2's CTAs on the requested SMs stop at a task boundary while the request
+            // stands; a grid of the panel's size joins RU2's task queue on J when the
+            // panel ends (the PF team joining RU2, section 4.1), and RU2 counts as done
+            // when both have drained the queue
+            LU_CUDA_TRY(cudaMemsetAsync(c.tile_ctr + 1, 0, sizeof(int), U));
+            LU_CUDA_TRY(cudaEventRecord(st->evGo, U));
+            const SmShare sh{st->share_req, smask, 2, 0};
+            LU_CUDA_TRY(traced(LU_TRACE_RU2, k, 1, U,
+                               [&] { return update<T>(c, sl, kb, w, rest0, n, U, cta_tag(LU_TRACE_RU2, k), sh); }));
+            LU_CUDA_TRY(cudaStreamWaitEvent(st->J, st->evPanelEnd, 0));
+            LU_CUDA_TRY(cudaStreamWaitEvent(st->J, st->evGo, 0));
+            LU_CUDA_TRY(update<T>(c, sl, kb, w, rest0, n, st->J, cta_tag(LU_TRACE_RU2, k), SmShare{nullptr, nullptr, 1, cctas}));
+            LU_CUDA_TRY(cudaEventRecord(st->evJ, st->J));
+            LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evJ, 0));
+        } else if (rest0 < n) {
             LU_CUDA_TRY(traced(LU_TRACE_RU2, k, 1, U,
                                [&] { return update<T>(c, sl, kb, w, rest0, n, U, cta_tag(LU_TRACE_RU2, k)); }));
+        }
         LU_CUDA_TRY(cudaEventRecord(st->evU[sl], U));
         if (wn > 0 && depth == 0) {
             LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[sl], 0));
@@ -645,6 +724,7 @@ extern "C" {
 static bool opts_valid(lu_dtype dt, const lu_opts *opts) {
     if (!opts) return true;
     if (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 || opts->update_ctas < 0 ||
+        opts->sm_share < -1 || opts->sm_share > 1 ||
         (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
          opts->update != LU_UPDATE_FP8 && opts->update != LU_UPDATE_F64EMU))
         return false;
@@ -671,6 +751,7 @@ int lu_plan_info(lu_dtype dt, int n, const lu_opts *opts, lu_opts *plan) {
     plan->update = opts ? opts->update : LU_UPDATE_NATIVE;
     plan->spin_ns = p.bound;
     plan->update_ctas = p.update_ctas;
+    plan->sm_share = p.share ? 1 : -1;
     return plan_fits(p, n, elem) ? LU_OK : LU_ERR_UNSUPPORTED;
 }
 

@@ -33,7 +33,7 @@ cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *
                              CtaTrace tr, bool transb, int lshift);
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift);
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift, SmShare sh);
 cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8);
 int f64emu_kpad();
 int f64emu_box_rows();
@@ -112,10 +112,10 @@ chol_panel(T *__restrict__ A, int lda, int m, int w, int kb_abs, int *__restrict
         if constexpr (sizeof(T) == 8) {
             if (sd.ptr && sd.fmt == 3) {
                 // digit slices of the row for the emulated FP64 update (stage row i - w)
-                double amax = 0.0;
+                unsigned long long amax = 0;
 #pragma unroll
-                for (int c = 0; c < kChW; ++c) amax = fmax(amax, c < w ? fabs(x[c]) : 0.0);
-                const int ex = lu_f64_scale_exp(amax);
+                for (int c = 0; c < kChW; ++c) amax = max(amax, c < w ? lu_f64_abs_bits(x[c]) : 0ull);
+                const int ex = lu_f64_scale_exp_bits(amax);
                 sd.dscale[i - w] = ldexp(1.0, ex);
                 __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(sd.ptr) + (size_t)(i - w) * sd.lds;
                 // the row just stored, read back (cached) so the slicing is not unrolled over the tile
@@ -233,7 +233,7 @@ cudaError_t chol_update(ChCtx<T> &c, int par, int kb, int w, int c0, int c1, int
         if (c.emu)
             return launch_gemm_f64emu(m, nn, c.mapA[par], c0 - r0, c.mapB[par], c0 - r0,
                                       reinterpret_cast<double *>(c.A) + c0 + (size_t)c0 * c.lda, c.lda, c.sc[par], c.sc[par],
-                                      c.ctr + ctr_slot, lu_device_status_ptr(), c.bound, 0, s, tr, 0);
+                                      c.ctr + ctr_slot, lu_device_status_ptr(), c.bound, 0, s, tr, 0, SmShare{});
     }
     const T *L21 = c.A + c0 + (size_t)kb * c.lda;
     return launch_gemm_simt<T>(m, nn, w, L21, c.lda, L21, c.lda, c.A + c0 + (size_t)c0 * c.lda, c.lda, s, tr, true, 0);

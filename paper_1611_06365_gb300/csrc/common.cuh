@@ -103,6 +103,31 @@ __device__ __forceinline__ void lu_trace_cta(const CtaTrace &tr, unsigned long l
     }
 }
 
+// Worker sharing between the panel branch and a persistent remainder update
+// (section 4.1, malleable BLAS).  A persistent update holds one CTA per SM
+// until its task queue is empty, so a panel cluster that reaches the GPU after
+// it would wait for the whole update.  Before such a panel the panel branch
+// raises *req; update CTAs on the SMs in mask (one cluster placement of the
+// panel's size, found by lu_probe_cluster_sms) then stop taking tasks, which
+// lets the cluster in; the panel clears *req when it starts, and a joining
+// grid launched after the panel (mode 1) hands its SMs back to the queue.
+//   mode 0: the launcher resets the task counter; 1: a joining grid of
+//   join_ctas CTAs on a running update's counter; 2: the caller has reset it.
+constexpr unsigned kShareMaskBits = 256;   // SM ids (%smid) a mask covers
+
+struct SmShare {
+    const int *req;
+    const unsigned *mask;   // bit s % 32 of mask[s / 32]: SM s (kShareMaskBits bits)
+    int mode;
+    int join_ctas;
+};
+
+__device__ __forceinline__ bool lu_share_yield(const int *req, const unsigned *mask) {
+    if (!req || !*reinterpret_cast<const volatile int *>(req)) return false;
+    const unsigned s = lu_smid();
+    return s < kShareMaskBits && ((mask[s >> 5] >> (s & 31u)) & 1u);
+}
+
 template <typename T> struct lu_abs_t;
 template <> struct lu_abs_t<double> { __device__ static double f(double x) { return fabs(x); } };
 template <> struct lu_abs_t<float>  { __device__ static float f(float x) { return fabsf(x); } };
@@ -140,32 +165,65 @@ struct StageDesc {
 // multiplication and its applications", Numer. Algorithms 59, 2012): an FP64
 // row (or column) v with |v_k| < 2^e is written as
 //   v_k = 2^e * sum_{s=0..6} x_{k,s} 2^{-8(s+1)} + r_k,  |r_k| <= 2^{e-57},
-// with integer digits |x_{k,0}| <= 256, |x_{k,s}| <= 128 (s >= 1), each taken
-// by rounding the running remainder times 2^8 to the nearest integer (exact
-// in FP64).  Digit s is stored pre-scaled, x_{k,s} 2^{-8(s+1)}: at most 8
-// significant bits, so exact in BF16, and the product of digits s and t lands
-// at its natural scale 2^{-8(s+t+2)}.
+// with integer digits |x_{k,0}| <= 256, |x_{k,s}| <= 128 (s >= 1): the
+// balanced base-256 digits of N_k = round(v_k 2^{56-e}), taken from the
+// least significant end.  Digit s is stored pre-scaled, x_{k,s} 2^{-8(s+1)}:
+// at most 8 significant bits, so exact in BF16, and the product of digits s
+// and t lands at its natural scale 2^{-8(s+t+2)}.  The digits come from the
+// bit fields of v with integer arithmetic (GB300's FP64 pipe is narrow).
 constexpr int kF64Slices = 7;
 
-// Exponent e of the scale 2^e of a row or column whose largest magnitude is
-// amax (|v| < 2^e); 0 for amax = 0.
-__device__ __forceinline__ int lu_f64_scale_exp(double amax) {
-    int e = 0;
-    frexp(amax, &e);
-    return e;
+// |x| as a bit pattern: non-negative doubles order like their patterns, so a
+// row's largest magnitude is an integer maximum.
+__device__ __forceinline__ unsigned long long lu_f64_abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// The kF64Slices digits of x (|x| < 2^e) into out[s * stride], s = 0..6.
+// Exponent e of the scale 2^e of a row or column whose largest magnitude has
+// pattern a: the least e with amax < 2^e (frexp's exponent), from the exponent
+// field, or a subnormal's bit length; 0 for zero.  A row holding an infinity
+// or a NaN gets e = 1025, so its scale 2^e is infinite and every result the
+// row (or column) takes part in becomes infinite or NaN, as with FP64 FMAs,
+// instead of losing the non-finite digits in the integer sums.
+__device__ __forceinline__ int lu_f64_scale_exp_bits(unsigned long long a) {
+    const int E = (int)(a >> 52);
+    if (E == 0x7ff) return 1025;
+    if (E) return E - 1022;
+    const unsigned long long M = a & 0xfffffffffffffull;
+    return M ? 64 - __clzll((long long)M) - 1074 : 0;
+}
+
+// The kF64Slices digits of x (|x| < 2^e) into out[s * stride], s = 0..6; a
+// NaN or infinite x gives NaN digits.
 template <typename BF>
 __device__ __forceinline__ void lu_f64_slices(double x, int e, BF *out, size_t stride) {
-    double r = ldexp(x, -e);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7ffu);
+    if (E == 0x7ff) {
 #pragma unroll
-    for (int s = 0; s < kF64Slices; ++s) {
-        const double t = r * 256.0;
-        const double d = rint(t);
-        r = t - d;
-        out[(size_t)s * stride] = __double2bfloat16(ldexp(d, -8 * (s + 1)));
+        for (int s = 0; s < kF64Slices; ++s) out[(size_t)s * stride] = __float2bfloat16_rn(__int_as_float(0x7fc00000));
+        return;
     }
+    unsigned long long M = b & 0xfffffffffffffull;
+    if (E) M |= 1ull << 52;
+    // |x| = M 2^{max(E,1) - 1075}, so N = round(|x| 2^{56-e}) = round(M 2^sh)
+    const int sh = (E ? E : 1) - 1075 + 56 - e;
+    long long N;
+    if (M == 0 || sh <= -64) N = 0;
+    else if (sh >= 0) N = sh < 64 ? (long long)(M << sh) : 0;              // M 2^sh < 2^56 as |x| < 2^e
+    else N = (long long)((M + (1ull << (-sh - 1))) >> -sh);                // round half up
+    if (b >> 63) N = -N;
+    int d[kF64Slices];
+#pragma unroll
+    for (int s = kF64Slices - 1; s > 0; --s) {
+        const int r = (int)((N + 128) & 255) - 128;   // balanced digit in [-128, 127]
+        d[s] = r;
+        N = (N - r) >> 8;                              // exact: N - r is a multiple of 256
+    }
+    d[0] = (int)N;                                     // |d0| <= 256
+#pragma unroll
+    for (int s = 0; s < kF64Slices; ++s)
+        out[(size_t)s * stride] = __float2bfloat16_rn((float)d[s] * __int_as_float((127 - 8 * (s + 1)) << 23));
 }
 
 // Power-of-two scaling into the e4m3 range: the multiplier 2^e with the

@@ -20,7 +20,8 @@
 // 2^-56 of the scales' product; the shared accumulator rounded to that unit),
 // converts it to FP64 (one rounding) and subtracts it from C with one fused
 // multiply-add by the two power-of-two scales: two roundings per element,
-// against K for a DFMA chain, and three FP64-pipe operations per element.  The scales are per row and column,
+// against K for a DFMA chain, and three FP64-pipe operations per element.
+// The scales are per row and column,
 // so a row whose entries differ widely in magnitude keeps the absolute, not
 // the relative, accuracy of its largest entry (the normwise property of the
 // splitting).
@@ -63,7 +64,8 @@ __global__ void __launch_bounds__(kEmThreads, 1)
 gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a_row0,
                    const __grid_constant__ CUtensorMap mapB, int b_col0, double *__restrict__ C, int ldc,
                    const double *__restrict__ scaleA, const double *__restrict__ scaleB, int nsub, int lshift,
-                   int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns, CtaTrace tr) {
+                   int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns, CtaTrace tr,
+                   const int *__restrict__ yreq, const unsigned *__restrict__ ymask) {
     const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -90,6 +92,16 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
     const int mt = (m + kEmBM - 1) / kEmBM;
     const int cols_task = kEmBN * nsub;
     const int ntasks = mt * ((n + cols_task - 1) / cols_task);
+
+    // a CTA that starts after the queue ran dry (the tail of a joining grid), or on
+    // an SM the panel branch asked back, leaves before claiming TMEM
+    __shared__ int leave;
+    if (tid == 0) leave = *reinterpret_cast<volatile int *>(tile_ctr) >= ntasks || lu_share_yield(yreq, ymask);
+    __syncthreads();
+    if (leave) {
+        if (tid == 0) lu_trace_cta(tr, t_start, 0);
+        return;
+    }
 
     if (tid == 0) {
         mbar_init(a_full, 1);
@@ -118,7 +130,8 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             int sb = 0;
             uint32_t bph = 0, aph = 0;
             for (;;) {
-                int t = atomicAdd(tile_ctr, 1);
+                // worker sharing: on the panel's SMs, stop at a task boundary when asked
+                int t = lu_share_yield(yreq, ymask) ? -1 : atomicAdd(tile_ctr, 1);
                 if (t >= ntasks || *abort_flag) t = -1;
                 int nj = 0, tm = 0, tn = 0;
                 while (t >= 0) {
@@ -241,11 +254,8 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             double *crow = C + (size_t)(rok ? row : 0);
 #pragma unroll
             for (int c = 0; c < 16; ++c) cv[c] = (rok && col0 + c < n) ? crow[(size_t)(col0 + c) * ldc] : 0.0;
-            // the row's scale 2^{e_i}, as its biased exponent (the scales are powers of two,
-            // so the product with the column's scale and the unit 2^-56 of the integer sum
-            // below is formed by adding exponents, off the FP64 pipe)
-            const double sa = rok ? scaleA[a_row0 + row] : 0.0;
-            const long long ea = (__double_as_longlong(sa) >> 52) & 0x7ff;
+            // the row's scale times 2^-56, the unit of the integer sum below
+            const double sa56 = rok ? scaleA[a_row0 + row] * 0x1p-56 : 0.0;
             if (!mbar_wait_bounded(accf0 + 8u * a, acc_ph, bound_ns) || *abort_flag) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t accb = tmem + (uint32_t)(a * kEmAcc * kEmBN + h * 16) + ((uint32_t)(q * 32) << 16);
@@ -273,16 +283,8 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const double sb = __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)]);
-                const long long es = ea + ((__double_as_longlong(sb) >> 52) & 0x7ff) - 1023 - 56;
-                // 2^{e_i + e_j - 56} from the exponents while it is a normal number; the warp
-                // takes the multiplication path only when one of its lanes needs it
-                double sc;
-                if (__all_sync(0xffffffffu, !rok || (ea > 0 && es >= 1 && es <= 2046))) sc = __longlong_as_double(es << 52);
-                else sc = sa * sb * 0x1p-56;
-                cv[c] = fma(-sc, __ll2double_rn(vi[c]), cv[c]);
-            }
+            for (int c = 0; c < 16; ++c)
+                cv[c] = fma(-(sa56 * __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])), __ll2double_rn(vi[c]), cv[c]);
             // accumulators read: the MMAs of the sub-tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8u * a) : "memory");
@@ -317,11 +319,11 @@ __global__ void stage_rows_f64emu(int rows, int k, int kpad, const double *__res
                                   __nv_bfloat16 *__restrict__ stage, int lds, double *__restrict__ scale) {
     const int lane = threadIdx.x & 31;
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < rows; i += gridDim.x * (blockDim.x >> 5)) {
-        double amax = 0.0;
-        for (int kk = lane; kk < k; kk += 32) amax = fmax(amax, fabs(L[(size_t)i + (size_t)kk * ld]));
+        unsigned long long amax = 0;
+        for (int kk = lane; kk < k; kk += 32) amax = max(amax, lu_f64_abs_bits(L[(size_t)i + (size_t)kk * ld]));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        const int e = lu_f64_scale_exp(amax);
+        for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        const int e = lu_f64_scale_exp_bits(amax);
         if (lane == 0) scale[i] = ldexp(1.0, e);
         for (int kk = lane; kk < kpad; kk += 32)
             lu_f64_slices(kk < k ? L[(size_t)i + (size_t)kk * ld] : 0.0, e, stage + (size_t)i * lds + kk, (size_t)kpad);
@@ -333,11 +335,11 @@ __global__ void stage_cols_f64emu(int k, int kpad, int cols, const double *__res
                                   __nv_bfloat16 *__restrict__ stage, int lds, double *__restrict__ scale) {
     const int lane = threadIdx.x & 31;
     for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < cols; j += gridDim.x * (blockDim.x >> 5)) {
-        double amax = 0.0;
-        for (int kk = lane; kk < k; kk += 32) amax = fmax(amax, fabs(B[(size_t)kk + (size_t)j * ld]));
+        unsigned long long amax = 0;
+        for (int kk = lane; kk < k; kk += 32) amax = max(amax, lu_f64_abs_bits(B[(size_t)kk + (size_t)j * ld]));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        const int e = lu_f64_scale_exp(amax);
+        for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        const int e = lu_f64_scale_exp_bits(amax);
         if (lane == 0) scale[j] = ldexp(1.0, e);
         for (int kk = lane; kk < kpad; kk += 32)
             lu_f64_slices(kk < k ? B[(size_t)kk + (size_t)j * ld] : 0.0, e, stage + (size_t)j * lds + kk, (size_t)kpad);
@@ -359,8 +361,9 @@ int f64emu_box_cols() { return kEmBN; }
 // the Cholesky factorization, where B is L21^T staged like A).
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift) {
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift, SmShare sh) {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    if (sh.req && !sh.mask) return cudaErrorInvalidValue;
     static int sms = 0;
     if (!sms) {
         int d = 0;
@@ -379,11 +382,14 @@ cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0
     while (nsub > 1 && mt * lu_ceil_div(n, (long long)kEmBN * nsub) < 2LL * sms) nsub >>= 1;
     const long long ntasks = mt * lu_ceil_div(n, (long long)kEmBN * nsub);
     const int cap = max_ctas > 0 && max_ctas < sms ? max_ctas : sms;
-    const int grid = (int)(ntasks < cap ? ntasks : cap);
-    cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
-    if (ez != cudaSuccess) return ez;
+    int grid = (int)(ntasks < cap ? ntasks : cap);
+    if (sh.mode == 1) grid = sh.join_ctas > 0 ? sh.join_ctas : 1;   // joins a running update: same counter
+    if (sh.mode == 0) {
+        cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
+        if (ez != cudaSuccess) return ez;
+    }
     gemm_update_f64emu<<<grid, kEmThreads, kEmSmem, s>>>(m, n, mapA, a_row0, mapB, b_col0, C, ldc, scaleA, scaleB, nsub,
-                                                          lshift, tile_ctr, status, bound_ns, tr);
+                                                          lshift, tile_ctr, status, bound_ns, tr, sh.req, sh.mask);
     lu_count_launch();
     return cudaGetLastError();
 }

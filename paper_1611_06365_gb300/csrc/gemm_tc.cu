@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, int a_row0,
                const __grid_constant__ CUtensorMap mapB, int b_col0, const __grid_constant__ CUtensorMap mapC,
                int *__restrict__ tile_ctr, int *__restrict__ status, long long bound_ns,
-               const float *__restrict__ scaleA, const float *__restrict__ scaleB, CtaTrace tr) {
+               const float *__restrict__ scaleA, const float *__restrict__ scaleB, CtaTrace tr,
+               const int *__restrict__ yreq, const unsigned *__restrict__ ymask) {
     const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr bool FP8 = NPROD == 8;
     constexpr int BK = FP8 ? kTcBK8 : kTcBK;        // K elements per 128-byte chunk
@@ -84,6 +85,16 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
     const int kpad_off = K;                         // lo halves start at x = K
     const int mt = (m + kTcBM - 1) / kTcBM, ntl = (n + kTcBN - 1) / kTcBN;
     const int ntiles = mt * ntl;
+
+    // a CTA that starts after the queue ran dry (the tail of a joining grid), or on
+    // an SM the panel branch asked back, leaves before claiming TMEM
+    __shared__ int leave;
+    if (tid == 0) leave = *reinterpret_cast<volatile int *>(tile_ctr) >= ntiles || lu_share_yield(yreq, ymask);
+    __syncthreads();
+    if (leave) {
+        if (tid == 0) lu_trace_cta(tr, t_start, 0);
+        return;
+    }
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) { mbar_init(full0 + 8u * i, 1); mbar_init(empty0 + 8u * i, 1); }
@@ -115,7 +126,8 @@ gemm_update_tc(int m, int n, int K, const __grid_constant__ CUtensorMap mapA, in
             int s = 0;
             uint32_t ph = 0, cph = 0;
             for (;;) {
-                int t = atomicAdd(tile_ctr, 1);
+                // worker sharing: on the panel's SMs, stop at a tile boundary when asked
+                int t = lu_share_yield(yreq, ymask) ? -1 : atomicAdd(tile_ctr, 1);
                 if (t >= ntiles || *abort_flag) t = -1;
                 if (t >= 0) *ntiles_done = *ntiles_done + 1;
                 const int tm = t >= 0 ? (t % mt) * kTcBM : 0, tn = t >= 0 ? (t / mt) * kTcBN : 0;
@@ -404,7 +416,8 @@ bool tc_c_aligned(const float *C, int ldc) { return ((uintptr_t)C % 16 == 0) && 
 template <int NPROD>
 static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                                   int b_col0, const CUtensorMap &mapC, int *tile_ctr, int *status, long long bound_ns,
-                                  const float *scaleA, const float *scaleB, cudaStream_t s, const CtaTrace &tr) {
+                                  const float *scaleA, const float *scaleB, cudaStream_t s, const CtaTrace &tr,
+                                  const SmShare &sh) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
@@ -412,7 +425,7 @@ static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorM
         attr = true;
     }
     gemm_update_tc<NPROD><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
-                                                             bound_ns, scaleA, scaleB, tr);
+                                                             bound_ns, scaleA, scaleB, tr, sh.req, sh.mask);
     lu_count_launch();
     return cudaGetLastError();
 }
@@ -423,8 +436,9 @@ static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorM
 // C must be 16-byte aligned with ldc a multiple of 4 (tc_c_aligned).
 cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB,
                            int b_col0, float *C, int ldc, int *tile_ctr, int *status, long long bound_ns, cudaStream_t s,
-                           const float *scaleA, const float *scaleB, int max_ctas, CtaTrace tr) {
+                           const float *scaleA, const float *scaleB, int max_ctas, CtaTrace tr, SmShare sh) {
     if (m <= 0 || n <= 0 || K <= 0) return cudaSuccess;
+    if (sh.req && !sh.mask) return cudaErrorInvalidValue;
     if (nprod != 1 && nprod != 3 && nprod != 8) return cudaErrorInvalidValue;
     const int bk = nprod == 8 ? kTcBK8 : kTcBK;
     if (K > (nprod == 8 ? 2 * kTcMaxK : kTcMaxK) || K % bk != 0) return cudaErrorInvalidValue;
@@ -443,12 +457,15 @@ cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &ma
     const int ntiles = lu_ceil_div(m, kTcBM) * lu_ceil_div(n, kTcBN);
     // persistent CTAs: one per SM, or max_ctas (> 0) to leave SMs to other work
     const int cap = max_ctas > 0 && max_ctas < sms ? max_ctas : sms;
-    const int grid = ntiles < cap ? ntiles : cap;
-    cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
-    if (ez != cudaSuccess) return ez;
-    if (nprod == 1) return launch_tc_mode<1>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s, tr);
-    if (nprod == 3) return launch_tc_mode<3>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s, tr);
-    return launch_tc_mode<8>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, scaleA, scaleB, s, tr);
+    int grid = ntiles < cap ? ntiles : cap;
+    if (sh.mode == 1) grid = sh.join_ctas > 0 ? sh.join_ctas : 1;   // joins a running update: same counter
+    if (sh.mode == 0) {
+        cudaError_t ez = cudaMemsetAsync(tile_ctr, 0, sizeof(int), s);
+        if (ez != cudaSuccess) return ez;
+    }
+    if (nprod == 1) return launch_tc_mode<1>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s, tr, sh);
+    if (nprod == 3) return launch_tc_mode<3>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, nullptr, nullptr, s, tr, sh);
+    return launch_tc_mode<8>(grid, m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status, bound_ns, scaleA, scaleB, s, tr, sh);
 }
 
 cudaError_t launch_stage_rows(int rows, int k, int kpad, const float *L, int ld, __nv_bfloat16 *stage, int lds, int split,

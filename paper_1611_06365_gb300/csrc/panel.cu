@@ -334,7 +334,7 @@ template <typename T, int RPT>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, int *__restrict__ ipiv, int row_base,
                      int *__restrict__ info, int *__restrict__ map_out, int *__restrict__ perm,
-                     StageDesc sd, int *__restrict__ status, long long bound_ns, CtaTrace tr) {
+                     StageDesc sd, int *__restrict__ status, long long bound_ns, CtaTrace tr, int *__restrict__ yreq) {
     const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr int BI = TileWidth<T, RPT>::BI;
     using V = typename Vec16<T>::type;
@@ -346,6 +346,8 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     const int C = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the cluster is in: a persistent update no longer needs to give SMs back
+    if (yreq && rank == 0 && tid == 0) atomicExch(yreq, 0);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PanelLayout<T> lay(bi, bo, C);
@@ -659,13 +661,13 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                 __syncthreads();
                 {
                     const int r = tid >> 4, sub = tid & 15;
-                    double amax = 0.0;
+                    unsigned long long amax = 0;
                     if (r < nrow)
-                        for (int k = sub; k < kmax; k += 16) amax = fmax(amax, fabs(tile[(size_t)r * 64 + k]));
+                        for (int k = sub; k < kmax; k += 16) amax = max(amax, lu_f64_abs_bits(tile[(size_t)r * 64 + k]));
 #pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                    for (int o = 8; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
                     if (sub == 0 && r < nrow) {
-                        const int ex = lu_f64_scale_exp(amax);
+                        const int ex = lu_f64_scale_exp_bits(amax);
                         rexp[r] = ex;
                         sd.dscale[rb + r - kmax] = ldexp(1.0, ex);
                     }
@@ -781,7 +783,7 @@ static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap,
 template <typename T, int RPT>
 static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int bo, int bi, int R, int *ipiv,
                               int row_base, int *info, int *map_out, int *perm, StageDesc sd, int *status, long long bound_ns,
-                              const CtaTrace &tr) {
+                              const CtaTrace &tr, int *yreq) {
     cudaError_t e = cudaFuncSetAttribute(panel_factor_cluster<T, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)cfg.dynamicSmemBytes);
     if (e != cudaSuccess) return e;
@@ -789,7 +791,7 @@ static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int
     if (e != cudaSuccess) return e;
     lu_count_launch();
     return cudaLaunchKernelEx(&cfg, panel_factor_cluster<T, RPT>, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out,
-                              perm, sd, status, bound_ns, tr);
+                              perm, sd, status, bound_ns, tr, yreq);
 }
 
 // Host launcher: factor the m x bo panel at P with inner width bi; pivots into
@@ -797,10 +799,12 @@ static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int
 // NULL); permutation vector update (may be NULL); optional BF16 staging of
 // L21 (stage rows 0.. = panel rows bo.., as described by sd).  A column
 // exchange that waits longer than bound_ns records LU_ERR_TIMEOUT in *status.
+// yreq (may be NULL): the worker-sharing request (SmShare), cleared once the
+// cluster runs.
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
-                               cudaStream_t s, CtaTrace tr) {
+                               cudaStream_t s, CtaTrace tr, int *yreq) {
     if (bi <= 0 || bo <= 0 || bo > kPanelBoMax || m <= 0) return cudaErrorInvalidValue;
     if (bi > bo) bi = bo;
     if (bi > kPanelWMax) return cudaErrorInvalidValue;
@@ -820,10 +824,10 @@ cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     switch (rows_per_thread(R)) {
-        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
-        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
-        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
-        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr);
+        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
+        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
+        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
+        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -850,9 +854,62 @@ bool panel_fits(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_ca
                      : panel_geometry<float>(m, bi, bo, max_ctas, smem_cap, &C, &R, &sm);
 }
 
+// CTAs of the cluster launch_panel_outer makes for these arguments (0: it
+// would refuse them).
+int panel_cluster_ctas(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_cap) {
+    if (bi > bo) bi = bo;
+    int C = 0, R = 0;
+    size_t sm = 0;
+    const bool ok = elem == 8 ? panel_geometry<double>(m, bi, bo, max_ctas, smem_cap, &C, &R, &sm)
+                              : panel_geometry<float>(m, bi, bo, max_ctas, smem_cap, &C, &R, &sm);
+    return ok ? C : 0;
+}
+
+// ---- worker sharing (SmShare) ----------------------------------------------
+
+// One cluster of C CTAs marks the SMs it was placed on: a set of SMs that can
+// hold a panel cluster of that size (clusters stay within one GPC).
+__global__ void cluster_sm_probe(unsigned *mask) {
+    if (threadIdx.x == 0) {
+        const unsigned s = lu_smid();
+        if (s < kShareMaskBits) atomicOr(&mask[s >> 5], 1u << (s & 31u));
+        else atomicOr(&mask[kShareMaskBits / 32], 1u);   // an id the mask cannot hold: sharing stays off
+    }
+}
+
+cudaError_t launch_cluster_sm_probe(int C, unsigned *mask, cudaStream_t s) {
+    if (C < 1 || C > kPanelMaxCtas) return cudaErrorInvalidValue;
+    if (C > 8) {
+        cudaError_t e = cudaFuncSetAttribute(cluster_sm_probe, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(32, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    lu_count_launch();
+    return cudaLaunchKernelEx(&cfg, cluster_sm_probe, mask);
+}
+
+__global__ void share_raise(int *req) { *req = 1; }
+
+// The panel branch asks for its SMs back (runs just before the panel).
+cudaError_t launch_share_raise(int *req, cudaStream_t s) {
+    share_raise<<<1, 1, 0, s>>>(req);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_panel_outer<double>(double *, int, int, int, int, int *, int, int *, int *, int *, StageDesc,
-                                                int, size_t, int *, long long, cudaStream_t, CtaTrace);
+                                                int, size_t, int *, long long, cudaStream_t, CtaTrace, int *);
 template cudaError_t launch_panel_outer<float>(float *, int, int, int, int, int *, int, int *, int *, int *, StageDesc, int,
-                                               size_t, int *, long long, cudaStream_t, CtaTrace);
+                                               size_t, int *, long long, cudaStream_t, CtaTrace, int *);
 
 }  // namespace lu

@@ -115,13 +115,16 @@ __device__ __forceinline__ bool get_tagged(const unsigned long long *w, unsigned
 // of the earlier published blocks straight from global memory (32 columns of
 // loads in flight), and so keeps only a shared-memory product, the diagonal
 // solve (shuffles) and the publication on the block-to-block chain.  NQ is
-// the number of right-hand sides handled per pass (a compile-time bound, so
-// the per-lane arrays stay in registers).  W holds the tagged solution words,
-// row i of right-hand side q at W[(q * n + i) * TagWords].
+// the number of right-hand sides a chain carries (a compile-time bound, so the
+// per-lane arrays stay in registers); the nrhs right-hand sides of a pass form
+// nchains independent chains of NQ, run side by side, so the block-to-block
+// chain stays as short as for one right-hand side.  W holds the tagged
+// solution words, row i of right-hand side q at W[(q * n + i) * TagWords].
 template <typename T, bool LOWER, int NQ>
 __global__ void __launch_bounds__(32 * kTWarps)
-trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ X, int ldx, int *__restrict__ ticket,
-            unsigned long long *__restrict__ W, unsigned tag, int *__restrict__ status, long long bound_ns) {
+trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, int nchains, T *__restrict__ Xall, int ldx,
+            int *__restrict__ ticket, unsigned long long *__restrict__ Wall, unsigned tag, int *__restrict__ status,
+            long long bound_ns) {
     constexpr int TW = TagWords<T>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -132,16 +135,22 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
         int t = 0;
         if (lane == 0) t = atomicAdd(ticket, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= nblk) break;
-        const int I = LOWER ? t : nblk - 1 - t;
+        if (t >= nblk * nchains) break;
+        // tickets interleave the chains, so they advance together and share the
+        // matrix blocks they read through L2
+        const int ch = t % nchains, tt = t / nchains;
+        const int I = LOWER ? tt : nblk - 1 - tt;
+        const int nq = min(NQ, nrhs - ch * NQ);   // right-hand sides of this chain
+        T *X = Xall + (size_t)ch * NQ * ldx;
+        unsigned long long *W = Wall + (size_t)ch * NQ * n * TW;
         const int r0 = I * kTB, rows = min(kTB, n - r0);
         const bool has0 = lane < rows, has1 = lane + 32 < rows;
         // right-hand sides of the block, loaded before any wait
         T x0[NQ], x1[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            x0[q] = (q < nrhs && has0) ? X[(size_t)(r0 + lane) + (size_t)q * ldx] : T(0);
-            x1[q] = (q < nrhs && has1) ? X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] : T(0);
+            x0[q] = (q < nq && has0) ? X[(size_t)(r0 + lane) + (size_t)q * ldx] : T(0);
+            x1[q] = (q < nq && has1) ? X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] : T(0);
         }
         const int ndep = LOWER ? I : nblk - 1 - I;
         const int Jlast = LOWER ? I - 1 : I + 1;
@@ -183,9 +192,9 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
                     for (int q = 0; q < NQ; ++q) {
                         y0[q] = T(0);
                         y1[q] = T(0);
-                        if (q < nrhs && lane < cols)
+                        if (q < nq && lane < cols)
                             got &= get_tagged(W + ((size_t)q * n + c0 + lane) * TW, tag, y0[q]);
-                        if (q < nrhs && lane + 32 < cols)
+                        if (q < nq && lane + 32 < cols)
                             got &= get_tagged(W + ((size_t)q * n + c0 + lane + 32) * TW, tag, y1[q]);
                     }
                     if (__all_sync(0xffffffffu, got)) break;
@@ -306,14 +315,14 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, T *__restrict__ 
         // publish the tagged words first (the chain), then the plain result
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            if (q < nrhs) {
+            if (q < nq) {
                 if (has0) put_tagged(W + ((size_t)q * n + r0 + lane) * TW, x0[q], tag);
                 if (has1) put_tagged(W + ((size_t)q * n + r0 + lane + 32) * TW, x1[q], tag);
             }
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            if (q < nrhs) {
+            if (q < nq) {
                 if (has0) X[(size_t)(r0 + lane) + (size_t)q * ldx] = x0[q];
                 if (has1) X[(size_t)(r0 + lane + 32) + (size_t)q * ldx] = x1[q];
             }
@@ -385,6 +394,7 @@ size_t trsv_workspace_ints(int n, int nrhs) {
 template <typename T, int NQ>
 static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, int n, int nq, T *X, int ldx, int *ws,
                                   int *status, long long bound_ns, cudaStream_t s) {
+    const int nchains = (nq + NQ - 1) / NQ;
     cudaError_t e = cudaFuncSetAttribute(trsv_blocks<T, true, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(trsv_blocks<T, false, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -392,10 +402,11 @@ static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, i
     unsigned long long *W = reinterpret_cast<unsigned long long *>(ws + 2 * kFlagPad);
     // the forward pass publishes with tag 1, the backward pass with tag 2 over the
     // same words: a backward reader never mistakes a forward value for its own
-    trsv_blocks<T, true, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws, W, 1u, status, bound_ns);
+    trsv_blocks<T, true, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, nchains, X, ldx, ws, W, 1u, status,
+                                                              bound_ns);
     lu_count_launch();
-    trsv_blocks<T, false, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, X, ldx, ws + kFlagPad, W, 2u, status,
-                                                               bound_ns);
+    trsv_blocks<T, false, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, nchains, X, ldx, ws + kFlagPad, W, 2u,
+                                                               status, bound_ns);
     lu_count_launch();
     return cudaGetLastError();
 }
@@ -406,21 +417,20 @@ cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ld
                              long long bound_ns, int sms, cudaStream_t s) {
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     const int nblk = (n + kTB - 1) / kTB;
-    const int grid = std::min((nblk + kTWarps - 1) / kTWarps, 8 * sms);
     const size_t smem = sizeof(T) * (size_t)kTWarps * 2 * kTB * kTB;
     cudaError_t e = cudaSuccess;
     for (int q0 = 0; q0 < nrhs; q0 += kMaxRhs) {
         const int nq = std::min(kMaxRhs, nrhs - q0);
+        // chains of one right-hand side up to 8, of two beyond
+        const int chains = nq <= 8 ? nq : (nq + 1) / 2;
+        const int grid = std::min((nblk * chains + kTWarps - 1) / kTWarps, 8 * sms);
         // tickets and the words of this pass's right-hand sides
         const size_t used = (size_t)2 * kFlagPad + (size_t)2 * TagWords<T>::value * nq * n;
         e = cudaMemsetAsync(ws, 0, sizeof(int) * used, s);
         if (e != cudaSuccess) return e;
         T *Xq = X + (size_t)q0 * ldx;
-        if (nq == 1) e = launch_trsv_nq<T, 1>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
-        else if (nq <= 2) e = launch_trsv_nq<T, 2>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
-        else if (nq <= 4) e = launch_trsv_nq<T, 4>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
-        else if (nq <= 8) e = launch_trsv_nq<T, 8>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
-        else e = launch_trsv_nq<T, 16>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
+        if (nq <= 8) e = launch_trsv_nq<T, 1>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
+        else e = launch_trsv_nq<T, 2>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -446,7 +456,7 @@ cudaError_t launch_trsv_timeout_selftest(const float *LU, int n, float *X, int *
     if (e != cudaSuccess) return e;
     const int nblk = (n + kTB - 1) / kTB;
     trsv_blocks<float, true, 1><<<(nblk + kTWarps - 1) / kTWarps, 32 * kTWarps, smem, s>>>(
-        LU, n, n, 1, X, n, ws, reinterpret_cast<unsigned long long *>(ws + 2 * kFlagPad), 1u, status, bound_ns);
+        LU, n, n, 1, 1, X, n, ws, reinterpret_cast<unsigned long long *>(ws + 2 * kFlagPad), 1u, status, bound_ns);
     lu_count_launch();
     return cudaGetLastError();
 }

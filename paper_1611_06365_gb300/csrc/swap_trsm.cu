@@ -185,13 +185,13 @@ swap_trsm_kernel(T *__restrict__ A, int lda, int kb, int b, const int *__restric
         // FP64 digit slices: one power-of-two scale per column, 8 threads per column
         int *colexp = reinterpret_cast<int *>(Lc);
         const int c = tid >> 3, sub = tid & 7;
-        double amax = 0.0;
+        unsigned long long amax = 0;
         if (c < ncol)
-            for (int r = sub; r < b; r += 8) amax = fmax(amax, fabs((double)V[(size_t)r * kVS + c]));
+            for (int r = sub; r < b; r += 8) amax = max(amax, lu_f64_abs_bits((double)V[(size_t)r * kVS + c]));
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        for (int o = 4; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         if (sub == 0 && c < ncol) {
-            const int ex = lu_f64_scale_exp(amax);
+            const int ex = lu_f64_scale_exp_bits(amax);
             colexp[c] = ex;
             sd.dscale[c0 + c - stage_c0] = ldexp(1.0, ex);
         }

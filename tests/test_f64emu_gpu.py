@@ -100,9 +100,10 @@ def test_f64emu_schedule_invariance_bits():
     import paper_1611_06365_gb300 as lu
     A = li.uniform(600, 600, seed=19)
     ref, piv_ref, _, _, _ = factor_gpu(A, "f64", update=lu.LU_UPDATE_F64EMU, nb=64, lookahead=-1)
-    for la, ctas in ((1, 8), (1, 2), (-1, 4), (2, 8), (3, 4)):
-        LU, ipiv, _, _, _ = factor_gpu(A, "f64", update=lu.LU_UPDATE_F64EMU, nb=64, lookahead=la, panel_ctas=ctas)
-        assert np.array_equal(ipiv, piv_ref) and np.array_equal(LU, ref)
+    for la, ctas, share in ((1, 8, 0), (1, 2, 0), (-1, 4, 0), (2, 8, 0), (3, 4, 0), (1, 8, -1), (2, 16, -1)):
+        LU, ipiv, _, _, _ = factor_gpu(A, "f64", update=lu.LU_UPDATE_F64EMU, nb=64, lookahead=la, panel_ctas=ctas,
+                                       sm_share=share)
+        assert np.array_equal(ipiv, piv_ref) and np.array_equal(LU, ref), (la, ctas, share)
 
 
 def test_f64emu_full_size_n8192(oracle_mod):
@@ -122,3 +123,21 @@ def test_f64emu_full_size_n8192(oracle_mod):
     A_f, LU_f = A.cpu().numpy().T, dA.cpu().numpy().T
     LUo, _ = oracle_parity(oracle_mod, np.asfortranarray(A_f), ipiv.cpu().numpy())
     assert np.max(np.abs(LU_f - LUo)) <= 10 * n * EPS64 * max(1.0, float(np.max(np.abs(LUo))))
+
+
+def test_f64emu_update_nonfinite_propagates():
+    """An infinity in a row of A or a NaN in a column of B makes that row or column
+    of the result non-finite, as in the DFMA update (the integer sums cannot hold
+    them, the infinite scale carries them)."""
+    import paper_1611_06365_gb300 as lu
+    m, n, k = 200, 70, 40
+    A = li.uniform(m, k, seed=3)
+    B = li.uniform(k, n, seed=4)
+    C = li.uniform(m, n, seed=5)
+    A[5, 7] = np.inf
+    B[11, 3] = np.nan
+    emu = _update(lu.LU_UPDATE_F64EMU, A, B, C)
+    nat = _update(lu.LU_UPDATE_NATIVE, A, B, C)
+    assert np.array_equal(np.isfinite(emu), np.isfinite(nat))
+    assert not np.any(np.isfinite(emu[5, :])) and not np.any(np.isfinite(emu[:, 3]))
+    assert np.isfinite(np.delete(np.delete(emu, 5, axis=0), 3, axis=1)).all()

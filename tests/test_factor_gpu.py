@@ -154,9 +154,9 @@ def test_f32_tc_update_large_lookahead_invariance(update):
     """The tensor-core path under look-ahead on and off gives identical bits."""
     A = li.uniform(2304, 2304, seed=16)
     ref, pref, _, _, _ = factor_gpu(A, "f32", update=update, lookahead=-1)
-    for depth in (1, 2, 4):
-        got, pgot, _, _, _ = factor_gpu(A, "f32", update=update, lookahead=depth)
-        assert np.array_equal(pref, pgot) and np.array_equal(ref, got), depth
+    for depth, share in ((1, 0), (2, 0), (4, 0), (1, -1), (2, -1)):
+        got, pgot, _, _, _ = factor_gpu(A, "f32", update=update, lookahead=depth, sm_share=share)
+        assert np.array_equal(pref, pgot) and np.array_equal(ref, got), (depth, share)
 
 
 @pytest.mark.parametrize("depth", [2, 3, 4])

@@ -26,6 +26,35 @@ def test_solve_f64_matches_oracle(oracle_mod, n, nrhs):
     assert oracle_mod.backward_error(A, X, B) <= 10 * n * EPS64
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_solve_rhs_independent_bits(dtype):
+    """The right-hand sides of a pass run as separate substitution chains (one or
+    two per chain): every column of a multi-column solve equals the solve of
+    that column alone, bit for bit, for 1..8 columns (chains of one), 9..16
+    (chains of two, a ragged last chain) and beyond 16 (several passes)."""
+    import torch
+
+    import paper_1611_06365_gb300 as lu
+    n = 777
+    A = li.uniform(n, n, seed=41)
+    B = li.uniform(n, 35, seed=42)
+    _, _, _, dA, dpiv = factor_gpu(A, dtype)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    single = []
+    for q in range(B.shape[1]):
+        dB = li.to_device_colmajor(B[:, q:q + 1], dev(), dtype=tdt)
+        lu.lu_solve(dA, dpiv, dB, n)
+        single.append(li.from_device_colmajor(dB, n)[:, 0])
+    torch.cuda.synchronize()
+    for nrhs in (2, 8, 11, 16, 35):
+        dB = li.to_device_colmajor(B[:, :nrhs], dev(), dtype=tdt)
+        lu.lu_solve(dA, dpiv, dB, n)
+        torch.cuda.synchronize()
+        X = li.from_device_colmajor(dB, n)
+        for q in range(nrhs):
+            assert np.array_equal(X[:, q], single[q]), (nrhs, q)
+
+
 def test_solve_dyadic_exact():
     import torch
 

@@ -68,14 +68,32 @@ def _well_formed(ev, nsteps):
     assert sorted({e["step"] for e in ev if e["kind"] == "panel"}) == list(range(nsteps))
 
 
-@pytest.mark.parametrize("dtype,update,n,nb", [("f64", 0, 2048, 32), ("f32", 2, 16384, 64), ("f64", 4, 8192, 64)])
+@pytest.mark.parametrize("dtype,update,n,nb", [("f64", 0, 4096, 64), ("f32", 2, 16384, 64), ("f64", 4, 8192, 64)])
 def test_panel_sms_join_the_remainder_update(dtype, update, n, nb):
     """Worker sharing needs a remainder update that outlasts the panel: the early
-    steps of these orders (RU2 of step k is the larger task there)."""
+    steps of these orders (RU2 of step k is the larger task there).  The DFMA
+    update is a grid of short CTAs the hardware hands to freed SMs; the
+    persistent tensor-core updates give a panel placement's SMs back on request
+    and take them again with a joining grid (SmShare)."""
     ev = _trace(n, dtype, nb=nb, update=update)
     _well_formed(ev, (n + nb - 1) // nb)
     shared = _sharing(ev)
     assert len(shared) >= 1, ("no step shows a panel SM taking update tiles afterwards", _timeline(ev, 4))
+
+
+@pytest.mark.parametrize("dtype,update,n,nb", [("f32", 2, 16384, 64), ("f64", 4, 8192, 64)])
+def test_panel_overlaps_persistent_update(dtype, update, n, nb):
+    """With worker sharing the panel k+1 cluster runs while RU2(k) is still
+    working in most early steps, instead of waiting for the persistent grid to
+    drain; with sm_share = -1 the trace still records every task (the flag
+    changes the schedule, not the work)."""
+    ev = _trace(n, dtype, nb=nb, update=update)
+    tl = _timeline(ev, 8)
+    overlapped = [r for r in tl if r[1] < r[4]]        # panel(k+1) started before RU2(k) ended
+    assert len(overlapped) >= len(tl) // 2, tl
+    off = _trace(n, dtype, nb=nb, update=update, sm_share=-1)
+    for e in (ev, off):
+        assert sum(x["tiles"] for x in e if x["kind"] == "ru2" and x["step"] == 0) > 0
 
 
 def test_trace_off_records_nothing():

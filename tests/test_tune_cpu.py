@@ -24,7 +24,7 @@ def test_put_get_clear(L):
     lu.lu_tune_put(lu.TUNE_BATCHED, lu.LU_F32, 256, nb=32, ms=5.0)
     assert lu.lu_tune_count() == 3
     got = lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F64, 4096)
-    assert got == {"nb": 16, "nb_inner": 0, "panel_ctas": 8, "lookahead": 0, "update": 0, "update_ctas": 0}
+    assert got == {"nb": 16, "nb_inner": 0, "panel_ctas": 8, "lookahead": 0, "update": 0, "update_ctas": 0, "sm_share": 0}
     # the key includes the update kind and the exact order
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096) is None
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096, update=lu.LU_UPDATE_BF16X3)["nb"] == 128
@@ -120,6 +120,16 @@ def test_plan_info_follows_table(L):
     assert rc == 0 and p["nb"] == 16 and p["panel_ctas"] == 4
     rc, p = lu.lu_plan_info(lu.LU_F64, 4097)
     assert p["nb"] == 32
+
+
+def test_plan_info_worker_sharing_option(L):
+    """sm_share: on unless -1; values outside -1..1 are refused like other bad options."""
+    assert lu.lu_plan_info(lu.LU_F32, 4096, update=lu.LU_UPDATE_BF16)[1]["sm_share"] == 1
+    assert lu.lu_plan_info(lu.LU_F32, 4096, update=lu.LU_UPDATE_BF16, sm_share=1)[1]["sm_share"] == 1
+    assert lu.lu_plan_info(lu.LU_F64, 4096, update=lu.LU_UPDATE_F64EMU, sm_share=-1)[1]["sm_share"] == -1
+    for bad in (-2, 2):
+        with pytest.raises(lu.LuError):
+            lu.lu_plan_info(lu.LU_F64, 4096, sm_share=bad)
 
 
 @pytest.mark.parametrize("dt,update,widths", [
