@@ -651,7 +651,7 @@ def time_to_solution(args, dev):
             # the sustained BF16 rate, or the FP32 trailing matrix streamed once per panel
             bound_ms = max(3 * flops_lu(n) / (bf16_peak * 1e12), (8.0 / 3.0) * n ** 3 / plan_bo / (hbm_peak * 1e9)) * 1e3
             entry = {"kappa": kappa, "nrhs": nrhs, "rung": rep.rung, "f32_refactor": rep.f32_refactor,
-                     "iterations": rep.iterations,
+                     "cost_stop": rep.cost_stop, "t_fallback_ms": rep.t_fallback_ms, "iterations": rep.iterations,
                      "gmres_iters": rep.gmres_iters, "fell_back": rep.fell_back, "eta": eta,
                      "forward_error": fwd, "forward_error_est": getattr(rep, "forward_error_est", None),
                      "mixed_ms": rep.t_total_ms, "mixed_wall_ms": wall * 1e3, "factor_ms": rep.t_factor_ms,
@@ -671,6 +671,7 @@ def time_to_solution(args, dev):
                                  f"{key}_eta": eta64})
             entry.update(fp64)
             entry["speedup_vs_fp64"] = fp64["fp64_ms"] / rep.t_total_ms if rep.t_total_ms > 0 else None
+            entry["speedup_vs_fp64emu"] = fp64["fp64emu_ms"] / rep.t_total_ms if rep.t_total_ms > 0 else None
             cases.append(entry)
             if tc_roof is None:
                 # the tensor-core update inside one more run, against the HBM roofline (C in FP32

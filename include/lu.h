@@ -216,6 +216,11 @@ typedef struct {
     int f32_refactor;    /* 0: when classic refinement stalls on the factors of a tensor-core
                             update, refactor once with the FP32 update and refine on before
                             GMRES-IR; -1: never */
+    double fallback_ratio; /* cost model of the ladder: the FP64 fallback (factorization and
+                            refinement) is predicted to take fallback_ratio times the first
+                            factorization's measured time; 0 = the ratio measured by an earlier
+                            fallback of the same order in this process, else 4 (emulated FP64
+                            update) or 32 (DFMA update); < 0 = no cost model */
 } lu_mixed_opts;
 
 /* Result of lu_solve_mixed (host memory, filled before the call returns). */
@@ -235,6 +240,10 @@ typedef struct {
                             2006) */
     int f32_refactor;    /* 1 if the FP32 factorization with the FP32 update was made after
                             classic refinement stalled on the tensor-core update's factors */
+    int cost_stop;       /* 1 if the cost model ended the low-precision rungs early: their
+                            predicted or spent refinement time reached the predicted cost of
+                            the FP64 fallback */
+    double t_fallback_ms;  /* host time of the FP64 fallback (factorization and refinement), 0 if none */
 } lu_mixed_report;
 
 /*
@@ -247,6 +256,11 @@ typedef struct {
  *   read only.  dX device FP64 n x nrhs (ldx), output.
  *   opts host pointer or NULL.  rep host pointer (may be NULL).
  *   Synchronizes `stream` before returning (to fill rep).
+ *   The preconditioner solves with the FP32 factors use the inverses of their
+ *   64 x 64 diagonal blocks (formed once per factorization), so a block's
+ *   diagonal solve is a product rather than a chain of substitution steps.
+ *   Environment: LU_MIXED_LOG=1 prints each step's backward error and time,
+ *   and the cost model's prediction, to stderr.
  */
 int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const double *dB, int ldb,
                    double *dX, int ldx, const lu_mixed_opts *opts, lu_mixed_report *rep,

@@ -63,14 +63,15 @@ class MixedOpts(ctypes.Structure):
     _fields_ = [("update", ctypes.c_int), ("nb", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("allow_gmres", ctypes.c_int), ("allow_fallback", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("fp64_factor", ctypes.c_int), ("fallback_native", ctypes.c_int),
-                ("f32_refactor", ctypes.c_int)]
+                ("f32_refactor", ctypes.c_int), ("fallback_ratio", ctypes.c_double)]
 
 
 class MixedReport(ctypes.Structure):
     _fields_ = [("rung", ctypes.c_int), ("iterations", ctypes.c_int), ("gmres_iters", ctypes.c_int),
                 ("fell_back", ctypes.c_int), ("info", ctypes.c_int), ("backward_error", ctypes.c_double),
                 ("t_factor_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
-                ("forward_error_est", ctypes.c_double), ("f32_refactor", ctypes.c_int)]
+                ("forward_error_est", ctypes.c_double), ("f32_refactor", ctypes.c_int), ("cost_stop", ctypes.c_int),
+                ("t_fallback_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -263,12 +264,13 @@ def lu_solve_batched(dtype_code, nrhs, ns, LU_ptrs, ldas, ipiv_ptrs, B_ptrs, ldb
 
 
 def lu_solve_mixed(A, B, X, n=None, *, update=LU_UPDATE_BF16X3, nb=0, max_iter=0, tol=0.0, allow_gmres=1,
-                   allow_fallback=1, gmres_restart=0, fp64_factor=0, fallback_native=0, f32_refactor=0, stream=None):
+                   allow_fallback=1, gmres_restart=0, fp64_factor=0, fallback_native=0, f32_refactor=0,
+                   fallback_ratio=0.0, stream=None):
     """Mixed-precision solve A X = B (FP64 in/out).  Returns a MixedReport."""
     n, lda = _cm_dims(A, n)
     nrhs = B.shape[0]
     o = MixedOpts(update, nb, max_iter, tol, allow_gmres, allow_fallback, gmres_restart, fp64_factor, fallback_native,
-                  f32_refactor)
+                  f32_refactor, fallback_ratio)
     rep = MixedReport()
     _check("lu_solve_mixed", lib().lu_solve_mixed(n, nrhs, _ptr(A), lda, _ptr(B), _ld(B), _ptr(X), _ld(X),
                                                   ctypes.byref(o), ctypes.byref(rep), _stream(stream)))

@@ -96,7 +96,11 @@ template <typename TI, typename TO>
 cudaError_t launch_gather_rows(int n, int nrhs, const int *perm, const TI *B, int ldb, TO *X, int ldx, cudaStream_t s);
 template <typename T>
 cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status, long long bound_ns,
-                             int sms, cudaStream_t s);
+                             int sms, cudaStream_t s, const T *Dinv = nullptr);
+template <typename T>
+cudaError_t launch_diag_inverse(const T *LU, int lda, int n, T *Dinv, cudaStream_t s);
+template <typename T>
+size_t trsv_inverse_elems(int n);
 size_t trsv_workspace_ints(int n, int nrhs);
 cudaError_t launch_trsv_timeout_selftest(const float *LU, int n, float *X, int *ws, int *status, long long bound_ns,
                                          cudaStream_t s);
@@ -694,7 +698,7 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
 
 template <typename T>
 int solve_impl(int n, int nrhs, const T *LU, int lda, const int *ipiv, const int *perm_opt, T *B, int ldb, long long bound,
-               cudaStream_t s) {
+               cudaStream_t s, const T *Dinv = nullptr) {
     DevState *st = nullptr;
     LU_CUDA_TRY(dev_state(&st));
     if (n == 0 || nrhs == 0) return LU_OK;
@@ -709,7 +713,7 @@ int solve_impl(int n, int nrhs, const T *LU, int lda, const int *ipiv, const int
     LU_CUDA_TRY((launch_gather_rows<T, T>(n, nrhs, perm, B, ldb, X, n, s)));
     int *tws = nullptr;
     LU_CUDA_TRY(ws.get(&tws, trsv_workspace_ints(n, nrhs)));
-    LU_CUDA_TRY(launch_trsv_pair<T>(LU, lda, n, nrhs, X, n, tws, st->status, bound, st->sms, s));
+    LU_CUDA_TRY(launch_trsv_pair<T>(LU, lda, n, nrhs, X, n, tws, st->status, bound, st->sms, s, Dinv));
     LU_CUDA_TRY(cudaMemcpy2DAsync(B, sizeof(T) * ldb, X, sizeof(T) * n, sizeof(T) * n, nrhs, cudaMemcpyDeviceToDevice, s));
     return LU_OK;
 }
@@ -1197,8 +1201,15 @@ int default_outer_width(lu_dtype dt, int n, int update) {
     o.update = update;
     return dt == LU_F64 ? make_plan<double>(n, &o).bo : make_plan<float>(n, &o).bo;
 }
-int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s) {
-    return solve_impl<float>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s);
+int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s,
+                   const float *Dinv) {
+    return solve_impl<float>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s, Dinv);
+}
+// Dinv := the inverses of the FP32 factors' 64 x 64 diagonal blocks (for solve_f32_perm)
+size_t f32_diag_inverse_elems(int n) { return trsv_inverse_elems<float>(n); }
+int f32_diag_inverse(int n, const float *LU, int lda, float *Dinv, cudaStream_t s) {
+    LU_CUDA_TRY(launch_diag_inverse<float>(LU, lda, n, Dinv, s));
+    return LU_OK;
 }
 int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s) {
     return solve_impl<double>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s);

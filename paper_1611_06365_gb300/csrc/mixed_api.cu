@@ -19,6 +19,15 @@
 //   eta = max_q ||b_q - A x_q||_inf / (||A||_inf ||x_q||_inf + ||b_q||_inf)
 // at most `tol`.  Stall: eta has not halved over the last two steps, or
 // max_iter steps were taken on the rung.
+// Cost model (unless opts->fallback_ratio < 0): the FP64 fallback is
+// predicted to cost C = ratio x (the first factorization's measured time),
+// the ratio measured by the last fallback of the same order in this process
+// or a default.  The low-precision rungs may spend at most C of refinement
+// time before the fallback is taken (the rent-or-buy rule: the whole call
+// then costs at most the factorization plus twice C), and a rung stops as
+// soon as its own contraction predicts it would pass that budget: classic
+// refinement from the observed ratio of successive backward errors, the FP32
+// refactorization from its predicted cost, GMRES-IR from the time left.
 // Forward-error estimate: the correction one more refinement step would make,
 // relative to the solution: max_q ||d_q||_inf / ||x_q||_inf with d = M^{-1} r,
 // r = b - A x in FP64 and M the factors of the rung that finished (the
@@ -30,14 +39,22 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 namespace lu {
 int factor_f32_internal(int n, float *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s);
 int factor_f64_internal(int n, double *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s);
-int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s);
+int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s,
+                   const float *Dinv = nullptr);
 int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s);
+size_t f32_diag_inverse_elems(int n);
+int f32_diag_inverse(int n, const float *LU, int lda, float *Dinv, cudaStream_t s);
 cudaError_t launch_cast_rowsum(int n, const double *A, int lda, float *A32, int lda32, double *rowsum, cudaStream_t s);
 size_t residual_workspace_doubles(int n, int nrhs);
 cudaError_t launch_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B, int ldb,
@@ -53,7 +70,7 @@ cudaError_t launch_absmax_scaled_f32(int n, int nrhs, const float *D32, int ldd,
                                      unsigned long long *out, cudaStream_t s);
 int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb, double *X, int ldx, const float *LU32,
              int ld32, const int *perm, double anorm, const double *bnorm, double tol, int max_outer, int restart,
-             int *iters_out, int *inner_out, double *eta_out, cudaStream_t s);
+             int *iters_out, int *inner_out, double *eta_out, cudaStream_t s, double budget_ms, const float *Dinv);
 }  // namespace lu
 
 using namespace lu;
@@ -82,6 +99,27 @@ double bits_to_double(unsigned long long b) {
     double d;
     memcpy(&d, &b, sizeof(d));
     return d;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Measured cost ratios of this process, per (order, kind): kind 0 = FP64 fallback
+// with the emulated update, 1 = with the DFMA update, 2 = FP32 refactorization;
+// each relative to the first (tensor-core) factorization of the same call.
+std::mutex g_ratio_mu;
+std::map<std::pair<int, int>, double> g_ratio;
+
+double ratio_get(int n, int kind, double dflt) {
+    std::lock_guard<std::mutex> lk(g_ratio_mu);
+    auto it = g_ratio.find({n, kind});
+    return it == g_ratio.end() ? dflt : it->second;
+}
+void ratio_put(int n, int kind, double r) {
+    if (!(r > 0.0) || !std::isfinite(r)) return;
+    std::lock_guard<std::mutex> lk(g_ratio_mu);
+    g_ratio[{n, kind}] = r;
 }
 
 }  // namespace
@@ -171,6 +209,8 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     LU_CUDA_TRY(ws.get(&R, (size_t)n * nrhs));
     LU_CUDA_TRY(ws.get(&part, residual_workspace_doubles(n, nrhs)));
     LU_CUDA_TRY(ws.get(&norms, 1 + 4 * (size_t)nrhs));
+    float *Dinv = nullptr;   // inverses of the FP32 factors' diagonal blocks (preconditioner solves)
+    LU_CUDA_TRY(ws.get(&Dinv, f32_diag_inverse_elems(n)));
     unsigned long long *d_anorm = norms, *d_rmax = norms + 1, *d_xmax = norms + 1 + nrhs, *d_bmax = norms + 1 + 2 * nrhs;
     unsigned long long *d_dmax = norms + 1 + 3 * nrhs;
 
@@ -186,6 +226,8 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     if (!fp64_only) {
         rc = factor_f32_internal(n, A32, ld32, ipiv, info, perm, &fo, s);
         if (rc != LU_OK) return rc;
+        rc = f32_diag_inverse(n, A32, ld32, Dinv, s);
+        if (rc != LU_OK) return rc;
     } else {
         LU_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
     }
@@ -196,6 +238,20 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     LU_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
     LU_CUDA_TRY(cudaStreamSynchronize(s));
     r.info = hinfo;
+    // cost model: the predicted cost of the FP64 fallback, the budget of the rungs before it
+    float tf_ms = 0.f;
+    LU_CUDA_TRY(cudaEventElapsedTime(&tf_ms, e0, e1));
+    const bool fb_native = opts && opts->fallback_native;
+    const bool cost_on = !(opts && opts->fallback_ratio < 0) && allow_fb && !fp64_only && tf_ms > 0.f;
+    const double ratio64 = (opts && opts->fallback_ratio > 0) ? opts->fallback_ratio
+                                                              : ratio_get(n, fb_native ? 1 : 0, fb_native ? 32.0 : 4.0);
+    const double c64 = ratio64 * tf_ms;
+    const auto t_ref = std::chrono::steady_clock::now();
+    const char *log_env = getenv("LU_MIXED_LOG");
+    const bool log_on = log_env && log_env[0] == '1';
+    if (log_on)
+        fprintf(stderr, "lu_solve_mixed: n %d nrhs %d factor %.2f ms, fallback predicted %.2f ms (ratio %.2f)\n", n, nrhs,
+                tf_ms, c64, ratio64);
     const double anorm = bits_to_double(hn[0]);
     std::vector<double> bnorm(nrhs);
     for (int q = 0; q < nrhs; ++q) bnorm[q] = bits_to_double(hn[1 + 2 * nrhs + q]);
@@ -214,9 +270,10 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     // classic refinement with the FP32 factors in A32, from the current X and R
     auto classic = [&]() -> int {
         hist.clear();
+        const auto t_rung = std::chrono::steady_clock::now();
         for (int it = 0; it < max_iter; ++it) {
             LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
-            int rc2 = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
+            int rc2 = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s, Dinv);
             if (rc2 != LU_OK) return rc2;
             LU_CUDA_TRY(launch_axpy_scaled(n, nrhs, R32, n, d_rmax, dX, ldx, s));
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
@@ -225,9 +282,20 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             if (rc2 != LU_OK) return rc2;
             r.iterations++;
             hist.push_back(eta);
+            if (log_on) fprintf(stderr, "lu_solve_mixed: classic step %d eta %.3e at %.2f ms\n", it, eta, ms_since(t_ref));
             if (eta <= tol) { done = true; break; }
             const size_t h = hist.size();
             if (h >= 3 && !(hist[h - 1] <= 0.5 * hist[h - 3])) break;   // stalled
+            const double rho = h >= 2 ? hist[h - 1] / hist[h - 2] : 1.0;
+            if (cost_on && rho > 0.0 && rho < 1.0) {
+                // steps still needed at the last contraction rate, at this rung's time per step
+                // (no contraction is left to the stall rule)
+                const double need = std::ceil(std::log(tol / eta) / std::log(rho));
+                if (ms_since(t_ref) + need * ms_since(t_rung) / (it + 1) > c64) {
+                    r.cost_stop = 1;
+                    break;
+                }
+            }
         }
         return LU_OK;
     };
@@ -238,35 +306,57 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     // rung 0, second part: factors of the tensor-core update too coarse for this
     // matrix (refinement stalled) -- refactor with the FP32 update (FP32-accurate
     // factors) and refine on from the current solution
-    if (!done && !fp64_only && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0)) {
+    const bool refactor_ok = !done && !fp64_only && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0);
+    if (refactor_ok && cost_on && ms_since(t_ref) + ratio_get(n, 2, 1.5) * tf_ms >= c64) r.cost_stop = 1;
+    if (refactor_ok && !r.cost_stop) {
         r.f32_refactor = 1;
+        const auto t_rf = std::chrono::steady_clock::now();
         LU_CUDA_TRY(launch_cast_rowsum(n, dA, lda, A32, ld32, rowsum, s));
         lu_opts fo2 = {};
         fo2.update = LU_UPDATE_NATIVE;
         rc = factor_f32_internal(n, A32, ld32, ipiv, info, perm, &fo2, s);
         if (rc != LU_OK) return rc;
+        rc = f32_diag_inverse(n, A32, ld32, Dinv, s);
+        if (rc != LU_OK) return rc;
         LU_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
         LU_CUDA_TRY(cudaStreamSynchronize(s));
+        if (tf_ms > 0.f) ratio_put(n, 2, ms_since(t_rf) / tf_ms);
+        if (log_on) fprintf(stderr, "lu_solve_mixed: FP32 refactorization %.2f ms\n", ms_since(t_rf));
         if (hinfo == 0) {
             rc = classic();
             if (rc != LU_OK) return rc;
         }
     }
     // rung 1: GMRES-IR with the FP32 factors as preconditioner
-    if (!done && hinfo == 0 && allow_gmres && !fp64_only) {
+    const double gm_budget = cost_on ? c64 - ms_since(t_ref) : 0.0;
+    if (!done && hinfo == 0 && allow_gmres && !fp64_only && cost_on && gm_budget <= 0.0) r.cost_stop = 1;
+    if (!done && hinfo == 0 && allow_gmres && !fp64_only && !(cost_on && gm_budget <= 0.0)) {
         r.rung = 1;
         int outer = 0, inner = 0;
         rc = gmres_ir(n, nrhs, dA, lda, dB, ldb, dX, ldx, A32, ld32, perm, anorm, bnorm.data(), tol, max_iter, restart, &outer,
-                      &inner, &eta, s);
+                      &inner, &eta, s, cost_on ? gm_budget : 0.0, Dinv);
         if (rc != LU_OK) return rc;
         r.iterations += outer;
         r.gmres_iters += inner;
         done = eta <= tol;
+        if (log_on)
+            fprintf(stderr, "lu_solve_mixed: GMRES-IR %d outer %d inner, eta %.3e at %.2f ms (budget %.2f)\n", outer, inner,
+                    eta, ms_since(t_ref), gm_budget);
+        if (!done) {
+            if (cost_on && ms_since(t_ref) >= c64) r.cost_stop = 1;
+            // the iterate as it stands (a budget stop leaves columns unmeasured)
+            LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
+            LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
+            rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+            if (rc != LU_OK) return rc;
+            done = eta <= tol;
+        }
     }
     // rung 2: FP64 factorization
     if (!done && (allow_fb || fp64_only)) {
         r.rung = 2;
         r.fell_back = fp64_only ? 0 : 1;
+        const auto t_fb = std::chrono::steady_clock::now();
         int *ipiv64 = nullptr, *info64 = nullptr;
         factors64 = true;
         LU_CUDA_TRY(ws.get(&A64, (size_t)n * n));
@@ -321,6 +411,11 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             }
             done = eta <= tol;
         }
+        r.t_fallback_ms = ms_since(t_fb);
+        if (log_on) fprintf(stderr, "lu_solve_mixed: FP64 fallback %.2f ms, eta %.3e\n", r.t_fallback_ms, eta);
+        // learn the ratio of the fallback as asked for (not of one that needed the DFMA safety net)
+        if (!fp64_only && tf_ms > 0.f && (fb_native || o64.update == LU_UPDATE_F64EMU))
+            ratio_put(n, fb_native ? 1 : 0, r.t_fallback_ms / tf_ms);
     }
     // forward-error estimate: one more correction with the finishing rung's factors
     if (hinfo == 0 || factors64) {
@@ -335,7 +430,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             LU_CUDA_TRY(launch_absmax(n, nrhs, D, n, d_dmax, s));
         } else {
             LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
-            rc = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s);
+            rc = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s, Dinv);
             if (rc != LU_OK) return rc;
             LU_CUDA_TRY(launch_absmax_scaled_f32(n, nrhs, R32, n, d_rmax, d_dmax, s));
         }

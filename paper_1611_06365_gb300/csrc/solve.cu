@@ -120,11 +120,11 @@ __device__ __forceinline__ bool get_tagged(const unsigned long long *w, unsigned
 // nchains independent chains of NQ, run side by side, so the block-to-block
 // chain stays as short as for one right-hand side.  W holds the tagged
 // solution words, row i of right-hand side q at W[(q * n + i) * TagWords].
-template <typename T, bool LOWER, int NQ>
+template <typename T, bool LOWER, int NQ, bool INV = false>
 __global__ void __launch_bounds__(32 * kTWarps)
 trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, int nchains, T *__restrict__ Xall, int ldx,
             int *__restrict__ ticket, unsigned long long *__restrict__ Wall, unsigned tag, int *__restrict__ status,
-            long long bound_ns) {
+            long long bound_ns, const T *__restrict__ Dinv = nullptr) {
     constexpr int TW = TagWords<T>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -155,8 +155,13 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, int nchains, T *
         const int ndep = LOWER ? I : nblk - 1 - I;
         const int Jlast = LOWER ? I - 1 : I + 1;
         const int clast = Jlast * kTB, ncl = ndep > 0 ? min(kTB, n - clast) : 0;
-        // stage the diagonal block and the last dependency's block (matrix data only)
-        for (int blk = 0; blk < 2; ++blk) {
+        // stage the diagonal block (with INV: its inverse, contiguous [c][r]) and the
+        // last dependency's block (matrix data only)
+        if (INV) {
+            const T *src = Dinv + ((size_t)(LOWER ? 0 : nblk) + I) * kTB * kTB;
+            for (int e = lane; e < kTB * kTB; e += 32) Dg[e] = src[e];
+        }
+        for (int blk = INV ? 1 : 0; blk < 2; ++blk) {
             const int cbase = blk == 0 ? r0 : clast, ncol = blk == 0 ? rows : ncl;
             T *dst = blk == 0 ? Dg : Lp;
             for (int cb = 0; cb < ncol; cb += 16) {
@@ -252,7 +257,23 @@ trsv_blocks(const T *__restrict__ LU, int lda, int n, int nrhs, int nchains, T *
             x1[q] += acc1[q];
         }
         __syncwarp();
-        if (LOWER) {
+        if (INV) {
+            // x := D^{-1} x with the block's inverse: independent products, no chain
+            T n0[NQ], n1[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) { n0[q] = T(0); n1[q] = T(0); }
+            for (int c = 0; c < rows; ++c) {
+                const T d0 = Dg[c * kTB + lane], d1 = Dg[c * kTB + lane + 32];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const T xc = __shfl_sync(0xffffffffu, c < 32 ? x0[q] : x1[q], c & 31);
+                    n0[q] = fma(d0, xc, n0[q]);
+                    n1[q] = fma(d1, xc, n1[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) { x0[q] = n0[q]; x1[q] = n1[q]; }
+        } else if (LOWER) {
             for (int jj = 0; jj < rows; ++jj) {
                 const T l0 = Dg[jj * kTB + lane], l1 = Dg[jj * kTB + lane + 32];
 #pragma unroll
@@ -391,30 +412,86 @@ size_t trsv_workspace_ints(int n, int nrhs) {
     return (size_t)2 * kFlagPad + (size_t)4 * q * (size_t)std::max(n, 1);
 }
 
-template <typename T, int NQ>
+// Inverses of the 64 x 64 diagonal blocks of the factors: block I of the unit
+// lower factor at Dinv[I], of the upper factor at Dinv[nblk + I], each
+// column-major [c][r] and zero outside the block's rows x rows.  One CTA of 64
+// threads per block; thread j forms column j by substitution (IEEE division).
+template <typename T>
+__global__ void __launch_bounds__(kTB) diag_inverse_kernel(const T *__restrict__ LU, int lda, int n, T *__restrict__ Dinv) {
+    __shared__ T D[kTB][kTB + 1];    // D[c][r]
+    __shared__ T Xs[kTB][kTB + 1];   // Xs[c][r]: the inverse
+    const int nblk = (n + kTB - 1) / kTB;
+    const bool lower = blockIdx.x < (unsigned)nblk;
+    const int I = lower ? blockIdx.x : blockIdx.x - nblk;
+    const int r0 = I * kTB, rows = min(kTB, n - r0), j = threadIdx.x;
+    for (int e = j; e < kTB * kTB; e += kTB) {
+        const int c = e / kTB, r = e % kTB;
+        D[c][r] = (c < rows && r < rows) ? LU[(size_t)(r0 + r) + (size_t)(r0 + c) * lda] : T(0);
+        Xs[c][r] = T(0);
+    }
+    __syncthreads();
+    if (j < rows) {
+        if (lower) {
+            Xs[j][j] = T(1);
+            for (int i = j + 1; i < rows; ++i) {
+                T acc = T(0);
+                for (int k = j; k < i; ++k) acc = fma(-D[k][i], Xs[j][k], acc);
+                Xs[j][i] = acc;
+            }
+        } else {
+            Xs[j][j] = T(1) / D[j][j];
+            for (int i = j - 1; i >= 0; --i) {
+                T acc = T(0);
+                for (int k = i + 1; k <= j; ++k) acc = fma(-D[k][i], Xs[j][k], acc);
+                Xs[j][i] = acc / D[i][i];
+            }
+        }
+    }
+    __syncthreads();
+    T *dst = Dinv + (size_t)blockIdx.x * kTB * kTB;
+    for (int e = j; e < kTB * kTB; e += kTB) dst[e] = Xs[e / kTB][e % kTB];
+}
+
+template <typename T>
+size_t trsv_inverse_elems(int n) { return (size_t)2 * lu_ceil_div(std::max(n, 1), kTB) * kTB * kTB; }
+
+template <typename T>
+cudaError_t launch_diag_inverse(const T *LU, int lda, int n, T *Dinv, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    diag_inverse_kernel<T><<<2 * lu_ceil_div(n, kTB), kTB, 0, s>>>(LU, lda, n, Dinv);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int NQ, bool INV>
 static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, int n, int nq, T *X, int ldx, int *ws,
-                                  int *status, long long bound_ns, cudaStream_t s) {
+                                  int *status, long long bound_ns, cudaStream_t s, const T *Dinv) {
     const int nchains = (nq + NQ - 1) / NQ;
-    cudaError_t e = cudaFuncSetAttribute(trsv_blocks<T, true, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(trsv_blocks<T, true, NQ, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(trsv_blocks<T, false, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(trsv_blocks<T, false, NQ, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     unsigned long long *W = reinterpret_cast<unsigned long long *>(ws + 2 * kFlagPad);
     // the forward pass publishes with tag 1, the backward pass with tag 2 over the
     // same words: a backward reader never mistakes a forward value for its own
-    trsv_blocks<T, true, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, nchains, X, ldx, ws, W, 1u, status,
-                                                              bound_ns);
+    trsv_blocks<T, true, NQ, INV><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, nchains, X, ldx, ws, W, 1u, status,
+                                                                   bound_ns, Dinv);
     lu_count_launch();
-    trsv_blocks<T, false, NQ><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, nchains, X, ldx, ws + kFlagPad, W, 2u,
-                                                               status, bound_ns);
+    trsv_blocks<T, false, NQ, INV><<<grid, 32 * kTWarps, smem, s>>>(LU, lda, n, nq, nchains, X, ldx, ws + kFlagPad, W,
+                                                                    2u, status, bound_ns, Dinv);
     lu_count_launch();
     return cudaGetLastError();
 }
 
 // Workspace: trsv_workspace_ints(n, nrhs) ints, zeroed here before each pass.
+// Dinv (may be NULL): the diagonal blocks' inverses from launch_diag_inverse;
+// given, each block's diagonal solve is a product with its inverse (off the
+// substitution chain's serial steps; the rounding differs from substitution,
+// so it serves the refinement's preconditioner solves, not lu_solve).
 template <typename T>
 cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status,
-                             long long bound_ns, int sms, cudaStream_t s) {
+                             long long bound_ns, int sms, cudaStream_t s, const T *Dinv) {
     if (n <= 0 || nrhs <= 0) return cudaSuccess;
     const int nblk = (n + kTB - 1) / kTB;
     const size_t smem = sizeof(T) * (size_t)kTWarps * 2 * kTB * kTB;
@@ -429,8 +506,13 @@ cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ld
         e = cudaMemsetAsync(ws, 0, sizeof(int) * used, s);
         if (e != cudaSuccess) return e;
         T *Xq = X + (size_t)q0 * ldx;
-        if (nq <= 8) e = launch_trsv_nq<T, 1>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
-        else e = launch_trsv_nq<T, 2>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s);
+        if (Dinv) {
+            if (nq <= 8) e = launch_trsv_nq<T, 1, true>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
+            else e = launch_trsv_nq<T, 2, true>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
+        } else {
+            if (nq <= 8) e = launch_trsv_nq<T, 1, false>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
+            else e = launch_trsv_nq<T, 2, false>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
+        }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -522,7 +604,11 @@ cudaError_t launch_iota(int *v, int n, cudaStream_t s) {
 
 template cudaError_t launch_gather_rows<double, double>(int, int, const int *, const double *, int, double *, int, cudaStream_t);
 template cudaError_t launch_gather_rows<float, float>(int, int, const int *, const float *, int, float *, int, cudaStream_t);
-template cudaError_t launch_trsv_pair<double>(const double *, int, int, int, double *, int, int *, int *, long long, int, cudaStream_t);
-template cudaError_t launch_trsv_pair<float>(const float *, int, int, int, float *, int, int *, int *, long long, int, cudaStream_t);
+template cudaError_t launch_trsv_pair<double>(const double *, int, int, int, double *, int, int *, int *, long long, int,
+                                              cudaStream_t, const double *);
+template cudaError_t launch_trsv_pair<float>(const float *, int, int, int, float *, int, int *, int *, long long, int,
+                                             cudaStream_t, const float *);
+template cudaError_t launch_diag_inverse<float>(const float *, int, int, float *, cudaStream_t);
+template size_t trsv_inverse_elems<float>(int);
 
 }  // namespace lu

@@ -148,7 +148,7 @@ def test_mixed_uniform_reaches_1e14(oracle_mod, nrhs):
     n = 1500
     A = li.uniform(n, n, seed=li.BASE_SEED + 2000)
     B = li.uniform(n, nrhs, seed=li.BASE_SEED + 2001)
-    X, rep = _mixed(A, B)
+    X, rep = _mixed(A, B, fallback_ratio=-1.0)
     eta = oracle_mod.backward_error(A, X, B)
     assert eta <= 1e-14 and rep.backward_error <= 1e-14
     assert rep.fell_back == 0
@@ -163,7 +163,7 @@ def test_mixed_kappa_ladder(oracle_mod, kappa, rung_max):
     xt = li.uniform(n, 1, seed=9)
     xt[:, 0] = 1.0
     B = A @ xt
-    X, rep = _mixed(A, B)
+    X, rep = _mixed(A, B, fallback_ratio=-1.0)
     eta = oracle_mod.backward_error(A, X, B)
     assert eta <= 1e-14, (rep.as_dict(), eta)
     assert rep.rung <= rung_max
@@ -190,7 +190,7 @@ def test_mixed_fp8_update(oracle_mod, kind, rung_max):
     else:
         A = li.kappa_matrix(n, 10.0 if kind == "kappa10" else 1e3, seed=li.BASE_SEED + 2150, k=n)
     B = A @ np.ones((n, 1))
-    X, rep = _mixed(A, B, update=lu.LU_UPDATE_FP8)
+    X, rep = _mixed(A, B, update=lu.LU_UPDATE_FP8, fallback_ratio=-1.0)
     eta = oracle_mod.backward_error(A, X, B)
     assert eta <= 1e-14 and rep.rung <= rung_max, (rep.as_dict(), eta)
 
@@ -203,10 +203,10 @@ def test_mixed_refactors_in_fp32_when_the_tensor_core_factors_stall(oracle_mod):
     n = 1200
     A = li.kappa_matrix(n, 1e5, seed=li.BASE_SEED + 2300, k=n)
     B = A @ np.ones((n, 1))
-    X, rep = _mixed(A, B, update=lu.LU_UPDATE_BF16)
+    X, rep = _mixed(A, B, update=lu.LU_UPDATE_BF16, fallback_ratio=-1.0)
     assert oracle_mod.backward_error(A, X, B) <= 1e-14
     assert rep.f32_refactor == 1 and rep.rung == 0 and rep.fell_back == 0, rep.as_dict()
-    X2, rep2 = _mixed(A, B, update=lu.LU_UPDATE_BF16, f32_refactor=-1)   # without it: a later rung
+    X2, rep2 = _mixed(A, B, update=lu.LU_UPDATE_BF16, f32_refactor=-1, fallback_ratio=-1.0)   # without it: a later rung
     assert oracle_mod.backward_error(A, X2, B) <= 1e-14
     assert rep2.f32_refactor == 0 and rep2.rung >= 1
 
@@ -227,3 +227,50 @@ def test_mixed_forced_fallback_path(oracle_mod):
     X, rep = _mixed(A, B, max_iter=1, allow_gmres=0, tol=1e-300)
     assert rep.fell_back == 1 and rep.rung == 2
     assert oracle_mod.backward_error(A, X, B) <= 1e-15
+
+
+def test_mixed_cost_model_takes_the_fallback_when_refinement_would_cost_more(oracle_mod):
+    """With the FP64 fallback predicted to cost next to nothing, the ladder stops
+    refining as soon as it has a contraction rate to predict from, skips the
+    FP32 refactorization and GMRES-IR, and the fallback reaches the target."""
+    import paper_1611_06365_gb300 as lu
+    n = 1200
+    A = li.kappa_matrix(n, 1e5, seed=li.BASE_SEED + 2300, k=n)
+    B = A @ np.ones((n, 1))
+    X, rep = _mixed(A, B, update=lu.LU_UPDATE_BF16, fallback_ratio=1e-6)
+    assert rep.cost_stop == 1 and rep.rung == 2 and rep.fell_back == 1, rep.as_dict()
+    assert rep.f32_refactor == 0 and rep.gmres_iters == 0 and rep.t_fallback_ms > 0.0
+    assert oracle_mod.backward_error(A, X, B) <= 1e-14
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_mixed_cost_model_generous_budget_changes_nothing(nrhs):
+    """A fallback predicted to cost far more than any refinement leaves the ladder
+    as it is without the cost model: the same rungs and the same bits."""
+    import paper_1611_06365_gb300 as lu
+    n = 1200
+    A = li.kappa_matrix(n, 1e5, seed=li.BASE_SEED + 2300, k=n)
+    B = A @ li.uniform(n, nrhs, seed=77)
+    X1, r1 = _mixed(A, B, update=lu.LU_UPDATE_BF16, fallback_ratio=-1.0)
+    X2, r2 = _mixed(A, B, update=lu.LU_UPDATE_BF16, fallback_ratio=1e12)
+    assert r2.cost_stop == 0
+    assert (r1.rung, r1.iterations, r1.gmres_iters, r1.f32_refactor) == (r2.rung, r2.iterations, r2.gmres_iters,
+                                                                          r2.f32_refactor)
+    assert np.array_equal(X1, X2)
+
+
+def test_mixed_gmres_columns_together_match_alone(oracle_mod):
+    """GMRES-IR iterates the right-hand side columns side by side, each with its
+    own basis and stopping decisions: every column of a 5-column solve reaches
+    the target, as when solved alone."""
+    import paper_1611_06365_gb300 as lu
+    n = 700
+    A = li.kappa_matrix(n, 1e3, seed=li.BASE_SEED + 2400, k=n)   # kappa * 2^-8 ~ 4: classic refinement stalls
+    B = A @ li.uniform(n, 5, seed=78)
+    X, rep = _mixed(A, B, update=lu.LU_UPDATE_BF16, f32_refactor=-1, allow_fallback=0, fallback_ratio=-1.0)
+    assert rep.rung == 1 and rep.gmres_iters > 0, rep.as_dict()
+    for q in range(5):
+        assert oracle_mod.backward_error(A, X[:, q:q + 1], B[:, q:q + 1]) <= 1e-14, q
+        Xq, rq = _mixed(A, B[:, q:q + 1], update=lu.LU_UPDATE_BF16, f32_refactor=-1, allow_fallback=0,
+                        fallback_ratio=-1.0)
+        assert rq.rung == 1 and oracle_mod.backward_error(A, Xq, B[:, q:q + 1]) <= 1e-14

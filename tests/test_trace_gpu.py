@@ -68,10 +68,12 @@ def _well_formed(ev, nsteps):
     assert sorted({e["step"] for e in ev if e["kind"] == "panel"}) == list(range(nsteps))
 
 
-@pytest.mark.parametrize("dtype,update,n,nb", [("f64", 0, 4096, 64), ("f32", 2, 16384, 64), ("f64", 4, 8192, 64)])
+@pytest.mark.parametrize("dtype,update,n,nb", [("f64", 0, 4096, 64), ("f32", 2, 16384, 64), ("f64", 4, 16384, 64)])
 def test_panel_sms_join_the_remainder_update(dtype, update, n, nb):
     """Worker sharing needs a remainder update that outlasts the panel: the early
-    steps of these orders (RU2 of step k is the larger task there).  The DFMA
+    steps of these orders (RU2 of step k is the larger task there; with the
+    emulated FP64 update that takes n = 16384, as an 8192-row FP64 panel on 8
+    SMs runs about as long as the update of step 0).  The DFMA
     update is a grid of short CTAs the hardware hands to freed SMs; the
     persistent tensor-core updates give a panel placement's SMs back on request
     and take them again with a joining grid (SmShare)."""
