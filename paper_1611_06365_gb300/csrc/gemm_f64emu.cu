@@ -18,9 +18,11 @@
 // a K-term DFMA chain may round by K^2 2^-53 = 2^-41 of the same units).
 // The epilogue adds the six accumulators exactly in a 64-bit integer (units of
 // 2^-56 of the scales' product; the shared accumulator rounded to that unit),
-// converts it to FP64 (one rounding) and subtracts it from C with one fused
-// multiply-add by the two power-of-two scales: two roundings per element,
-// against K for a DFMA chain, and three FP64-pipe operations per element.
+// converts it to FP64 (one rounding), multiplies it by the column's
+// power-of-two scale by adding to its exponent field, and subtracts it from C
+// with one fused multiply-add by the row's scale: two roundings per element,
+// against K for a DFMA chain, and two FP64-pipe operations per element (a
+// column scale outside the exponent-add range takes an FP64 multiply instead).
 // The scales are per row and column,
 // so a row whose entries differ widely in magnitude keeps the absolute, not
 // the relative, accuracy of its largest entry (the normwise property of the
@@ -263,7 +265,8 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             // (on the integer and FP32 pipes; GB300's FP64 pipe is narrow): diagonal g <= 4
             // holds an integer multiple of 2^{-8(g+2)} below 2^24 of those units, so
             // acc_g * 2^{8(g+2)} converts exactly and scales by 2^{40-8g}; the shared sixth
-            // accumulator is rounded to the unit (at most 2^-57 of the scales' product).
+            // accumulator is rounded to the unit (at most 2^-57 of the scales' product; its
+            // magnitude stays below 2^24 units, so a 32-bit conversion holds it).
             // |sum| < 2^63; one conversion to FP64 and one FMA then give C - A B.
             long long vi[16];
 #pragma unroll
@@ -279,12 +282,26 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
                     for (int c = 0; c < 16; ++c) vi[c] += (long long)__float2int_rz(f[c] * up) * mul;
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) vi[c] += __float2ll_rn(f[c] * 0x1p56f);
+                    for (int c = 0; c < 16; ++c) vi[c] += (long long)__float2int_rn(f[c] * 0x1p56f);
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                cv[c] = fma(-(sa56 * __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])), __ll2double_rn(vi[c]), cv[c]);
+            for (int c = 0; c < 16; ++c) {
+                // column scale 2^eb (the same for every lane: a uniform branch); a nonzero
+                // converted sum has a biased exponent in [1023, 1085], so adding eb to it
+                // stays a normal number for biased eb in [1, 1984]
+                const double sb = __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)]);
+                const long long sbb = __double_as_longlong(sb);
+                const int ebias = (int)((sbb >> 52) & 0x7ff);
+                const double d = __ll2double_rn(vi[c]);
+                if (ebias >= 1 && ebias <= 1984) {
+                    const long long db = __double_as_longlong(d);
+                    cv[c] = fma(-__longlong_as_double(db == 0 ? 0 : db + (long long)(ebias - 1023) * (1LL << 52)), sa56,
+                                cv[c]);
+                } else {
+                    cv[c] = fma(-(sa56 * sb), d, cv[c]);   // the scales' product first: d sb may overflow
+                }
+            }
             // accumulators read: the MMAs of the sub-tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8u * a) : "memory");

@@ -275,6 +275,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             LU_CUDA_TRY(launch_to_f32_scaled(n, nrhs, R, n, d_rmax, R32, n, s));
             int rc2 = solve_f32_perm(n, nrhs, A32, ld32, perm, R32, n, s, Dinv);
             if (rc2 != LU_OK) return rc2;
+            if (log_on) LU_CUDA_TRY(launch_absmax_scaled_f32(n, nrhs, R32, n, d_rmax, d_dmax, s));
             LU_CUDA_TRY(launch_axpy_scaled(n, nrhs, R32, n, d_rmax, dX, ldx, s));
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
             LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
@@ -282,7 +283,13 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             if (rc2 != LU_OK) return rc2;
             r.iterations++;
             hist.push_back(eta);
-            if (log_on) fprintf(stderr, "lu_solve_mixed: classic step %d eta %.3e at %.2f ms\n", it, eta, ms_since(t_ref));
+            if (log_on) {
+                double corr = 0.0;   // max_q ||d_q|| / ||x_q|| of this step's correction
+                rc2 = ferr_now(nrhs, d_dmax, d_xmax, &corr, s);
+                if (rc2 != LU_OK) return rc2;
+                fprintf(stderr, "lu_solve_mixed: classic step %d eta %.3e correction %.3e at %.2f ms\n", it, eta, corr,
+                        ms_since(t_ref));
+            }
             if (eta <= tol) { done = true; break; }
             const size_t h = hist.size();
             if (h >= 3 && !(hist[h - 1] <= 0.5 * hist[h - 3])) break;   // stalled
@@ -307,8 +314,11 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     // matrix (refinement stalled) -- refactor with the FP32 update (FP32-accurate
     // factors) and refine on from the current solution
     const bool refactor_ok = !done && !fp64_only && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0);
-    if (refactor_ok && cost_on && ms_since(t_ref) + ratio_get(n, 2, 1.5) * tf_ms >= c64) r.cost_stop = 1;
-    if (refactor_ok && !r.cost_stop) {
+    // the refactorization's own predicted cost decides (a classic rung the cost model
+    // ended early is no reason to skip it: FP32 factors may contract where these did not)
+    const bool refactor_too_dear = refactor_ok && cost_on && ms_since(t_ref) + ratio_get(n, 2, 1.5) * tf_ms >= c64;
+    if (refactor_too_dear) r.cost_stop = 1;
+    if (refactor_ok && !refactor_too_dear) {
         r.f32_refactor = 1;
         const auto t_rf = std::chrono::steady_clock::now();
         LU_CUDA_TRY(launch_cast_rowsum(n, dA, lda, A32, ld32, rowsum, s));

@@ -484,6 +484,36 @@ static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, i
     return cudaGetLastError();
 }
 
+// CTAs of the substitution kernel resident per SM (shared memory bound).
+template <typename T, bool INV>
+static int trsv_ctas_per_sm(size_t smem) {
+    static int cached[2] = {0, 0};
+    int &c = cached[sizeof(T) == 8];
+    if (c == 0) {
+        int k = 0;
+        if (cudaFuncSetAttribute(trsv_blocks<T, true, 1, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, trsv_blocks<T, true, 1, INV>, 32 * kTWarps, smem) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            k = 1;
+        }
+        c = std::max(1, k);
+    }
+    return c;
+}
+
+template <typename T, bool INV>
+static cudaError_t launch_trsv_per(int per, int grid, size_t smem, const T *LU, int lda, int n, int nq, T *X, int ldx,
+                                   int *ws, int *status, long long bound_ns, cudaStream_t s, const T *Dinv) {
+    switch (per) {
+        case 1: return launch_trsv_nq<T, 1, INV>(grid, smem, LU, lda, n, nq, X, ldx, ws, status, bound_ns, s, Dinv);
+        case 2: return launch_trsv_nq<T, 2, INV>(grid, smem, LU, lda, n, nq, X, ldx, ws, status, bound_ns, s, Dinv);
+        case 4: return launch_trsv_nq<T, 4, INV>(grid, smem, LU, lda, n, nq, X, ldx, ws, status, bound_ns, s, Dinv);
+        default: return launch_trsv_nq<T, 8, INV>(grid, smem, LU, lda, n, nq, X, ldx, ws, status, bound_ns, s, Dinv);
+    }
+}
+
 // Workspace: trsv_workspace_ints(n, nrhs) ints, zeroed here before each pass.
 // Dinv (may be NULL): the diagonal blocks' inverses from launch_diag_inverse;
 // given, each block's diagonal solve is a product with its inverse (off the
@@ -498,21 +528,23 @@ cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ld
     cudaError_t e = cudaSuccess;
     for (int q0 = 0; q0 < nrhs; q0 += kMaxRhs) {
         const int nq = std::min(kMaxRhs, nrhs - q0);
-        // chains of one right-hand side up to 8, of two beyond
-        const int chains = nq <= 8 ? nq : (nq + 1) / 2;
+        // As many chains as keep every block's warp resident from the start (a block
+        // whose warp starts late sums all its dependencies on the chain's critical
+        // path), each carrying the fewest right-hand sides that allows.
+        const int per_sm = Dinv ? trsv_ctas_per_sm<T, true>(smem) : trsv_ctas_per_sm<T, false>(smem);
+        const int resident = std::max(1, per_sm) * kTWarps * sms;
+        int chains = std::max(1, std::min(nq, resident / std::max(nblk, 1)));
+        int per = (nq + chains - 1) / chains;
+        per = per <= 1 ? 1 : per <= 2 ? 2 : per <= 4 ? 4 : 8;
+        chains = (nq + per - 1) / per;
         const int grid = std::min((nblk * chains + kTWarps - 1) / kTWarps, 8 * sms);
         // tickets and the words of this pass's right-hand sides
         const size_t used = (size_t)2 * kFlagPad + (size_t)2 * TagWords<T>::value * nq * n;
         e = cudaMemsetAsync(ws, 0, sizeof(int) * used, s);
         if (e != cudaSuccess) return e;
         T *Xq = X + (size_t)q0 * ldx;
-        if (Dinv) {
-            if (nq <= 8) e = launch_trsv_nq<T, 1, true>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
-            else e = launch_trsv_nq<T, 2, true>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
-        } else {
-            if (nq <= 8) e = launch_trsv_nq<T, 1, false>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
-            else e = launch_trsv_nq<T, 2, false>(grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
-        }
+        if (Dinv) e = launch_trsv_per<T, true>(per, grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
+        else e = launch_trsv_per<T, false>(per, grid, smem, LU, lda, n, nq, Xq, ldx, ws, status, bound_ns, s, Dinv);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

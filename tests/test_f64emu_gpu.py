@@ -60,6 +60,31 @@ def test_f64emu_update_accuracy(m, n, k):
     assert np.max(err_emu) <= max(np.max(err_nat), 4 * EPS64 * float(np.max(np.abs(ref.astype(np.float64)))))
 
 
+def test_f64emu_update_extreme_column_scales():
+    """Columns of B near the top of the FP64 range (scale 2^970: the column scale is
+    applied by an FP64 multiply) and in the subnormal range (the same), beside
+    ordinary and tiny normal columns (applied by adding to the exponent): every
+    element within the accuracy bound of the extended-precision reference."""
+    import paper_1611_06365_gb300 as lu
+    m, n, k = 300, 6, 64
+    A = li.uniform(m, k, seed=11)
+    B = li.uniform(k, n, seed=12)
+    B[:, 0] *= 2.0 ** 970
+    B[:, 1] *= 2.0 ** -1040          # subnormal entries
+    B[:, 2] *= 2.0 ** -1000
+    B[:, 3] *= 2.0 ** 900
+    C = li.uniform(m, n, seed=13)
+    C[:, 0] *= 2.0 ** 970
+    C[:, 3] *= 2.0 ** 900
+    ref = _reference(A, B, C)
+    emu = _update(lu.LU_UPDATE_F64EMU, A, B, C)
+    err = np.abs(emu.astype(np.longdouble) - ref)
+    scale = (np.max(np.abs(A), axis=1)[:, None] * np.max(np.abs(B), axis=0)[None, :]).astype(np.longdouble)
+    bound = 2 * EPS64 * np.abs(ref) + np.longdouble(2.0 ** -46) * scale + np.longdouble(2.0 ** -1074)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert np.all(np.isfinite(emu))
+
+
 def test_f64emu_update_exact_on_dyadic_operands():
     """Operands with few significant bits (multiples of 1/8 below 8) give exact products:
     the result equals the exactly rounded one bit for bit."""
