@@ -285,22 +285,29 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
                     for (int c = 0; c < 16; ++c) vi[c] += (long long)__float2int_rn(f[c] * 0x1p56f);
                 }
             }
+            // Column scales 2^eb: a nonzero converted sum has a biased exponent in [1023, 1085],
+            // so adding eb to it stays a normal number for biased eb in [1, 1984].  The 16
+            // columns are the same for every lane, so the choice is made once for all of them
+            // (a branch per column would be if-converted and issue both paths).
+            bool fast = true;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                // column scale 2^eb (the same for every lane: a uniform branch); a nonzero
-                // converted sum has a biased exponent in [1023, 1085], so adding eb to it
-                // stays a normal number for biased eb in [1, 1984]
-                const double sb = __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)]);
-                const long long sbb = __double_as_longlong(sb);
-                const int ebias = (int)((sbb >> 52) & 0x7ff);
-                const double d = __ll2double_rn(vi[c]);
-                if (ebias >= 1 && ebias <= 1984) {
-                    const long long db = __double_as_longlong(d);
-                    cv[c] = fma(-__longlong_as_double(db == 0 ? 0 : db + (long long)(ebias - 1023) * (1LL << 52)), sa56,
-                                cv[c]);
-                } else {
-                    cv[c] = fma(-(sa56 * sb), d, cv[c]);   // the scales' product first: d sb may overflow
+                const int eb = (int)((__double_as_longlong(__ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])) >> 52) & 0x7ff);
+                fast = fast && eb >= 1 && eb <= 1984;
+            }
+            if (fast) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int eb = (int)((__double_as_longlong(__ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])) >> 52) & 0x7ff);
+                    const long long db = __double_as_longlong(__ll2double_rn(vi[c]));
+                    cv[c] = fma(-__longlong_as_double(db == 0 ? 0 : db + (long long)(eb - 1023) * (1LL << 52)), sa56, cv[c]);
                 }
+            } else {
+                // the scales' product first: the converted sum times a column scale above 2^961
+                // may overflow
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    cv[c] = fma(-(sa56 * __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])), __ll2double_rn(vi[c]), cv[c]);
             }
             // accumulators read: the MMAs of the sub-tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
