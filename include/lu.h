@@ -110,6 +110,11 @@ typedef struct {
                           tiles while panel k+1 waits for them, and a grid of as many CTAs
                           joins RU2's tile queue when the panel ends; -1 = off (RU2 keeps
                           its SMs until its queue is empty) */
+    int tile;          /* trailing-update tile shape: 0 = auto; 1 = large (DFMA update 64 x 64
+                          output tiles; emulated FP64 update tasks of 8 sub-tiles of 32 columns);
+                          2 = small (32 x 32; 2 sub-tiles).  Changes the schedule, not the
+                          arithmetic (results are the same bits); the FP32 tensor-core updates
+                          have one shape and ignore it */
 } lu_opts;
 
 /*
@@ -343,7 +348,8 @@ typedef struct {
  * {64, 128, 256} (FP32 and its tensor-core updates); then panel teams of 8 and
  * 4 CTAs at the best b_o; for n <= 2048 also the plan without look-ahead; the
  * look-ahead of depth 2; for the tensor-core updates also a remainder-update
- * grid of 112 CTAs (update_ctas).  budget_ms > 0 stops adding candidates once
+ * grid of 112 CTAs (update_ctas); for the DFMA and emulated FP64 updates both
+ * tile shapes (tile 1 and 2).  budget_ms > 0 stops adding candidates once
  * that much device time has been spent (at least one is timed).
  * update: LU_UPDATE_* (BF16 .. FP8 with LU_F32, F64EMU with LU_F64).
  * Synchronizes `stream`.

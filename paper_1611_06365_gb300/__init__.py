@@ -52,7 +52,7 @@ class LuError(RuntimeError):
 class LuOpts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("nb_inner", ctypes.c_int), ("panel_ctas", ctypes.c_int),
                 ("lookahead", ctypes.c_int), ("update", ctypes.c_int), ("spin_ns", ctypes.c_longlong),
-                ("update_ctas", ctypes.c_int), ("sm_share", ctypes.c_int)]
+                ("update_ctas", ctypes.c_int), ("sm_share", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 class TuneResult(ctypes.Structure):
@@ -199,10 +199,10 @@ def _cm_dims(A, n=None):
 
 
 def lu_factor(A, ipiv, info, n=None, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0,
-              update=LU_UPDATE_NATIVE, spin_ns=0, update_ctas=0, sm_share=0, stream=None):
+              update=LU_UPDATE_NATIVE, spin_ns=0, update_ctas=0, sm_share=0, tile=0, stream=None):
     """P A = L U in place (see include/lu.h).  A: column-major (n, lda) tensor."""
     n, lda = _cm_dims(A, n)
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns, update_ctas, sm_share)
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns, update_ctas, sm_share, tile)
     return _check("lu_factor", lib().lu_factor(_dtype_code(A), n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
                                                 ctypes.byref(o), _stream(stream)))
 
@@ -399,7 +399,7 @@ def from_colmajor(T, m=None):
 
 def _opts_dict(o):
     return {"nb": o.nb, "nb_inner": o.nb_inner, "panel_ctas": o.panel_ctas, "lookahead": o.lookahead, "update": o.update,
-            "update_ctas": o.update_ctas, "sm_share": o.sm_share}
+            "update_ctas": o.update_ctas, "sm_share": o.sm_share, "tile": o.tile}
 
 
 def lu_autotune(dtype_code, n, *, update=LU_UPDATE_NATIVE, budget_ms=0.0, stream=None):
@@ -419,10 +419,10 @@ def lu_autotune_batched(dtype_code, ns, max_n, *, stream=None):
 
 
 def lu_plan_info(dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE, update_ctas=0,
-                 sm_share=0):
+                 sm_share=0, tile=0):
     """(status, plan dict) of the plan lu_factor would run for these options (no CUDA call);
     status 0 = every panel fits, LU_ERR_UNSUPPORTED = one does not."""
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas, sm_share)
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas, sm_share, tile)
     p = LuOpts()
     rc = lib().lu_plan_info(dtype_code, n, ctypes.byref(o), ctypes.byref(p))
     if rc < 0 and rc > -100:
@@ -437,8 +437,8 @@ def lu_tune_get(kind, dtype_code, n, *, update=LU_UPDATE_NATIVE):
 
 
 def lu_tune_put(kind, dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE,
-                update_ctas=0, ms=0.0):
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas)
+                update_ctas=0, tile=0, ms=0.0):
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas, 0, tile)
     return _check("lu_tune_put", lib().lu_tune_put(kind, dtype_code, update, n, ctypes.byref(o), float(ms)))
 
 

@@ -56,7 +56,7 @@ cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c
 // gemm_simt.cu
 template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s,
-                             CtaTrace tr = CtaTrace{}, bool transb = false, int lshift = -1);
+                             CtaTrace tr = CtaTrace{}, bool transb = false, int lshift = -1, int tile = 0);
 // gemm_tc.cu
 cudaError_t make_stage_maps(CUtensorMap *mapA, const void *stageA, int rowsA, CUtensorMap *mapB, const void *stageB,
                             int colsB, int kinner, int lds, int fp8);
@@ -82,7 +82,7 @@ bool tc_c_aligned(const float *C, int ldc);
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
                                long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr = CtaTrace{},
-                               int lshift = -1, SmShare sh = SmShare{});
+                               int lshift = -1, SmShare sh = SmShare{}, int tile = 0);
 cudaError_t launch_stage_rows_f64emu(int rows, int k, const double *L, int ld, __nv_bfloat16 *stage, int lds, double *scale,
                                      cudaStream_t s);
 cudaError_t launch_stage_cols_f64emu(int k, int cols, const double *B, int ld, __nv_bfloat16 *stage, int lds, double *scale,
@@ -330,6 +330,7 @@ struct Plan {
     int panel_ctas = 16;
     int update_ctas = 0;   // persistent CTAs of the remainder update (0: one per SM)
     bool share = true;     // worker sharing with the persistent tensor-core update (SmShare)
+    int tile = 0;          // update tile shape (lu_opts.tile)
     long long bound = 2000000000LL;
 };
 
@@ -371,6 +372,7 @@ Plan make_plan(int n, const lu_opts *o) {
     p.panel_ctas = (o && o->panel_ctas > 0) ? std::min(16, o->panel_ctas) : (sizeof(T) == 8 ? 8 : 16);
     p.update_ctas = (o && o->update_ctas > 0) ? o->update_ctas : 0;
     p.share = !(o && o->sm_share < 0);
+    p.tile = o ? o->tile : 0;
     p.bound = lu_spin_bound_ns(o);
     return p;
 }
@@ -386,6 +388,7 @@ const lu_opts *with_tuned(int kind, lu_dtype dt, int n, const lu_opts *o, lu_opt
     if (buf->panel_ctas == 0) buf->panel_ctas = t.panel_ctas;
     if (buf->lookahead == 0) buf->lookahead = t.lookahead;
     if (buf->update_ctas == 0) buf->update_ctas = t.update_ctas;
+    if (buf->tile == 0) buf->tile = t.tile;
     return buf;
 }
 
@@ -453,7 +456,7 @@ cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int
         if (c.pl.tc)
             return launch_gemm_f64emu(m, nn, c.mapA[k_par], 0, c.mapB, c0 - r0, reinterpret_cast<double *>(c.A) + r0 + (size_t)c0 * c.lda,
                                       c.lda, c.dscA[k_par], c.dscB, c.tile_ctr + (ru ? 1 : 0), c.st->status,
-                                      c.pl.bound, ru ? c.pl.update_ctas : 0, s, tr, -1, sh);
+                                      c.pl.bound, ru ? c.pl.update_ctas : 0, s, tr, -1, sh, c.pl.tile);
     }
     if constexpr (sizeof(T) == 4) {
         if (c.pl.tc)
@@ -463,7 +466,7 @@ cudaError_t update_launch(FactorCtx<T> &c, int k_par, int kb, int w, int c0, int
                                   ru ? c.pl.update_ctas : 0, tr, sh);
     }
     return launch_gemm_simt<T>(m, nn, w, c.A + r0 + (size_t)kb * c.lda, c.lda, c.A + kb + (size_t)c0 * c.lda, c.lda,
-                               c.A + r0 + (size_t)c0 * c.lda, c.lda, s, tr);
+                               c.A + r0 + (size_t)c0 * c.lda, c.lda, s, tr, false, -1, c.pl.tile);
 }
 
 template <typename T>
@@ -728,7 +731,7 @@ extern "C" {
 static bool opts_valid(lu_dtype dt, const lu_opts *opts) {
     if (!opts) return true;
     if (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 || opts->update_ctas < 0 ||
-        opts->sm_share < -1 || opts->sm_share > 1 ||
+        opts->sm_share < -1 || opts->sm_share > 1 || opts->tile < 0 || opts->tile > 2 ||
         (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
          opts->update != LU_UPDATE_FP8 && opts->update != LU_UPDATE_F64EMU))
         return false;
@@ -756,6 +759,7 @@ int lu_plan_info(lu_dtype dt, int n, const lu_opts *opts, lu_opts *plan) {
     plan->spin_ns = p.bound;
     plan->update_ctas = p.update_ctas;
     plan->sm_share = p.share ? 1 : -1;
+    plan->tile = p.tile;
     return plan_fits(p, n, elem) ? LU_OK : LU_ERR_UNSUPPORTED;
 }
 

@@ -30,10 +30,11 @@
 namespace lu {
 template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s,
-                             CtaTrace tr, bool transb, int lshift);
+                             CtaTrace tr, bool transb, int lshift, int tile);
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift, SmShare sh);
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift, SmShare sh,
+                               int tile);
 cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8);
 int f64emu_kpad();
 int f64emu_box_rows();
@@ -234,10 +235,10 @@ cudaError_t chol_update(ChCtx<T> &c, int par, int kb, int w, int c0, int c1, int
         if (c.emu)
             return launch_gemm_f64emu(m, nn, c.mapA[par], c0 - r0, c.mapB[par], c0 - r0,
                                       reinterpret_cast<double *>(c.A) + c0 + (size_t)c0 * c.lda, c.lda, c.sc[par], c.sc[par],
-                                      c.ctr + ctr_slot, lu_device_status_ptr(), c.bound, 0, s, tr, 0, SmShare{});
+                                      c.ctr + ctr_slot, lu_device_status_ptr(), c.bound, 0, s, tr, 0, SmShare{}, 0);
     }
     const T *L21 = c.A + c0 + (size_t)kb * c.lda;
-    return launch_gemm_simt<T>(m, nn, w, L21, c.lda, L21, c.lda, c.A + c0 + (size_t)c0 * c.lda, c.lda, s, tr, true, 0);
+    return launch_gemm_simt<T>(m, nn, w, L21, c.lda, L21, c.lda, c.A + c0 + (size_t)c0 * c.lda, c.lda, s, tr, true, 0, 0);
 }
 
 template <typename T>

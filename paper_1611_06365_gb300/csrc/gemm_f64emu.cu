@@ -385,7 +385,8 @@ int f64emu_box_cols() { return kEmBN; }
 // the Cholesky factorization, where B is L21^T staged like A).
 cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
                                double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift, SmShare sh) {
+                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift, SmShare sh,
+                               int tile) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     if (sh.req && !sh.mask) return cudaErrorInvalidValue;
     static int sms = 0;
@@ -402,8 +403,11 @@ cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0
         attr = true;
     }
     const long long mt = lu_ceil_div(m, kEmBM);
-    int nsub = kEmMaxSub;   // fewer sub-tiles per task while the queue would not fill the GPU twice
-    while (nsub > 1 && mt * lu_ceil_div(n, (long long)kEmBN * nsub) < 2LL * sms) nsub >>= 1;
+    // sub-tiles per task: tile 1: kEmMaxSub; 2: two; 0: fewer while the queue would not fill
+    // the GPU twice (the task shape changes the schedule, not the arithmetic)
+    int nsub = tile == 2 ? 2 : kEmMaxSub;
+    if (tile == 0)
+        while (nsub > 1 && mt * lu_ceil_div(n, (long long)kEmBN * nsub) < 2LL * sms) nsub >>= 1;
     const long long ntasks = mt * lu_ceil_div(n, (long long)kEmBN * nsub);
     const int cap = max_ctas > 0 && max_ctas < sms ? max_ctas : sms;
     int grid = (int)(ntasks < cap ? ntasks : cap);

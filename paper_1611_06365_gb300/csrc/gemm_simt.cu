@@ -88,7 +88,7 @@ gemm_update_simt(int m, int n, int k, const T *__restrict__ A, int lda, const T 
 
 template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc,
-                             cudaStream_t s, CtaTrace tr, bool transb, int lshift) {
+                             cudaStream_t s, CtaTrace tr, bool transb, int lshift, int tile) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
     static int sms = 0;
     if (!sms) {
@@ -97,8 +97,10 @@ cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
         if (e != cudaSuccess) return e;
     }
+    // tile 1: 64 x 64 tiles, 2: 32 x 32, 0: 64 x 64 when that makes at least one tile per SM
+    // (both shapes accumulate in the same order: the same bits)
     const long long big = (long long)lu_ceil_div(m, 64) * lu_ceil_div(n, 64);
-    if (big >= sms) {
+    if (tile == 1 || (tile != 2 && big >= sms)) {
         dim3 grid(lu_ceil_div(m, 64), lu_ceil_div(n, 64));
         if (grid.y > 65535) return cudaErrorInvalidValue;
         if (transb)
@@ -117,8 +119,8 @@ cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *
 }
 
 template cudaError_t launch_gemm_simt<double>(int, int, int, const double *, int, const double *, int, double *, int, cudaStream_t,
-                                              CtaTrace, bool, int);
+                                              CtaTrace, bool, int, int);
 template cudaError_t launch_gemm_simt<float>(int, int, int, const float *, int, const float *, int, float *, int, cudaStream_t,
-                                             CtaTrace, bool, int);
+                                             CtaTrace, bool, int, int);
 
 }  // namespace lu

@@ -61,8 +61,9 @@ bool valid_update(lu_dtype dt, int update) {
     return dt == LU_F32 && (update == LU_UPDATE_BF16 || update == LU_UPDATE_BF16X3 || update == LU_UPDATE_FP8);
 }
 
-lu_opts make_opts(int nb, int nb_inner, int panel_ctas, int lookahead, int update, int update_ctas = 0) {
+lu_opts make_opts(int nb, int nb_inner, int panel_ctas, int lookahead, int update, int update_ctas = 0, int tile = 0) {
     lu_opts o = {};
+    o.tile = tile;
     o.nb = nb;
     o.nb_inner = nb_inner;
     o.panel_ctas = panel_ctas;
@@ -74,7 +75,7 @@ lu_opts make_opts(int nb, int nb_inner, int panel_ctas, int lookahead, int updat
 
 bool opts_in_range(int kind, const lu_opts &o) {
     if (o.nb < 0 || o.nb_inner < 0 || o.panel_ctas < 0 || o.panel_ctas > 16 || o.lookahead < -1 || o.lookahead > 4 ||
-        o.update_ctas < 0 || o.update_ctas > 4096)
+        o.update_ctas < 0 || o.update_ctas > 4096 || o.tile < 0 || o.tile > 2)
         return false;
     return kind != 1 || o.nb == 0 || o.nb == 1 || o.nb == 16 || o.nb == 32;
 }
@@ -106,7 +107,7 @@ int lu_tune_put(int kind, lu_dtype dt, int update, int n, const lu_opts *o, doub
     if (!valid_update(dt, update)) return -3;
     if (n < 0) return -4;
     if (!o || !opts_in_range(kind, *o)) return -5;
-    lu_opts c = make_opts(o->nb, o->nb_inner, o->panel_ctas, o->lookahead, update, o->update_ctas);
+    lu_opts c = make_opts(o->nb, o->nb_inner, o->panel_ctas, o->lookahead, update, o->update_ctas, o->tile);
     std::lock_guard<std::mutex> lk(g_tmu);
     g_table[Key{kind, (int)dt, update, n}] = Entry{c, ms};
     return LU_OK;
@@ -127,11 +128,12 @@ int lu_tune_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return -1;
     std::lock_guard<std::mutex> lk(g_tmu);
-    fprintf(f, "# liblu tuning table v1\n# kind dtype update n nb nb_inner panel_ctas lookahead update_ctas ms\n");
+    fprintf(f, "# liblu tuning table v2\n# kind dtype update n nb nb_inner panel_ctas lookahead update_ctas tile ms\n");
     for (const auto &kv : g_table) {
         const lu_opts &o = kv.second.o;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                std::get<3>(kv.first), o.nb, o.nb_inner, o.panel_ctas, o.lookahead, o.update_ctas, kv.second.ms);
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                std::get<2>(kv.first), std::get<3>(kv.first), o.nb, o.nb_inner, o.panel_ctas, o.lookahead, o.update_ctas,
+                o.tile, kv.second.ms);
     }
     const int bad = ferror(f);
     fclose(f);
@@ -156,9 +158,22 @@ int lu_tune_load(const char *path) {
         if (*p == '#' || *p == '\n' || *p == '\r' || *p == '\0') continue;
         Row r{};
         char tail = 0;
-        const int got = sscanf(p, "%d %d %d %d %d %d %d %d %d %lf %c", &r.kind, &r.dt, &r.update, &r.n, &r.o.nb,
-                               &r.o.nb_inner, &r.o.panel_ctas, &r.o.lookahead, &r.o.update_ctas, &r.ms, &tail);
-        if (got != 10) {
+        // v2 lines carry the tile shape before ms (11 fields); v1 lines have 10 and mean tile 0
+        int fields = 0;
+        for (const char *q = p; *q;) {
+            while (*q == ' ' || *q == '\t' || *q == '\n' || *q == '\r') ++q;
+            if (!*q) break;
+            ++fields;
+            while (*q && *q != ' ' && *q != '\t' && *q != '\n' && *q != '\r') ++q;
+        }
+        int got = -1;
+        if (fields == 11)
+            got = sscanf(p, "%d %d %d %d %d %d %d %d %d %d %lf %c", &r.kind, &r.dt, &r.update, &r.n, &r.o.nb,
+                         &r.o.nb_inner, &r.o.panel_ctas, &r.o.lookahead, &r.o.update_ctas, &r.o.tile, &r.ms, &tail);
+        else if (fields == 10)
+            got = 1 + sscanf(p, "%d %d %d %d %d %d %d %d %d %lf %c", &r.kind, &r.dt, &r.update, &r.n, &r.o.nb,
+                             &r.o.nb_inner, &r.o.panel_ctas, &r.o.lookahead, &r.o.update_ctas, &r.ms, &tail);
+        if (got != 11) {
             ok = false;
             break;
         }
@@ -266,6 +281,13 @@ int lu_autotune(lu_dtype dt, int n, int update, double budget_ms, lu_tune_result
         if (update != LU_UPDATE_NATIVE &&
             (rc = consider(make_opts(best.nb, 0, best.panel_ctas, best.lookahead, update, 112))) != LU_OK)
             break;
+        // the update's tile shape (DFMA tiles, emulated FP64 task length)
+        if (update == LU_UPDATE_NATIVE || update == LU_UPDATE_F64EMU)
+            for (int tl : {1, 2})
+                if ((rc = consider(make_opts(best.nb, 0, best.panel_ctas, best.lookahead, update, best.update_ctas, tl))) !=
+                    LU_OK)
+                    break;
+        if (rc != LU_OK) break;
     } while (false);
     g_bypass = false;
     if (A0) cudaFreeAsync(A0, s);

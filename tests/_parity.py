@@ -17,17 +17,24 @@ import numpy as np
 EPS64 = np.finfo(np.float64).eps
 
 
-def tie_bound(n: int) -> float:
-    return 64.0 * n * EPS64
+EPS32 = float(np.finfo(np.float32).eps)
 
 
-def oracle_parity(oracle_mod, A, ipiv_gpu, max_reruns: int = 4, threads: int | None = None):
+def tie_bound(n: int, eps: float = EPS64) -> float:
+    return 64.0 * n * eps
+
+
+def oracle_parity(oracle_mod, A, ipiv_gpu, max_reruns: int = 4, threads: int | None = None, eps: float = EPS64):
     """Compare the GPU's pivots with the oracle's under the near-tie rule.
 
+    eps: the unit roundoff of the GPU's arithmetic (FP64 by default; an FP32
+    factorization is compared with the oracle run on its FP32-rounded input,
+    where rounding can reorder candidates up to 64 n eps32 apart).
     Returns (LU of the final oracle run, list of (step, gap) re-runs).  Raises
     AssertionError at a mismatch whose gap exceeds the bound, or after
     max_reruns forced re-runs."""
     n = A.shape[0]
+    bound = tie_bound(n, eps)
     threads = oracle_mod.default_threads() if threads is None else threads
     ipiv_gpu = np.asarray(ipiv_gpu, dtype=np.int32)
     forced = np.zeros(n, dtype=np.int32)
@@ -38,9 +45,9 @@ def oracle_parity(oracle_mod, A, ipiv_gpu, max_reruns: int = 4, threads: int | N
         if bad.size == 0:
             return LUo, reruns
         j = int(bad[0])
-        assert gaps[j] <= tie_bound(n), (
+        assert gaps[j] <= bound, (
             f"pivot mismatch at step {j}: GPU row {ipiv_gpu[j]}, oracle row {pivo[j]}, "
-            f"top-2 gap {gaps[j]:.3e} > {tie_bound(n):.3e}")
+            f"top-2 gap {gaps[j]:.3e} > {bound:.3e}")
         assert len(reruns) < max_reruns, f"more than {max_reruns} near-tie re-runs: {reruns}"
         reruns.append((j, float(gaps[j])))
         forced[j] = ipiv_gpu[j]

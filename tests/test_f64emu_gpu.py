@@ -125,10 +125,11 @@ def test_f64emu_schedule_invariance_bits():
     import paper_1611_06365_gb300 as lu
     A = li.uniform(600, 600, seed=19)
     ref, piv_ref, _, _, _ = factor_gpu(A, "f64", update=lu.LU_UPDATE_F64EMU, nb=64, lookahead=-1)
-    for la, ctas, share in ((1, 8, 0), (1, 2, 0), (-1, 4, 0), (2, 8, 0), (3, 4, 0), (1, 8, -1), (2, 16, -1)):
+    for la, ctas, share, tile in ((1, 8, 0, 0), (1, 2, 0, 0), (-1, 4, 0, 0), (2, 8, 0, 0), (3, 4, 0, 0), (1, 8, -1, 0),
+                                  (2, 16, -1, 0), (1, 8, 0, 1), (1, 8, 0, 2), (2, 4, -1, 2)):
         LU, ipiv, _, _, _ = factor_gpu(A, "f64", update=lu.LU_UPDATE_F64EMU, nb=64, lookahead=la, panel_ctas=ctas,
-                                       sm_share=share)
-        assert np.array_equal(ipiv, piv_ref) and np.array_equal(LU, ref), (la, ctas, share)
+                                       sm_share=share, tile=tile)
+        assert np.array_equal(ipiv, piv_ref) and np.array_equal(LU, ref), (la, ctas, share, tile)
 
 
 def test_f64emu_full_size_n8192(oracle_mod):

@@ -60,10 +60,10 @@ def test_schedule_invariance_bits():
     """Look-ahead on/off and panel cluster sizes change the schedule, not the arithmetic."""
     A = li.uniform(600, 600, seed=9)
     ref, piv_ref, _, _, _ = factor_gpu(A, "f64", nb=32, lookahead=-1, panel_ctas=16)
-    for la, ctas in ((1, 16), (1, 4), (-1, 2), (1, 1)):
-        LU, ipiv, _, _, _ = factor_gpu(A, "f64", nb=32, lookahead=la, panel_ctas=ctas)
+    for la, ctas, tile in ((1, 16, 0), (1, 4, 0), (-1, 2, 0), (1, 1, 0), (1, 8, 1), (1, 8, 2), (2, 8, 2)):
+        LU, ipiv, _, _, _ = factor_gpu(A, "f64", nb=32, lookahead=la, panel_ctas=ctas, tile=tile)
         assert np.array_equal(ipiv, piv_ref)
-        assert np.array_equal(LU, ref)
+        assert np.array_equal(LU, ref), (la, ctas, tile)
 
 
 @pytest.mark.parametrize("dtype,update", [("f64", 0), ("f32", 0), ("f32", 1), ("f32", 2), ("f32", 3)])

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import lu_inputs as li
+from tests._parity import EPS32, oracle_parity
 from tests.gpu_util import EPS64, dev, factor_gpu
 
 pytestmark = pytest.mark.gpu
@@ -130,8 +131,13 @@ def test_batched_matches_oracle(oracle_mod, dtype):
             assert np.max(np.abs(LU - LUs[t])) <= 10 * n * EPS64 * max(1.0, np.max(np.abs(LUs[t])))
             assert np.max(np.abs(devB[t].view(-1).cpu().numpy() - xs[t])) <= 1e-9
         else:
+            # the whole pivot vector against the oracle run on the FP32-rounded matrix (near
+            # ties at FP32 resolution re-run with the GPU's choice), then the factors
+            A32 = A.astype(np.float32).astype(np.float64)
             LU = li.from_device_colmajor(devA[t], n)
-            r, a = oracle_mod.lu_residual_fro(A.astype(np.float32).astype(np.float64), LU, gp)
+            LUo32, _ = oracle_parity(oracle_mod, A32, gp, max_reruns=64, threads=1, eps=EPS32)
+            assert np.max(np.abs(LU - LUo32)) <= 64 * n * EPS32 * max(1.0, float(np.max(np.abs(LUo32)))), t
+            r, a = oracle_mod.lu_residual_fro(A32, LU, gp)
             assert r / a <= 10 * n * 1.2e-7
             assert np.max(np.abs(devB[t].view(-1).cpu().numpy() - 1.0)) <= 1e-2
 

@@ -24,7 +24,8 @@ def test_put_get_clear(L):
     lu.lu_tune_put(lu.TUNE_BATCHED, lu.LU_F32, 256, nb=32, ms=5.0)
     assert lu.lu_tune_count() == 3
     got = lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F64, 4096)
-    assert got == {"nb": 16, "nb_inner": 0, "panel_ctas": 8, "lookahead": 0, "update": 0, "update_ctas": 0, "sm_share": 0}
+    assert got == {"nb": 16, "nb_inner": 0, "panel_ctas": 8, "lookahead": 0, "update": 0, "update_ctas": 0, "sm_share": 0,
+                   "tile": 0}
     # the key includes the update kind and the exact order
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096) is None
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096, update=lu.LU_UPDATE_BF16X3)["nb"] == 128
@@ -70,6 +71,21 @@ def test_save_load_round_trip(L, tmp_path):
     assert after == before and None not in after.values()
 
 
+def test_load_accepts_both_table_versions(L, tmp_path):
+    """A v1 line (no tile field) loads with tile 0; a v2 line keeps its tile shape."""
+    p = tmp_path / "mixed.txt"
+    p.write_text("# v1 and v2 lines\n0 0 0 1024 16 0 16 1 0 5.0\n0 0 4 2048 64 0 8 1 0 2 7.5\n")
+    assert lu.lu_tune_load(p) == 2
+    assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F64, 1024)["tile"] == 0
+    got = lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F64, 2048, update=lu.LU_UPDATE_F64EMU)
+    assert got["tile"] == 2 and got["nb"] == 64
+    lu.lu_tune_put(lu.TUNE_FACTOR, lu.LU_F64, 4096, nb=32, tile=1, ms=1.0)
+    q = tmp_path / "again.txt"
+    lu.lu_tune_save(q)
+    lu.lu_tune_clear()
+    assert lu.lu_tune_load(q) == 3 and lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F64, 4096)["tile"] == 1
+
+
 @pytest.mark.parametrize("line", [
     "0 0 0 512 32 0 16 1 0",               # a field missing
     "0 0 0 512 32 0 16 1 0 2.0 extra",     # a field too many
@@ -78,6 +94,8 @@ def test_save_load_round_trip(L, tmp_path):
     "0 0 0 512 32 0 99 1 0 2.0",           # panel team 99
     "0 1 1 512 64 0 16 1 -3 2.0",          # negative update grid
     "zero 0 0 512 32 0 16 1 0 2.0",
+    "0 0 0 512 32 0 16 1 0 3 2.0",         # tile shape 3
+    "0 0 0 512 32 0 16 1 0 1 2.0 extra",   # a field too many (v2)
 ])
 def test_load_refuses_whole_file(L, tmp_path, line):
     p = tmp_path / "bad.txt"
@@ -130,6 +148,10 @@ def test_plan_info_worker_sharing_option(L):
     for bad in (-2, 2):
         with pytest.raises(lu.LuError):
             lu.lu_plan_info(lu.LU_F64, 4096, sm_share=bad)
+    assert lu.lu_plan_info(lu.LU_F64, 4096, tile=2)[1]["tile"] == 2
+    for bad in (-1, 3):
+        with pytest.raises(lu.LuError):
+            lu.lu_plan_info(lu.LU_F64, 4096, tile=bad)
 
 
 @pytest.mark.parametrize("dt,update,widths", [
