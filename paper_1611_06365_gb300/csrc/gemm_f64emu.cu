@@ -37,9 +37,10 @@
 //   warp 1   MMA issuer (one thread): 28 products x 4 K-steps of
 //            tcgen05.mma kind::f16 (M = 128, N = 32, K = 16) into one of two
 //            sets of six TMEM accumulators (2 x 6 x 32 columns);
-//   warps 2-9 epilogue: load the sub-tile's C while the MMAs run, read the
+//   warps 2-17 epilogue: load the sub-tile's C while the MMAs run, read the
 //            accumulators (tcgen05.ld), combine them in integer arithmetic,
-//            store C (two warps per TMEM lane quarter, 16 columns each).
+//            store C (four warps per TMEM lane quarter, 8 columns each: the
+//            epilogue is latency-bound, so more warps at fewer registers each).
 // Every wait is bounded; on expiry the kernel records LU_ERR_TIMEOUT, gives
 // its copies in flight one bounded wait, frees its TMEM and returns.
 #include "common.cuh"
@@ -53,7 +54,9 @@ constexpr int kEmBN = 32;
 constexpr int kEmK = 64;                       // K per slice: one 128-byte swizzle span of BF16
 constexpr int kEmAcc = 6;
 constexpr int kEmMaxSub = 8;
-constexpr int kEmThreads = 320;               // TMA, MMA, 8 epilogue warps
+constexpr int kEmEpiWarps = 16;               // epilogue warps: four per TMEM lane quarter
+constexpr int kEmEpiCols = kEmBN * 4 / kEmEpiWarps;   // sub-tile columns per epilogue warp (8)
+constexpr int kEmThreads = 64 + 32 * kEmEpiWarps;     // TMA, MMA, epilogue
 constexpr int kEmSliceA = kEmBM * kEmK * 2;    // 16 KB
 constexpr int kEmSliceB = kEmBN * kEmK * 2;    // 4 KB
 constexpr int kEmStageB = kF64Slices * kEmSliceB;
@@ -109,7 +112,7 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
         mbar_init(a_full, 1);
         mbar_init(a_empty, 1);
         for (int i = 0; i < kEmStagesB; ++i) { mbar_init(b_full0 + 8u * i, 1); mbar_init(b_empty0 + 8u * i, 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(accf0 + 8u * i, 1); mbar_init(acce0 + 8u * i, 256); mbar_init(tilef0 + 8u * i, 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(accf0 + 8u * i, 1); mbar_init(acce0 + 8u * i, 32 * kEmEpiWarps); mbar_init(tilef0 + 8u * i, 1); }
         *abort_flag = 0;
         for (int i = 0; i <= kEmStagesB; ++i) issued[i] = 0;
         *ntasks_done = 0;
@@ -237,8 +240,8 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             }
         }
     } else {
-        // epilogue: warps 2..9; warp w reads TMEM lane quarter w % 4 (thread = tile row) and
-        // handles 16 of the sub-tile's 32 columns (h: warps 2-5 the first half, 6-9 the second)
+        // epilogue: warps 2..17; warp w reads TMEM lane quarter w % 4 (thread = tile row) and
+        // handles kEmEpiCols of the sub-tile's 32 columns (h = (w - 2) / 4: the column group)
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int r = q * 32 + lane;
         for (int it = 0;; ++it) {
@@ -249,18 +252,18 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             if (t < 0) break;
             const int j = acc_sub[a] & (kEmLast - 1);
             const int row = (t % mt) * kEmBM + r;
-            const int col0 = (t / mt) * cols_task + j * kEmBN + h * 16;
+            const int col0 = (t / mt) * cols_task + j * kEmBN + h * kEmEpiCols;
             const bool rok = row < m;
             // this sub-tile's C, loaded while its products are formed
-            double cv[16];
+            double cv[kEmEpiCols];
             double *crow = C + (size_t)(rok ? row : 0);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) cv[c] = (rok && col0 + c < n) ? crow[(size_t)(col0 + c) * ldc] : 0.0;
+            for (int c = 0; c < kEmEpiCols; ++c) cv[c] = (rok && col0 + c < n) ? crow[(size_t)(col0 + c) * ldc] : 0.0;
             // the row's scale times 2^-56, the unit of the integer sum below
             const double sa56 = rok ? scaleA[a_row0 + row] * 0x1p-56 : 0.0;
             if (!mbar_wait_bounded(accf0 + 8u * a, acc_ph, bound_ns) || *abort_flag) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t accb = tmem + (uint32_t)(a * kEmAcc * kEmBN + h * 16) + ((uint32_t)(q * 32) << 16);
+            const uint32_t accb = tmem + (uint32_t)(a * kEmAcc * kEmBN + h * kEmEpiCols) + ((uint32_t)(q * 32) << 16);
             // The six accumulators combined exactly in a 64-bit integer in units of 2^-56
             // (on the integer and FP32 pipes; GB300's FP64 pipe is narrow): diagonal g <= 4
             // holds an integer multiple of 2^{-8(g+2)} below 2^24 of those units, so
@@ -268,36 +271,36 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
             // accumulator is rounded to the unit (at most 2^-57 of the scales' product; its
             // magnitude stays below 2^24 units, so a 32-bit conversion holds it).
             // |sum| < 2^63; one conversion to FP64 and one FMA then give C - A B.
-            long long vi[16];
+            long long vi[kEmEpiCols];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) vi[c] = 0;
+            for (int c = 0; c < kEmEpiCols; ++c) vi[c] = 0;
 #pragma unroll
             for (int g = 0; g < kEmAcc; ++g) {
-                float f[16];
-                tmem_ld16(accb + (uint32_t)(g * kEmBN), f);
+                float f[kEmEpiCols];
+                tmem_ld8(accb + (uint32_t)(g * kEmBN), f);
                 if (g < kEmAcc - 1) {
                     const float up = __int_as_float((127 + 8 * (g + 2)) << 23);   // 2^{8(g+2)}
                     const long long mul = 1LL << (40 - 8 * g);
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) vi[c] += (long long)__float2int_rz(f[c] * up) * mul;
+                    for (int c = 0; c < kEmEpiCols; ++c) vi[c] += (long long)__float2int_rz(f[c] * up) * mul;
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) vi[c] += (long long)__float2int_rn(f[c] * 0x1p56f);
+                    for (int c = 0; c < kEmEpiCols; ++c) vi[c] += (long long)__float2int_rn(f[c] * 0x1p56f);
                 }
             }
             // Column scales 2^eb: a nonzero converted sum has a biased exponent in [1023, 1085],
-            // so adding eb to it stays a normal number for biased eb in [1, 1984].  The 16
+            // so adding eb to it stays a normal number for biased eb in [1, 1984].  The warp's
             // columns are the same for every lane, so the choice is made once for all of them
             // (a branch per column would be if-converted and issue both paths).
             bool fast = true;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < kEmEpiCols; ++c) {
                 const int eb = (int)((__double_as_longlong(__ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])) >> 52) & 0x7ff);
                 fast = fast && eb >= 1 && eb <= 1984;
             }
             if (fast) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
+                for (int c = 0; c < kEmEpiCols; ++c) {
                     const int eb = (int)((__double_as_longlong(__ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])) >> 52) & 0x7ff);
                     const long long db = __double_as_longlong(__ll2double_rn(vi[c]));
                     cv[c] = fma(-__longlong_as_double(db == 0 ? 0 : db + (long long)(eb - 1023) * (1LL << 52)), sa56, cv[c]);
@@ -306,14 +309,14 @@ gemm_update_f64emu(int m, int n, const __grid_constant__ CUtensorMap mapA, int a
                 // the scales' product first: the converted sum times a column scale above 2^961
                 // may overflow
 #pragma unroll
-                for (int c = 0; c < 16; ++c)
+                for (int c = 0; c < kEmEpiCols; ++c)
                     cv[c] = fma(-(sa56 * __ldg(&scaleB[b_col0 + min(col0 + c, n - 1)])), __ll2double_rn(vi[c]), cv[c]);
             }
             // accumulators read: the MMAs of the sub-tile after next may start
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8u * a) : "memory");
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < kEmEpiCols; ++c)
                 if (rok && col0 + c < n && (lshift < 0 || row >= col0 + c + lshift)) crow[(size_t)(col0 + c) * ldc] = cv[c];
         }
     }
