@@ -844,6 +844,41 @@ def run_case(args):
     elif args.case == "peaks":
         print(json.dumps(measure_peaks(dev)), flush=True)
         return
+    elif args.case == "cholesky":
+        # A = L L^T of an SPD matrix of order --n ((B + B^T) / 2 + n I, B uniform [-1, 1)), with
+        # the DFMA and the emulated FP64 updates: n^3 / 3 flop, CUDA events around each call,
+        # the best of two after a warm-up, and a randomized residual probe of each factor
+        import numpy as np
+        n = args.n
+        B = li.uniform_colmajor_torch(n, n, 20161106 + 9100, dev, torch.float64)
+        A0 = (B + B.t()) / 2
+        del B
+        A0.diagonal().add_(float(n))
+        A = torch.empty_like(A0)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        out = {"case": "cholesky", "n": n, "matrix": "(B + B^T)/2 + n I, B uniform [-1, 1)"}
+        for name, upd, la in (("dfma", lu.LU_UPDATE_NATIVE, 0), ("f64emu", lu.LU_UPDATE_F64EMU, 0),
+                              ("f64emu_no_lookahead", lu.LU_UPDATE_F64EMU, -1)):
+            best = None
+            for rep in range(3):
+                A.copy_(A0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                lu.lu_cholesky(A, info, n, update=upd, lookahead=la)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                if rep > 0:
+                    best = ms if best is None else min(best, ms)
+            L = torch.tril(A.t())
+            w = torch.from_numpy(np.random.default_rng(5).standard_normal(n)).to(dev)
+            r = A0.t() @ w - L @ (L.t() @ w)
+            out[name] = {"ms": best, "gflops": n ** 3 / 3.0 / (best / 1e3) / 1e9, "info": int(info.item()),
+                         "residual_probe": float(r.norm() / (A0.norm() * w.norm()))}
+            del L, r
+        print(json.dumps(out), flush=True)
+        return
     elif args.case == "emu_update":
         # the emulated FP64 update alone: C 8192 x 8192 FP64 (512 MiB, larger than L2), K = 64
         m = n = 8192
@@ -921,7 +956,7 @@ def make_parser():
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
                                        "fp8_large", "solve_f32", "torch_context", "peaks", "c3_grid", "probe_dfma",
-                                       "emu_update"],
+                                       "emu_update", "cholesky"],
                     default=None,
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")
