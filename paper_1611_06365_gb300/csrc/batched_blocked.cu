@@ -42,7 +42,6 @@ struct BBShared {
     __align__(16) T U12[kBBMaxN][LS];                    // column c of U12: its NB entries
     __align__(16) T wst[2][kBBWarps][NB];                // each warp's candidate row (double-buffered)
     __align__(16) T jst[2][NB];                          // row j of the panel
-    T wrcp[2][kBBWarps];                                 // FP64: RN(1 / pivot) of each warp's candidate
     unsigned long long red_key[2][kBBWarps];
     int red_idx[2][kBBWarps];
     int piv[NB];                                         // panel-local pivot rows
@@ -87,23 +86,13 @@ __device__ __forceinline__ void bb_argmax_t(unsigned long long &key, int &idx) {
 // Column step LJ of the panel on this thread's row i (panel-local): scaling
 // and rank-1 update for i > LJ, and the candidate key of column LJ+1.
 template <typename T, int NB, int LJ>
-__device__ __forceinline__ void bb_rank1(T (&a)[NB], const T *__restrict__ urow, T pv, T rcp, bool zero, int i, bool own,
-                                         int w, unsigned long long &best, int &bidx) {
+__device__ __forceinline__ void bb_rank1(T (&a)[NB], const T *__restrict__ urow, T pv, bool zero, int i, bool own, int w,
+                                         unsigned long long &best, int &bidx) {
     using V = typename BBVec<T>::type;
     constexpr int VEC = 16 / sizeof(T);
     const bool act = own && i > LJ && !zero;
     if (act) {
-        // FP64 with 16-column panels (the tuned width): the correctly rounded quotient from
-        // the pivot's reciprocal (Markstein's correction, three FP64-pipe operations against
-        // about ten for the division), the IEEE division where an operand is outside its
-        // safe range; same bits.  (32-column FP64 panels keep the division: the extra live
-        // values would spill their register tile.)
-        T l;
-        if constexpr (sizeof(T) == 8 && NB <= 16) {
-            l = lu_div_safe(a[LJ], lu_div_range<T>::in(pv)) ? lu_div_fast(a[LJ], pv, rcp) : a[LJ] / pv;
-        } else {
-            l = a[LJ] / pv;
-        }
+        const T l = a[LJ] / pv;
         a[LJ] = l;
 #pragma unroll
         for (int q = (LJ + 1) / VEC; q < NB / VEC; ++q) {
@@ -124,7 +113,7 @@ __device__ __forceinline__ void bb_rank1(T (&a)[NB], const T *__restrict__ urow,
 
 #define LU_BB_CASE(L)                                                                                   \
     case (L):                                                                                           \
-        if constexpr ((L) < NB) bb_rank1<T, NB, ((L) < NB ? (L) : 0)>(a, urow, pv, rcp, zero, tid, own, w, best, bidx); \
+        if constexpr ((L) < NB) bb_rank1<T, NB, ((L) < NB ? (L) : 0)>(a, urow, pv, zero, tid, own, w, best, bidx); \
         break;
 #define LU_BB_CASE4(L) LU_BB_CASE(L) LU_BB_CASE((L) + 1) LU_BB_CASE((L) + 2) LU_BB_CASE((L) + 3)
 #define LU_BB_CASE16(L) LU_BB_CASE4(L) LU_BB_CASE4((L) + 4) LU_BB_CASE4((L) + 8) LU_BB_CASE4((L) + 12)
@@ -157,7 +146,6 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
             if (bidx != INT_MAX && lane == (bidx & 31)) {
 #pragma unroll
                 for (int q = 0; q < NB / VEC; ++q) reinterpret_cast<V *>(S.wst[par][warp])[q] = reinterpret_cast<const V *>(a)[q];
-                if constexpr (sizeof(T) == 8 && NB <= 16) S.wrcp[par][warp] = T(1) / a[lj];   // one division per warp
             }
             if (tid == lj) {
 #pragma unroll
@@ -173,7 +161,6 @@ __device__ int bb_factor(BBShared<T, NB> &S, T *__restrict__ A, int lda, int n, 
             const T *urow = valid ? S.wst[par][cr >> 5] : S.jst[par];
             const T *drow = S.jst[par];
             const T pv = urow[lj];
-            const T rcp = (sizeof(T) == 8 && NB <= 16 && valid) ? S.wrcp[par][cr >> 5] : T(1);
             const bool zero = (pv == T(0));
             if (tid == 0) S.piv[lj] = zero ? lj : p;
             if (zero && info == 0) info = k + lj + 1;
