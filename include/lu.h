@@ -225,7 +225,10 @@ typedef struct {
                             refinement) is predicted to take fallback_ratio times the first
                             factorization's measured time; 0 = the ratio measured by an earlier
                             fallback of the same order in this process, else 4 (emulated FP64
-                            update) or 32 (DFMA update); < 0 = no cost model */
+                            update) or 32 (DFMA update); < 0 = no cost model.  With the model
+                            on, a matrix whose condition estimate (report.cond_est) times
+                            eps32 sqrt(n) exceeds 1/4 goes to the fallback as soon as classic
+                            refinement stalls */
 } lu_mixed_opts;
 
 /* Result of lu_solve_mixed (host memory, filled before the call returns). */
@@ -249,6 +252,9 @@ typedef struct {
                             predicted or spent refinement time reached the predicted cost of
                             the FP64 fallback */
     double t_fallback_ms;  /* host time of the FP64 fallback (factorization and refinement), 0 if none */
+    double cond_est;     /* ||A||_inf ||M^{-1} r||_inf / ||r||_inf for one right-hand side r uniform in
+                            [-1, 1) and M the first factorization: a lower estimate of the condition
+                            number (0 when the first factorization was not made or was singular) */
 } lu_mixed_report;
 
 /*

@@ -71,7 +71,7 @@ class MixedReport(ctypes.Structure):
                 ("fell_back", ctypes.c_int), ("info", ctypes.c_int), ("backward_error", ctypes.c_double),
                 ("t_factor_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
                 ("forward_error_est", ctypes.c_double), ("f32_refactor", ctypes.c_int), ("cost_stop", ctypes.c_int),
-                ("t_fallback_ms", ctypes.c_double)]
+                ("t_fallback_ms", ctypes.c_double), ("cond_est", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -183,6 +183,26 @@ cudaError_t launch_absmax_scaled_f32(int n, int nrhs, const float *D32, int ldd,
     return cudaGetLastError();
 }
 
+// R32 := n values uniform in [-1, 1) from a counter hash of (seed, i): splitmix64
+// (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014), top 24 bits.  The right-hand side of the condition estimate.
+__global__ void fill_probe_kernel(int n, unsigned long long seed, float *__restrict__ R32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        R32[i] = (float)(z >> 40) * 0x1p-23f - 1.0f;
+    }
+}
+
+cudaError_t launch_fill_probe(int n, unsigned long long seed, float *R32, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    fill_probe_kernel<<<grid_for(n), 256, 0, s>>>(n, seed, R32);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vecmax(int n, const double *v, unsigned long long *out, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess || n <= 0) return e;

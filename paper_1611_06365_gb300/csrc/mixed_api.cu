@@ -27,7 +27,10 @@
 // then costs at most the factorization plus twice C), and a rung stops as
 // soon as its own contraction predicts it would pass that budget: classic
 // refinement from the observed ratio of successive backward errors, the FP32
-// refactorization from its predicted cost, GMRES-IR from the time left.
+// refactorization from its predicted cost, GMRES-IR from the time left.  With
+// the cost model on, a condition estimate (one solve with the first factors and
+// a random right-hand side) sends a matrix whose estimate times eps32 sqrt(n)
+// exceeds 1/4 straight to the fallback once classic refinement stalls.
 // Forward-error estimate: the correction one more refinement step would make,
 // relative to the solution: max_q ||d_q||_inf / ||x_q||_inf with d = M^{-1} r,
 // r = b - A x in FP64 and M the factors of the rung that finished (the
@@ -38,6 +41,7 @@
 #include "common.cuh"
 #include <algorithm>
 #include <chrono>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -61,6 +65,7 @@ cudaError_t launch_residual(int n, int nrhs, const double *A, int lda, const dou
                             double *R, int ldr, double *part, unsigned long long *rmax, cudaStream_t s);
 cudaError_t launch_absmax(int n, int nrhs, const double *V, int ldv, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_vecmax(int n, const double *v, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_fill_probe(int n, unsigned long long seed, float *R32, cudaStream_t s);
 cudaError_t launch_to_f32_scaled(int n, int nrhs, const double *R, int ldr, const unsigned long long *rmax, float *R32,
                                  int ldr32, cudaStream_t s);
 cudaError_t launch_axpy_scaled(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax, double *X, int ldx,
@@ -255,6 +260,21 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     const double anorm = bits_to_double(hn[0]);
     std::vector<double> bnorm(nrhs);
     for (int q = 0; q < nrhs; ++q) bnorm[q] = bits_to_double(hn[1 + 2 * nrhs + q]);
+    // condition estimate: one solve with the first factors and a random right-hand side
+    if (!fp64_only && hinfo == 0) {
+        LU_CUDA_TRY(launch_fill_probe(n, 20161106ull + (unsigned long long)n, R32, s));
+        rc = solve_f32_perm(n, 1, A32, ld32, perm, R32, n, s, Dinv);
+        if (rc != LU_OK) return rc;
+        unsigned long long *kbuf = nullptr;   // [0] = 0: scale 1; [1]: max |M^{-1} r|
+        LU_CUDA_TRY(ws.get(&kbuf, 2));
+        LU_CUDA_TRY(cudaMemsetAsync(kbuf, 0, 2 * sizeof(unsigned long long), s));
+        LU_CUDA_TRY(launch_absmax_scaled_f32(n, 1, R32, n, kbuf, kbuf + 1, s));
+        unsigned long long hk = 0;
+        LU_CUDA_TRY(cudaMemcpyAsync(&hk, kbuf + 1, sizeof(hk), cudaMemcpyDeviceToHost, s));
+        LU_CUDA_TRY(cudaStreamSynchronize(s));
+        r.cond_est = anorm * bits_to_double(hk);   // ||r||_inf is 1 to within 2 / n
+        if (log_on) fprintf(stderr, "lu_solve_mixed: condition estimate %.3e\n", r.cond_est);
+    }
 
     // rung 0: classic refinement from x = 0, r = b
     LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
@@ -313,7 +333,16 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     // rung 0, second part: factors of the tensor-core update too coarse for this
     // matrix (refinement stalled) -- refactor with the FP32 update (FP32-accurate
     // factors) and refine on from the current solution
-    const bool refactor_ok = !done && !fp64_only && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0);
+    // too ill-conditioned for FP32 factors: when the estimate times eps32 sqrt(n) (the size of
+    // an FP32 factorization's error relative to A, up to its growth) passes 1/4, neither the
+    // FP32 refactorization nor GMRES-IR is tried after classic refinement stalls
+    const double cond_meter = r.cond_est * (double)FLT_EPSILON * std::sqrt((double)n);
+    const bool hopeless = cost_on && !done && !fp64_only && cond_meter > 0.25;
+    if (hopeless) {
+        r.cost_stop = 1;
+        if (log_on) fprintf(stderr, "lu_solve_mixed: condition estimate x eps32 sqrt(n) = %.3g: straight to FP64\n", cond_meter);
+    }
+    const bool refactor_ok = !done && !fp64_only && !hopeless && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0);
     // the refactorization's own predicted cost decides (a classic rung the cost model
     // ended early is no reason to skip it: FP32 factors may contract where these did not)
     const bool refactor_too_dear = refactor_ok && cost_on && ms_since(t_ref) + ratio_get(n, 2, 1.5) * tf_ms >= c64;
@@ -340,7 +369,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     // rung 1: GMRES-IR with the FP32 factors as preconditioner
     const double gm_budget = cost_on ? c64 - ms_since(t_ref) : 0.0;
     if (!done && hinfo == 0 && allow_gmres && !fp64_only && cost_on && gm_budget <= 0.0) r.cost_stop = 1;
-    if (!done && hinfo == 0 && allow_gmres && !fp64_only && !(cost_on && gm_budget <= 0.0)) {
+    if (!done && hinfo == 0 && allow_gmres && !fp64_only && !hopeless && !(cost_on && gm_budget <= 0.0)) {
         r.rung = 1;
         int outer = 0, inner = 0;
         rc = gmres_ir(n, nrhs, dA, lda, dB, ldb, dX, ldx, A32, ld32, perm, anorm, bnorm.data(), tol, max_iter, restart, &outer,

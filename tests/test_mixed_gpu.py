@@ -229,6 +229,26 @@ def test_mixed_forced_fallback_path(oracle_mod):
     assert oracle_mod.backward_error(A, X, B) <= 1e-15
 
 
+def test_mixed_condition_estimate_and_hopeless_matrices(oracle_mod):
+    """The report's condition estimate grows with kappa (a lower estimate, from one
+    random right-hand side); with the cost model on, a matrix far too ill-conditioned
+    for FP32 factors skips the FP32 refactorization and GMRES-IR once classic
+    refinement stalls, and the FP64 fallback reaches the target."""
+    n = 400
+    ests = []
+    for kappa in (1e2, 1e6):
+        A = li.kappa_matrix(n, kappa, seed=li.BASE_SEED + 2500, k=n)
+        _, rep = _mixed(A, A @ np.ones((n, 1)), fallback_ratio=-1.0)
+        ests.append(rep.cond_est)
+    assert 1.0 <= ests[0] < ests[1] and ests[1] > 100 * ests[0], ests
+    A = li.kappa_matrix(n, 1e12, seed=li.BASE_SEED + 2200, k=n)
+    B = A @ np.ones((n, 1))
+    X, rep = _mixed(A, B, fallback_ratio=1e9)   # a generous budget: only the condition rule can stop
+    assert rep.cond_est * np.finfo(np.float32).eps * np.sqrt(n) > 0.25
+    assert rep.rung == 2 and rep.cost_stop == 1 and rep.f32_refactor == 0 and rep.gmres_iters == 0, rep.as_dict()
+    assert oracle_mod.backward_error(A, X, B) <= 1e-14
+
+
 def test_mixed_cost_model_takes_the_fallback_when_refinement_would_cost_more(oracle_mod):
     """With the FP64 fallback predicted to cost next to nothing, the ladder stops
     refining as soon as it has a contraction rate to predict from, skips the
