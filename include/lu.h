@@ -227,7 +227,7 @@ typedef struct {
                             fallback of the same order in this process, else 4 (emulated FP64
                             update) or 32 (DFMA update); < 0 = no cost model.  With the model
                             on, a matrix whose condition estimate (report.cond_est) times
-                            eps32 sqrt(n) exceeds 1/4 goes to the fallback as soon as classic
+                            eps32 exceeds 16 goes to the fallback as soon as classic
                             refinement stalls */
 } lu_mixed_opts;
 

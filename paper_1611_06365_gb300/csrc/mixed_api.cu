@@ -29,8 +29,8 @@
 // refinement from the observed ratio of successive backward errors, the FP32
 // refactorization from its predicted cost, GMRES-IR from the time left.  With
 // the cost model on, a condition estimate (one solve with the first factors and
-// a random right-hand side) sends a matrix whose estimate times eps32 sqrt(n)
-// exceeds 1/4 straight to the fallback once classic refinement stalls.
+// a random right-hand side) sends a matrix whose estimate times eps32 exceeds 16
+// straight to the fallback once classic refinement stalls.
 // Forward-error estimate: the correction one more refinement step would make,
 // relative to the solution: max_q ||d_q||_inf / ||x_q||_inf with d = M^{-1} r,
 // r = b - A x in FP64 and M the factors of the rung that finished (the
@@ -333,14 +333,16 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     // rung 0, second part: factors of the tensor-core update too coarse for this
     // matrix (refinement stalled) -- refactor with the FP32 update (FP32-accurate
     // factors) and refine on from the current solution
-    // too ill-conditioned for FP32 factors: when the estimate times eps32 sqrt(n) (the size of
-    // an FP32 factorization's error relative to A, up to its growth) passes 1/4, neither the
-    // FP32 refactorization nor GMRES-IR is tried after classic refinement stalls
-    const double cond_meter = r.cond_est * (double)FLT_EPSILON * std::sqrt((double)n);
-    const bool hopeless = cost_on && !done && !fp64_only && cond_meter > 0.25;
+    // too ill-conditioned for FP32 factors: when the estimate times eps32 passes 16, neither the
+    // FP32 refactorization nor GMRES-IR is tried after classic refinement stalls (measured at
+    // n = 16384 on products of Householder reflectors: the estimate is 17 to 130 times
+    // kappa_2; kappa_2 = 1e5 gives 1.5 and converges through the refactorization and GMRES-IR,
+    // kappa_2 = 1e8 gives 199 and does not)
+    const double cond_meter = r.cond_est * (double)FLT_EPSILON;
+    const bool hopeless = cost_on && !done && !fp64_only && cond_meter > 16.0;
     if (hopeless) {
         r.cost_stop = 1;
-        if (log_on) fprintf(stderr, "lu_solve_mixed: condition estimate x eps32 sqrt(n) = %.3g: straight to FP64\n", cond_meter);
+        if (log_on) fprintf(stderr, "lu_solve_mixed: condition estimate x eps32 = %.3g: straight to FP64\n", cond_meter);
     }
     const bool refactor_ok = !done && !fp64_only && !hopeless && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0);
     // the refactorization's own predicted cost decides (a classic rung the cost model

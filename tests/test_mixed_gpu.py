@@ -244,7 +244,7 @@ def test_mixed_condition_estimate_and_hopeless_matrices(oracle_mod):
     A = li.kappa_matrix(n, 1e12, seed=li.BASE_SEED + 2200, k=n)
     B = A @ np.ones((n, 1))
     X, rep = _mixed(A, B, fallback_ratio=1e9)   # a generous budget: only the condition rule can stop
-    assert rep.cond_est * np.finfo(np.float32).eps * np.sqrt(n) > 0.25
+    assert rep.cond_est * np.finfo(np.float32).eps > 16
     assert rep.rung == 2 and rep.cost_stop == 1 and rep.f32_refactor == 0 and rep.gmres_iters == 0, rep.as_dict()
     assert oracle_mod.backward_error(A, X, B) <= 1e-14
 
