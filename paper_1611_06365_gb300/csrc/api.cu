@@ -1215,7 +1215,13 @@ int f32_diag_inverse(int n, const float *LU, int lda, float *Dinv, cudaStream_t 
     LU_CUDA_TRY(launch_diag_inverse<float>(LU, lda, n, Dinv, s));
     return LU_OK;
 }
-int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s) {
-    return solve_impl<double>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s);
+int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s,
+                   const double *Dinv) {
+    return solve_impl<double>(n, nrhs, LU, lda, nullptr, perm, B, ldb, lu_spin_bound_ns(nullptr), s, Dinv);
+}
+size_t f64_diag_inverse_elems(int n) { return trsv_inverse_elems<double>(n); }
+int f64_diag_inverse(int n, const double *LU, int lda, double *Dinv, cudaStream_t s) {
+    LU_CUDA_TRY(launch_diag_inverse<double>(LU, lda, n, Dinv, s));
+    return LU_OK;
 }
 }  // namespace lu

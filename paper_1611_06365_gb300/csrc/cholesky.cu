@@ -39,7 +39,8 @@ cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int o
 int f64emu_kpad();
 int f64emu_box_rows();
 int f64emu_box_cols();
-int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s);
+int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s,
+                   const double *Dinv = nullptr);
 int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s,
                    const float *Dinv = nullptr);
 cudaError_t launch_iota(int *v, int n, cudaStream_t s);

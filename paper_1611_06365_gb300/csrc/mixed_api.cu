@@ -56,8 +56,11 @@ int factor_f32_internal(int n, float *A, int lda, int *ipiv, int *info, int *per
 int factor_f64_internal(int n, double *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s);
 int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s,
                    const float *Dinv = nullptr);
-int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s);
+int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s,
+                   const double *Dinv = nullptr);
 size_t f32_diag_inverse_elems(int n);
+size_t f64_diag_inverse_elems(int n);
+int f64_diag_inverse(int n, const double *LU, int lda, double *Dinv, cudaStream_t s);
 int f32_diag_inverse(int n, const float *LU, int lda, float *Dinv, cudaStream_t s);
 cudaError_t launch_cast_rowsum(int n, const double *A, int lda, float *A32, int lda32, double *rowsum, cudaStream_t s);
 size_t residual_workspace_doubles(int n, int nrhs);
@@ -284,6 +287,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
     double eta = 1.0, ferr = INFINITY;
     bool factors64 = false;
     double *A64 = nullptr;
+    double *Dinv64 = nullptr;   // inverses of the FP64 factors' diagonal blocks (refinement solves)
     int *perm64 = nullptr;
     std::vector<double> hist;
     bool done = false;
@@ -326,24 +330,24 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
         }
         return LU_OK;
     };
-    if (hinfo == 0 && !fp64_only) {
+    // too ill-conditioned for FP32 factors: when the estimate times eps32 passes 16, no
+    // low-precision rung is tried (measured at
+    // n = 16384 on products of Householder reflectors: the estimate is 17 to 130 times
+    // kappa_2; kappa_2 = 1e5 gives 1.5 and converges through the refactorization and GMRES-IR,
+    // kappa_2 = 1e8 gives 199 and does not)
+    const double cond_meter = r.cond_est * (double)FLT_EPSILON;
+    const bool hopeless = cost_on && !fp64_only && hinfo == 0 && cond_meter > 16.0;
+    if (hopeless) {
+        r.cost_stop = 1;
+        if (log_on) fprintf(stderr, "lu_solve_mixed: condition estimate x eps32 = %.3g: straight to FP64\n", cond_meter);
+    }
+    if (hinfo == 0 && !fp64_only && !hopeless) {
         rc = classic();
         if (rc != LU_OK) return rc;
     }
     // rung 0, second part: factors of the tensor-core update too coarse for this
     // matrix (refinement stalled) -- refactor with the FP32 update (FP32-accurate
     // factors) and refine on from the current solution
-    // too ill-conditioned for FP32 factors: when the estimate times eps32 passes 16, neither the
-    // FP32 refactorization nor GMRES-IR is tried after classic refinement stalls (measured at
-    // n = 16384 on products of Householder reflectors: the estimate is 17 to 130 times
-    // kappa_2; kappa_2 = 1e5 gives 1.5 and converges through the refactorization and GMRES-IR,
-    // kappa_2 = 1e8 gives 199 and does not)
-    const double cond_meter = r.cond_est * (double)FLT_EPSILON;
-    const bool hopeless = cost_on && !done && !fp64_only && cond_meter > 16.0;
-    if (hopeless) {
-        r.cost_stop = 1;
-        if (log_on) fprintf(stderr, "lu_solve_mixed: condition estimate x eps32 = %.3g: straight to FP64\n", cond_meter);
-    }
     const bool refactor_ok = !done && !fp64_only && !hopeless && update != LU_UPDATE_NATIVE && !(opts && opts->f32_refactor < 0);
     // the refactorization's own predicted cost decides (a classic rung the cost model
     // ended early is no reason to skip it: FP32 factors may contract where these did not)
@@ -410,6 +414,9 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
         o64.update = (opts && opts->fallback_native) ? LU_UPDATE_NATIVE : LU_UPDATE_F64EMU;
         rc = factor_f64_internal(n, A64, n, ipiv64, info64, perm64, &o64, s);
         if (rc != LU_OK) return rc;
+        if (!Dinv64) LU_CUDA_TRY(ws.get(&Dinv64, f64_diag_inverse_elems(n)));
+        rc = f64_diag_inverse(n, A64, n, Dinv64, s);
+        if (rc != LU_OK) return rc;
         LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
         LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
                                       cudaMemcpyDeviceToDevice, s));
@@ -417,7 +424,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
         LU_CUDA_TRY(ws.get(&D, (size_t)n * nrhs));
         for (int it = 0; it < 5; ++it) {
             LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-            rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
+            rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s, Dinv64);
             if (rc != LU_OK) return rc;
             LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));   // X += D
             LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
@@ -435,12 +442,15 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             o64.update = LU_UPDATE_NATIVE;
             rc = factor_f64_internal(n, A64, n, ipiv64, info64, perm64, &o64, s);
             if (rc != LU_OK) return rc;
+            if (!Dinv64) LU_CUDA_TRY(ws.get(&Dinv64, f64_diag_inverse_elems(n)));
+            rc = f64_diag_inverse(n, A64, n, Dinv64, s);
+            if (rc != LU_OK) return rc;
             LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
             LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
                                           cudaMemcpyDeviceToDevice, s));
             for (int it = 0; it < 5; ++it) {
                 LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-                rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
+                rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s, Dinv64);
                 if (rc != LU_OK) return rc;
                 LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));
                 LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
@@ -466,7 +476,7 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             double *D = nullptr;
             LU_CUDA_TRY(ws.get(&D, (size_t)n * nrhs));
             LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-            rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s);
+            rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s, Dinv64);
             if (rc != LU_OK) return rc;
             LU_CUDA_TRY(launch_absmax(n, nrhs, D, n, d_dmax, s));
         } else {

@@ -418,8 +418,9 @@ size_t trsv_workspace_ints(int n, int nrhs) {
 // threads per block; thread j forms column j by substitution (IEEE division).
 template <typename T>
 __global__ void __launch_bounds__(kTB) diag_inverse_kernel(const T *__restrict__ LU, int lda, int n, T *__restrict__ Dinv) {
-    __shared__ T D[kTB][kTB + 1];    // D[c][r]
-    __shared__ T Xs[kTB][kTB + 1];   // Xs[c][r]: the inverse
+    extern __shared__ __align__(16) unsigned char di_smem[];
+    T(*D)[kTB + 1] = reinterpret_cast<T(*)[kTB + 1]>(di_smem);   // D[c][r]
+    T(*Xs)[kTB + 1] = D + kTB;                                     // Xs[c][r]: the inverse
     const int nblk = (n + kTB - 1) / kTB;
     const bool lower = blockIdx.x < (unsigned)nblk;
     const int I = lower ? blockIdx.x : blockIdx.x - nblk;
@@ -458,7 +459,10 @@ size_t trsv_inverse_elems(int n) { return (size_t)2 * lu_ceil_div(std::max(n, 1)
 template <typename T>
 cudaError_t launch_diag_inverse(const T *LU, int lda, int n, T *Dinv, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    diag_inverse_kernel<T><<<2 * lu_ceil_div(n, kTB), kTB, 0, s>>>(LU, lda, n, Dinv);
+    const size_t smem = sizeof(T) * 2 * kTB * (kTB + 1);
+    cudaError_t e = cudaFuncSetAttribute(diag_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    diag_inverse_kernel<T><<<2 * lu_ceil_div(n, kTB), kTB, smem, s>>>(LU, lda, n, Dinv);
     lu_count_launch();
     return cudaGetLastError();
 }
@@ -641,6 +645,8 @@ template cudaError_t launch_trsv_pair<double>(const double *, int, int, int, dou
 template cudaError_t launch_trsv_pair<float>(const float *, int, int, int, float *, int, int *, int *, long long, int,
                                              cudaStream_t, const float *);
 template cudaError_t launch_diag_inverse<float>(const float *, int, int, float *, cudaStream_t);
+template cudaError_t launch_diag_inverse<double>(const double *, int, int, double *, cudaStream_t);
 template size_t trsv_inverse_elems<float>(int);
+template size_t trsv_inverse_elems<double>(int);
 
 }  // namespace lu
