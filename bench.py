@@ -369,6 +369,10 @@ def run_ours(args):
         if not args.no_autotune:
             tuned["fp64_n512"] = lu.lu_autotune(lu.LU_F64, 512)
         small = small_case(dev)
+    chol = None
+    if rank == 0 and not args.skip_chol:
+        # Cholesky on the same look-ahead schedule (n = 16384: DFMA and emulated updates)
+        chol = cholesky_measure(16384, dev, 2)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -382,6 +386,7 @@ def run_ours(args):
                    "autotuned": tuned or None},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "fp64_emulated": emu, "time_to_solution": tts, "batched": batched, "latency_n512": small,
+        "cholesky": chol,
     }
     if rank == 0 and not args.skip_cpu:
         dt, threads = oracle_sample(args.cpu_n, SEED)
@@ -733,6 +738,49 @@ def fp8_large(args, dev):
         torch.cuda.empty_cache()
 
 
+def cholesky_measure(n, dev, reps):
+    """A = L L^T of an SPD matrix of order n ((B + B^T) / 2 + n I, B uniform [-1, 1)), with the
+    DFMA and the emulated FP64 updates (and the emulated one without look-ahead): n^3 / 3 flop,
+    CUDA events around each call, the best of reps - 1 after a warm-up, and a randomized residual
+    probe of each factor."""
+    import numpy as np
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    B = li.uniform_colmajor_torch(n, n, 20161106 + 9100, dev, torch.float64)
+    A0 = (B + B.t()) / 2
+    del B
+    A0.diagonal().add_(float(n))
+    A = torch.empty_like(A0)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {"n": n, "matrix": "(B + B^T)/2 + n I, B uniform [-1, 1)"}
+    for name, upd, la in (("dfma", lu.LU_UPDATE_NATIVE, 0), ("f64emu", lu.LU_UPDATE_F64EMU, 0),
+                          ("f64emu_no_lookahead", lu.LU_UPDATE_F64EMU, -1)):
+        best = None
+        for rep in range(reps):
+            A.copy_(A0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lu.lu_cholesky(A, info, n, update=upd, lookahead=la)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if rep > 0 or reps == 1:
+                best = ms if best is None else min(best, ms)
+        L = torch.tril(A.t())
+        w = torch.from_numpy(np.random.default_rng(5).standard_normal(n)).to(dev)
+        r = A0.t() @ w - L @ (L.t() @ w)
+        out[name] = {"ms": best, "gflops": n ** 3 / 3.0 / (best / 1e3) / 1e9, "info": int(info.item()),
+                     "residual_probe": float(r.norm() / (A0.norm() * w.norm()))}
+        del L, r
+    del A, A0
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_peaks(dev):
     """ALU peaks on this GPU: DFMA, DMMA and FFMA throughput probes (lu_peak_probe), each
     a launch of about a second after a short warm-up, with the SM clocks sampled
@@ -845,39 +893,7 @@ def run_case(args):
         print(json.dumps(measure_peaks(dev)), flush=True)
         return
     elif args.case == "cholesky":
-        # A = L L^T of an SPD matrix of order --n ((B + B^T) / 2 + n I, B uniform [-1, 1)), with
-        # the DFMA and the emulated FP64 updates: n^3 / 3 flop, CUDA events around each call,
-        # the best of two after a warm-up, and a randomized residual probe of each factor
-        import numpy as np
-        n = args.n
-        B = li.uniform_colmajor_torch(n, n, 20161106 + 9100, dev, torch.float64)
-        A0 = (B + B.t()) / 2
-        del B
-        A0.diagonal().add_(float(n))
-        A = torch.empty_like(A0)
-        info = torch.zeros(1, dtype=torch.int32, device=dev)
-        out = {"case": "cholesky", "n": n, "matrix": "(B + B^T)/2 + n I, B uniform [-1, 1)"}
-        for name, upd, la in (("dfma", lu.LU_UPDATE_NATIVE, 0), ("f64emu", lu.LU_UPDATE_F64EMU, 0),
-                              ("f64emu_no_lookahead", lu.LU_UPDATE_F64EMU, -1)):
-            best = None
-            for rep in range(3):
-                A.copy_(A0)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                lu.lu_cholesky(A, info, n, update=upd, lookahead=la)
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1)
-                if rep > 0:
-                    best = ms if best is None else min(best, ms)
-            L = torch.tril(A.t())
-            w = torch.from_numpy(np.random.default_rng(5).standard_normal(n)).to(dev)
-            r = A0.t() @ w - L @ (L.t() @ w)
-            out[name] = {"ms": best, "gflops": n ** 3 / 3.0 / (best / 1e3) / 1e9, "info": int(info.item()),
-                         "residual_probe": float(r.norm() / (A0.norm() * w.norm()))}
-            del L, r
-        print(json.dumps(out), flush=True)
+        print(json.dumps(dict({"case": "cholesky"}, **cholesky_measure(args.n, dev, 3))), flush=True)
         return
     elif args.case == "emu_update":
         # the emulated FP64 update alone: C 8192 x 8192 FP64 (512 MiB, larger than L2), K = 64
@@ -946,6 +962,7 @@ def make_parser():
                     help="skip the factorization with the emulated FP64 update")
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
     ap.add_argument("--skip-batched", dest="skip_batched", action="store_true")
+    ap.add_argument("--skip-chol", dest="skip_chol", action="store_true", help="leave out the Cholesky line")
     ap.add_argument("--skip-small", dest="skip_small", action="store_true",
                     help="skip the n = 512 latency measurement")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
