@@ -628,11 +628,13 @@ def time_to_solution(args, dev):
     plan_bo = None
     cases = []
     tc_roof = None
-    for kappa in MIXED_KAPPAS:
+    kappas = [float(k) for k in args.c3_kappas.split(",")] if args.c3_kappas else MIXED_KAPPAS
+    nrhs_list = [int(q) for q in args.c3_nrhs.split(",")] if args.c3_nrhs else MIXED_NRHS
+    for kappa in kappas:
         A = li.kappa_from_factors_torch(Q_u, Vt, kappa)
         anorm = A.abs().sum(0).max()
         fp64 = None
-        for nrhs in MIXED_NRHS:
+        for nrhs in sorted(nrhs_list):
             Xt = torch.from_numpy(li.uniform(n, nrhs, MIXED_FAMILY + 500 + nrhs)).to(dev)
             Xt[:, 0] = 1.0
             Xt = Xt.t().contiguous()                       # (nrhs, n): row q = right-hand side q
@@ -662,7 +664,7 @@ def time_to_solution(args, dev):
                      "mixed_ms": rep.t_total_ms, "mixed_wall_ms": wall * 1e3, "factor_ms": rep.t_factor_ms,
                      "refine_ms": rep.t_refine_ms, "factor_bound_ms": bound_ms,
                      "factor_frac_of_bound": bound_ms / rep.t_factor_ms if rep.t_factor_ms > 0 else None}
-            if nrhs == 1:
+            if fp64 is None:
                 # the plain FP64 path to the same target: FP64 factorization with the DFMA
                 # update, FP64 refinement; and the same with the emulated FP64 update
                 fp64 = {}
@@ -695,7 +697,7 @@ def time_to_solution(args, dev):
         del A
     del Q_u, Vt
     torch.cuda.empty_cache()
-    head = next(c for c in cases if c["kappa"] == 1e5 and c["nrhs"] == 1)
+    head = next((c for c in cases if c["kappa"] == 1e5 and c["nrhs"] == 1), cases[0])
     return {"n": n, "reflectors_per_side": n, "target_eta": 1e-14, "generation_s": gen_s, "plan_nb": plan_bo,
             "cases": cases, "update_roofline": tc_roof,
             "mixed_ms": head["mixed_ms"], "fp64_ms": head["fp64_ms"], "speedup_vs_fp64": head["speedup_vs_fp64"]}
@@ -978,6 +980,10 @@ def make_parser():
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")
     ap.add_argument("--kappas", default="1e3,1e6,1e12", help="condition numbers of the fp8_large case")
+    ap.add_argument("--c3-kappas", dest="c3_kappas", default=None,
+                    help="condition numbers of the time-to-solution grid (default 1e2,1e5,1e8)")
+    ap.add_argument("--c3-nrhs", dest="c3_nrhs", default=None,
+                    help="right-hand side counts of the time-to-solution grid (default 1,8)")
     ap.add_argument("--nb", type=int, default=0, help="outer panel width of the fp64_factor case (0: 64)")
     ap.add_argument("--panel-ctas", dest="panel_ctas", type=int, default=0,
                     help="panel team of the fp64_factor case (0: 8)")
