@@ -38,7 +38,8 @@ def _sources():
 
 def _stamp(srcs) -> str:
     h = hashlib.sha256()
-    for p in srcs + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "lu.h")]:
+    for p in (srcs + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(CSRC, "*.h"))) +
+              [os.path.join(ROOT, "include", "lu.h")]):
         with open(p, "rb") as f:
             h.update(f.read())
     h.update(" ".join(ARCH + FLAGS).encode())

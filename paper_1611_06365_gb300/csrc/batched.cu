@@ -10,6 +10,7 @@
 // written once); larger ones are factored in place in global memory, where
 // the L2 cache holds them.
 #include "common.cuh"
+#include "internal.h"
 #include <climits>
 
 namespace lu {

@@ -21,6 +21,7 @@
 // matrix per column).  The matrices stay in global memory; each CTA works on
 // one at a time, so its working set (at most 512 KiB) stays in L2.
 #include "common.cuh"
+#include "internal.h"
 #include <algorithm>
 #include <climits>
 

@@ -20,6 +20,7 @@
 // rows as A; both write only the lower triangle.  Two streams ordered by
 // events, as for the LU factorization (section 3.2, Figure 3).
 #include "common.cuh"
+#include "internal.h"
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <algorithm>
@@ -28,23 +29,6 @@
 #include <vector>
 
 namespace lu {
-template <typename T>
-cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc, cudaStream_t s,
-                             CtaTrace tr, bool transb, int lshift, int tile);
-cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0, const CUtensorMap &mapB, int b_col0,
-                               double *C, int ldc, const double *scaleA, const double *scaleB, int *tile_ctr, int *status,
-                               long long bound_ns, int max_ctas, cudaStream_t s, CtaTrace tr, int lshift, SmShare sh,
-                               int tile);
-cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int outer, int lds, int box_outer, int fp8);
-int f64emu_kpad();
-int f64emu_box_rows();
-int f64emu_box_cols();
-int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s,
-                   const double *Dinv = nullptr);
-int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s,
-                   const float *Dinv = nullptr);
-cudaError_t launch_iota(int *v, int n, cudaStream_t s);
-CtaTrace cta_tag_ext(int kind, int step);   // api.cu: the per-CTA trace argument of a launch
 
 constexpr int kChW = 64;          // widest panel
 constexpr int kChThreads = 256;   // one row of L21 per thread

@@ -44,6 +44,7 @@
 // Every wait is bounded; on expiry the kernel records LU_ERR_TIMEOUT, gives
 // its copies in flight one bounded wait, frees its TMEM and returns.
 #include "common.cuh"
+#include "internal.h"
 #include "tcgen05.cuh"
 #include <cuda_bf16.h>
 

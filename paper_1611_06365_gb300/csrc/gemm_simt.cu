@@ -20,6 +20,7 @@
 // (i, j) of C is kept when i >= j + lshift, and tiles wholly above that
 // diagonal return at once).
 #include "common.cuh"
+#include "internal.h"
 
 namespace lu {
 

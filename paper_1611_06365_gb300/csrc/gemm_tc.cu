@@ -30,6 +30,7 @@
 // scaleA[i] (= 2^-e_i, the inverse of the factor applied to row i) and
 // scaleB[j].
 #include "common.cuh"
+#include "internal.h"
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>

@@ -11,6 +11,7 @@
 // while one multi-column preconditioner solve, one multi-column product with
 // A and one host synchronisation per Gram-Schmidt pass serve all of them.
 #include "common.cuh"
+#include "internal.h"
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -18,12 +19,6 @@
 #include <vector>
 
 namespace lu {
-int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s,
-                   const float *Dinv = nullptr);
-cudaError_t launch_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B, int ldb,
-                            double *R, int ldr, double *part, unsigned long long *rmax, cudaStream_t s);
-size_t residual_workspace_doubles(int n, int nrhs);
-cudaError_t launch_absmax(int n, int nrhs, const double *V, int ldv, unsigned long long *out, cudaStream_t s);
 
 constexpr int kDotThreads = 512;
 constexpr int kGmresChunk = 16;   // right-hand side columns iterated together

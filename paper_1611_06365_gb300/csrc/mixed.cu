@@ -8,6 +8,7 @@
 //                 pattern, which orders non-negative doubles);
 //   to_f32_scaled / axpy_scaled  the scaled FP32 correction solve glue.
 #include "common.cuh"
+#include "internal.h"
 #include <algorithm>
 
 namespace lu {

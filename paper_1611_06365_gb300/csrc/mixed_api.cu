@@ -51,35 +51,7 @@
 #include <utility>
 #include <vector>
 
-namespace lu {
-int factor_f32_internal(int n, float *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s);
-int factor_f64_internal(int n, double *A, int lda, int *ipiv, int *info, int *perm, const lu_opts *o, cudaStream_t s);
-int solve_f32_perm(int n, int nrhs, const float *LU, int lda, const int *perm, float *B, int ldb, cudaStream_t s,
-                   const float *Dinv = nullptr);
-int solve_f64_perm(int n, int nrhs, const double *LU, int lda, const int *perm, double *B, int ldb, cudaStream_t s,
-                   const double *Dinv = nullptr);
-size_t f32_diag_inverse_elems(int n);
-size_t f64_diag_inverse_elems(int n);
-int f64_diag_inverse(int n, const double *LU, int lda, double *Dinv, cudaStream_t s);
-int f32_diag_inverse(int n, const float *LU, int lda, float *Dinv, cudaStream_t s);
-cudaError_t launch_cast_rowsum(int n, const double *A, int lda, float *A32, int lda32, double *rowsum, cudaStream_t s);
-size_t residual_workspace_doubles(int n, int nrhs);
-cudaError_t launch_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B, int ldb,
-                            double *R, int ldr, double *part, unsigned long long *rmax, cudaStream_t s);
-cudaError_t launch_absmax(int n, int nrhs, const double *V, int ldv, unsigned long long *out, cudaStream_t s);
-cudaError_t launch_vecmax(int n, const double *v, unsigned long long *out, cudaStream_t s);
-cudaError_t launch_fill_probe(int n, unsigned long long seed, float *R32, cudaStream_t s);
-cudaError_t launch_to_f32_scaled(int n, int nrhs, const double *R, int ldr, const unsigned long long *rmax, float *R32,
-                                 int ldr32, cudaStream_t s);
-cudaError_t launch_axpy_scaled(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax, double *X, int ldx,
-                               cudaStream_t s);
-cudaError_t launch_axpy_f64(int n, int nrhs, const double *D, int ldd, double *X, int ldx, cudaStream_t s);
-cudaError_t launch_absmax_scaled_f32(int n, int nrhs, const float *D32, int ldd, const unsigned long long *rmax,
-                                     unsigned long long *out, cudaStream_t s);
-int gmres_ir(int n, int nrhs, const double *A, int lda, const double *B, int ldb, double *X, int ldx, const float *LU32,
-             int ld32, const int *perm, double anorm, const double *bnorm, double tol, int max_outer, int restart,
-             int *iters_out, int *inner_out, double *eta_out, cudaStream_t s, double budget_ms, const float *Dinv);
-}  // namespace lu
+#include "internal.h"
 
 using namespace lu;
 

@@ -44,6 +44,7 @@
 // its threads finished column j (a CTA barrier separates the two).  No
 // cluster-wide barrier is needed per column.
 #include "common.cuh"
+#include "internal.h"
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <climits>

@@ -16,6 +16,7 @@
 //   its own, which belong to warps already running, so the chain always
 //   advances; every wait is bounded and records LU_ERR_TIMEOUT on expiry.
 #include "common.cuh"
+#include "internal.h"
 #include <algorithm>
 
 namespace lu {

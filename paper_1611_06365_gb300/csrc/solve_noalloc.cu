@@ -24,15 +24,7 @@
 #include <algorithm>
 #include <mutex>
 
-namespace lu {
-cudaError_t launch_ipiv_to_perm(const int *ipiv, int n, int *perm, cudaStream_t s);
-template <typename TI, typename TO>
-cudaError_t launch_gather_rows(int n, int nrhs, const int *perm, const TI *B, int ldb, TO *X, int ldx, cudaStream_t s);
-template <typename T>
-cudaError_t launch_trsv_pair(const T *LU, int lda, int n, int nrhs, T *X, int ldx, int *ws, int *status, long long bound_ns,
-                             int sms, cudaStream_t s, const T *Dinv = nullptr);
-size_t trsv_workspace_ints(int n, int nrhs);
-}  // namespace lu
+#include "internal.h"
 
 namespace {
 

@@ -10,6 +10,7 @@
 // parallel -- the paper notes the permutation is embarrassingly parallel
 // (section 3.1) and spreads it over all threads (section 3.2).
 #include "common.cuh"
+#include "internal.h"
 #include <cuda_bf16.h>
 
 namespace lu {

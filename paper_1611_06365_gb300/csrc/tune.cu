@@ -17,9 +17,7 @@
 #include "common.cuh"
 #include "lu.h"
 
-namespace lu {
-int default_outer_width(lu_dtype dt, int n, int update);   // api.cu: the built-in b_o
-}
+#include "internal.h"
 
 namespace {
 
