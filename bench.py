@@ -844,13 +844,14 @@ def run_case(args):
         C = li.uniform_colmajor_torch(m, n, 3, dev, torch.float32)
         lu.lu_trailing_update(lu.LU_UPDATE_BF16X3, A, B, C, m, n, k)
     elif args.case == "fp64_factor":
-        # FP64 factorization, n = 8192 (512 MiB), by default with the plan the autotuner
-        # picks for the n = 16384 workload on GB300 (b_o = 64, an 8-CTA panel team)
-        n = 8192
+        # FP64 factorization, n = 8192 (512 MiB) unless --n is given, by default with the plan
+        # the autotuner picks for the large orders on GB300 (b_o = 64, an 8-CTA panel team)
+        n = 8192 if args.n == N_MAIN else args.n
         A = li.uniform_colmajor_torch(n, n, 5, dev, torch.float64)
         ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
         info = torch.zeros(1, dtype=torch.int32, device=dev)
-        lu.lu_factor(A, ipiv, info, nb=args.nb or 64, panel_ctas=args.panel_ctas or 8)
+        lu.lu_factor(A, ipiv, info, nb=args.nb or 64, panel_ctas=args.panel_ctas or 8,
+                     update=lu.LU_UPDATE_F64EMU if args.emu else lu.LU_UPDATE_NATIVE)
     elif args.case == "mixed_factor":
         # FP32 factorization with the split-BF16 update, n = 8192
         n = 8192
@@ -985,6 +986,7 @@ def make_parser():
     ap.add_argument("--c3-nrhs", dest="c3_nrhs", default=None,
                     help="right-hand side counts of the time-to-solution grid (default 1,8)")
     ap.add_argument("--nb", type=int, default=0, help="outer panel width of the fp64_factor case (0: 64)")
+    ap.add_argument("--emu", action="store_true", help="fp64_factor case with the emulated FP64 update")
     ap.add_argument("--panel-ctas", dest="panel_ctas", type=int, default=0,
                     help="panel team of the fp64_factor case (0: 8)")
     return ap
