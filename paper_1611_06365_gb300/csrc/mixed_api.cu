@@ -394,18 +394,27 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
                                       cudaMemcpyDeviceToDevice, s));
         double *D = nullptr;
         LU_CUDA_TRY(ws.get(&D, (size_t)n * nrhs));
-        for (int it = 0; it < 5; ++it) {
-            LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-            rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s, Dinv64);
-            if (rc != LU_OK) return rc;
-            LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));   // X += D
-            LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
-            LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
-            rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
-            if (rc != LU_OK) return rc;
-            r.iterations++;
-            if (eta <= tol) break;
-        }
+        // up to five refinement steps from the current X and R with the FP64 factors; the
+        // solves use the diagonal-block inverses, and if that does not reach the target
+        // (a diagonal block too ill-conditioned for its explicit inverse) exact substitution
+        // takes over on the same factors
+        auto refine64 = [&](const double *dinv) -> int {
+            for (int it = 0; it < 5 && !(eta <= tol); ++it) {
+                LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
+                int rc2 = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s, dinv);
+                if (rc2 != LU_OK) return rc2;
+                LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));   // X += D
+                LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
+                LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
+                rc2 = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
+                if (rc2 != LU_OK) return rc2;
+                r.iterations++;
+            }
+            return LU_OK;
+        };
+        eta = INFINITY;
+        if ((rc = refine64(Dinv64)) != LU_OK) return rc;
+        if (!(eta <= tol) && (rc = refine64(nullptr)) != LU_OK) return rc;
         done = eta <= tol;
         if (!done && o64.update == LU_UPDATE_F64EMU && (allow_fb || fp64_only)) {
             // the emulated FP64 factors did not reach the target: the DFMA factorization
@@ -420,18 +429,9 @@ extern "C" int lu_solve_mixed(int n, int nrhs, const double *dA, int lda, const 
             LU_CUDA_TRY(cudaMemset2DAsync(dX, sizeof(double) * ldx, 0, sizeof(double) * n, nrhs, s));
             LU_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(double) * n, dB, sizeof(double) * ldb, sizeof(double) * n, nrhs,
                                           cudaMemcpyDeviceToDevice, s));
-            for (int it = 0; it < 5; ++it) {
-                LU_CUDA_TRY(cudaMemcpyAsync(D, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-                rc = solve_f64_perm(n, nrhs, A64, n, perm64, D, n, s, Dinv64);
-                if (rc != LU_OK) return rc;
-                LU_CUDA_TRY(launch_axpy_f64(n, nrhs, D, n, dX, ldx, s));
-                LU_CUDA_TRY(launch_residual(n, nrhs, dA, lda, dX, ldx, dB, ldb, R, n, part, d_rmax, s));
-                LU_CUDA_TRY(launch_absmax(n, nrhs, dX, ldx, d_xmax, s));
-                rc = eta_now(nrhs, d_rmax, d_xmax, anorm, bnorm, &eta, s);
-                if (rc != LU_OK) return rc;
-                r.iterations++;
-                if (eta <= tol) break;
-            }
+            eta = INFINITY;
+            if ((rc = refine64(Dinv64)) != LU_OK) return rc;
+            if (!(eta <= tol) && (rc = refine64(nullptr)) != LU_OK) return rc;
             done = eta <= tol;
         }
         r.t_fallback_ms = ms_since(t_fb);
