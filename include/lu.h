@@ -527,6 +527,12 @@ long long lu_kernel_launches(void);
 /* Version string of the build (architecture and options). */
 const char *lu_version(void);
 
+/* sizeof of a public struct of this header, by name ("lu_opts", "lu_mixed_opts",
+ * "lu_mixed_report", "lu_tune_result", "lu_trace_event", "lu_cta_event"), 0 for
+ * any other name: lets a binding check its copies of these layouts against the
+ * library it loaded. */
+size_t lu_abi_size(const char *name);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,8 @@ def lib():
         L.lu_get_status.argtypes = [vp]
         L.lu_get_status.restype = i
         L.lu_version.restype = ctypes.c_char_p
+        L.lu_abi_size.argtypes = [ctypes.c_char_p]
+        L.lu_abi_size.restype = ctypes.c_size_t
         L.lu_solve_noalloc.argtypes = [i, i, i, vp, i, ip, vp, i, ip, vp]
         L.lu_solve_noalloc.restype = i
         L.lu_solve_noalloc_capacity.restype = ctypes.c_size_t

@@ -1084,7 +1084,20 @@ int lu_cta_trace_read(lu_cta_event *out, int max_events) {
 
 long long lu_kernel_launches(void) { return g_launches.load(); }
 
-const char *lu_version(void) { return "liblu 0.1 (sm_103a; cluster panel, tcgen05 BF16 update, FP64 DFMA update)"; }
+const char *lu_version(void) {
+    return "liblu 0.2 (sm_103a; cluster panel, tcgen05 BF16 / split-BF16 / FP8 and emulated FP64 updates, FP64 DFMA update)";
+}
+
+size_t lu_abi_size(const char *name) {
+    if (!name) return 0;
+    if (!strcmp(name, "lu_opts")) return sizeof(lu_opts);
+    if (!strcmp(name, "lu_mixed_opts")) return sizeof(lu_mixed_opts);
+    if (!strcmp(name, "lu_mixed_report")) return sizeof(lu_mixed_report);
+    if (!strcmp(name, "lu_tune_result")) return sizeof(lu_tune_result);
+    if (!strcmp(name, "lu_trace_event")) return sizeof(lu_trace_event);
+    if (!strcmp(name, "lu_cta_event")) return sizeof(lu_cta_event);
+    return 0;
+}
 
 }  // extern "C"
 

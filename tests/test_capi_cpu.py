@@ -73,3 +73,13 @@ def test_colmajor_helpers():
     T = lu.to_colmajor(M, ld=5)
     assert T.shape == (4, 5) and float(T[1, 2]) == float(M[2, 1])
     assert torch.equal(lu.from_colmajor(T, 3), M)
+
+
+def test_binding_struct_layouts_match_the_library(L):
+    """Every public struct the binding mirrors has the size the library was built with
+    (a field added on one side only would shift the fields after it)."""
+    for name, cls in (("lu_opts", lu.LuOpts), ("lu_mixed_opts", lu.MixedOpts), ("lu_mixed_report", lu.MixedReport),
+                      ("lu_tune_result", lu.TuneResult), ("lu_trace_event", lu.TraceEvent),
+                      ("lu_cta_event", lu.CtaEvent)):
+        assert L.lu_abi_size(name.encode()) == ctypes.sizeof(cls), name
+    assert L.lu_abi_size(b"no_such_struct") == 0
