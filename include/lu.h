@@ -79,9 +79,11 @@ enum {
                               U12 is split below a power-of-two scale into seven
                               8-bit BF16 digits (Ozaki, Ogita, Oishi and Rump,
                               Numer. Algorithms 59, 2012); the 28 digit products
-                              that reach 2^-56 of the leading one are accumulated
-                              exactly in FP32 per diagonal, summed in FP64 and
-                              subtracted from C with one FP64 rounding */
+                              that reach 2^-56 of the leading one are accumulated in
+                              FP32 per diagonal (exactly for the five leading
+                              diagonals, the last two sharing a rounded sum), added
+                              exactly as a 64-bit integer and subtracted from C with
+                              one FP64 rounding */
 };
 
 /* Tuning knobs.  Pass NULL for the built-in choice; a zero field means "auto". */
