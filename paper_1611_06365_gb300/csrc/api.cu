@@ -135,6 +135,21 @@ struct Workspace {
 static std::atomic<long long> g_launches{0};
 void lu_count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+cudaError_t lu_sm_count(int *sms) {
+    static std::atomic<int> cache[kMaxDev];
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= kMaxDev) return cudaErrorInvalidDevice;
+    int v = cache[d].load(std::memory_order_relaxed);
+    if (v == 0) {
+        if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d)) != cudaSuccess) return e;
+        cache[d].store(v, std::memory_order_relaxed);
+    }
+    *sms = v;
+    return cudaSuccess;
+}
+
 // trailing-update instrumentation (lu_update_timing)
 namespace {
 struct TimedLaunch {

@@ -24,6 +24,8 @@ int *lu_device_status_ptr();
 void lu_count_launch(int k = 1);
 // Default bound for device-side waits, in globaltimer nanoseconds.
 long long lu_spin_bound_ns(const lu_opts *o);
+// SM count of the current device (looked up once per device; thread-safe).
+cudaError_t lu_sm_count(int *sms);
 
 __device__ __forceinline__ unsigned long long lu_globaltimer() {
     unsigned long long t;

@@ -393,19 +393,12 @@ cudaError_t launch_gemm_f64emu(int m, int n, const CUtensorMap &mapA, int a_row0
                                int tile) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     if (sh.req && !sh.mask) return cudaErrorInvalidValue;
-    static int sms = 0;
-    if (!sms) {
-        int d = 0;
-        cudaError_t e = cudaGetDevice(&d);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
-        if (e != cudaSuccess) return e;
-    }
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_update_f64emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    int sms = 0;
+    cudaError_t e = lu_sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    // set on every launch: the attribute belongs to the current device's context
+    e = cudaFuncSetAttribute(gemm_update_f64emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEmSmem);
+    if (e != cudaSuccess) return e;
     const long long mt = lu_ceil_div(m, kEmBM);
     // sub-tiles per task: tile 1: kEmMaxSub; 2: two; 0: fewer while the queue would not fill
     // the GPU twice (the task shape changes the schedule, not the arithmetic)

@@ -91,13 +91,9 @@ template <typename T>
 cudaError_t launch_gemm_simt(int m, int n, int k, const T *A, int lda, const T *B, int ldb, T *C, int ldc,
                              cudaStream_t s, CtaTrace tr, bool transb, int lshift, int tile) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
-    static int sms = 0;
-    if (!sms) {
-        int d = 0;
-        cudaError_t e = cudaGetDevice(&d);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
-        if (e != cudaSuccess) return e;
-    }
+    int sms = 0;
+    cudaError_t e = lu_sm_count(&sms);
+    if (e != cudaSuccess) return e;
     // tile 1: 64 x 64 tiles, 2: 32 x 32, 0: 64 x 64 when that makes at least one tile per SM
     // (both shapes accumulate in the same order: the same bits)
     const long long big = (long long)lu_ceil_div(m, 64) * lu_ceil_div(n, 64);

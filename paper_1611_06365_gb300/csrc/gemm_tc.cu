@@ -380,7 +380,7 @@ cudaError_t make_stage_map(CUtensorMap *map, const void *base, int kinner, int o
     cuuint64_t strides[1] = {(cuuint64_t)lds * esz};
     cuuint32_t box[2] = {(cuuint32_t)(fp8 ? kTcBK8 : kTcBK), (cuuint32_t)box_outer};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    CUresult r = g_encode.load()(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                           const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -407,7 +407,7 @@ static cudaError_t make_c_map(CUtensorMap *map, float *C, int m, int n, int ldc)
     cuuint64_t strides[1] = {(cuuint64_t)ldc * 4};
     cuuint32_t box[2] = {(cuuint32_t)kTcBM, (cuuint32_t)kTcCBox};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    CUresult r = g_encode.load()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -419,12 +419,9 @@ static cudaError_t launch_tc_mode(int grid, int m, int n, int K, const CUtensorM
                                   int b_col0, const CUtensorMap &mapC, int *tile_ctr, int *status, long long bound_ns,
                                   const float *scaleA, const float *scaleB, cudaStream_t s, const CtaTrace &tr,
                                   const SmShare &sh) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set on every launch: the attribute belongs to the current device's context
+    cudaError_t e = cudaFuncSetAttribute(gemm_update_tc<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
     gemm_update_tc<NPROD><<<grid, kTcThreads, kTcSmem, s>>>(m, n, K, mapA, a_row0, mapB, b_col0, mapC, tile_ctr, status,
                                                              bound_ns, scaleA, scaleB, tr, sh.req, sh.mask);
     lu_count_launch();
@@ -448,13 +445,9 @@ cudaError_t launch_gemm_tc(int nprod, int m, int n, int K, const CUtensorMap &ma
     CUtensorMap mapC;
     cudaError_t ec = make_c_map(&mapC, C, m, n, ldc);
     if (ec != cudaSuccess) return ec;
-    static int sms = 0;
-    if (!sms) {
-        int d = 0;
-        cudaGetDevice(&d);
-        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
-        if (e != cudaSuccess) return e;
-    }
+    int sms = 0;
+    ec = lu_sm_count(&sms);
+    if (ec != cudaSuccess) return ec;
     const int ntiles = lu_ceil_div(m, kTcBM) * lu_ceil_div(n, kTcBN);
     // persistent CTAs: one per SM, or max_ctas (> 0) to leave SMs to other work
     const int cap = max_ctas > 0 && max_ctas < sms ? max_ctas : sms;

@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include <algorithm>
+#include <atomic>
 
 namespace lu {
 
@@ -492,8 +493,9 @@ static cudaError_t launch_trsv_nq(int grid, size_t smem, const T *LU, int lda, i
 // CTAs of the substitution kernel resident per SM (shared memory bound).
 template <typename T, bool INV>
 static int trsv_ctas_per_sm(size_t smem) {
-    static int cached[2] = {0, 0};
-    int &c = cached[sizeof(T) == 8];
+    // the occupancy of one architecture: the same on every device this library runs on
+    static std::atomic<int> cached{0};
+    int c = cached.load(std::memory_order_relaxed);
     if (c == 0) {
         int k = 0;
         if (cudaFuncSetAttribute(trsv_blocks<T, true, 1, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -504,6 +506,7 @@ static int trsv_ctas_per_sm(size_t smem) {
             k = 1;
         }
         c = std::max(1, k);
+        cached.store(c, std::memory_order_relaxed);
     }
     return c;
 }

@@ -252,12 +252,9 @@ cudaError_t launch_swap_trsm(T *A, int lda, int kb, int b, const int *map, int c
                              int do_trsm, StageDesc sd, int stage_c0, cudaStream_t s, CtaTrace tr) {
     if (c_end <= c_begin) return cudaSuccess;
     size_t smem = swap_trsm_smem_bytes(b, sizeof(T));
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
-        cudaError_t e = cudaFuncSetAttribute(swap_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set[sizeof(T) == 8] = true;
-    }
+    // set on every launch: the attribute belongs to the current device's context
+    cudaError_t e = cudaFuncSetAttribute(swap_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
     int grid = lu_ceil_div(c_end - c_begin, kStrip);
     swap_trsm_kernel<T><<<grid, kSwapThreads, smem, s>>>(A, lda, kb, b, map, c_begin, c_end, do_trsm, sd, stage_c0, tr);
     return cudaGetLastError();

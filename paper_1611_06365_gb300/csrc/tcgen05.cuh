@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <atomic>
 #include <cstdint>
 #include "common.cuh"
 
@@ -141,18 +142,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-inline PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+inline std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 
 // cuTensorMapEncodeTiled, resolved at run time through the runtime (no link
-// dependency on the driver library)
+// dependency on the driver library); callers then use g_encode.load()
 inline cudaError_t get_encoder() {
-    if (g_encode) return cudaSuccess;
+    if (g_encode.load()) return cudaSuccess;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess) return e;
     if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    g_encode.store(reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn));
     return cudaSuccess;
 }
 
