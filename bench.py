@@ -825,6 +825,45 @@ def measure_peaks(dev):
     return out
 
 
+def early_term_case(dev):
+    """Early termination (section 4.2) against the same plan without it: lu_factor time
+    (CUDA events on the caller's stream, so the host's wait for each panel's width is
+    inside), panels, and how many stopped early.  One JSON line per workload."""
+    import torch
+
+    import lu_inputs as li
+    import paper_1611_06365_gb300 as lu
+
+    cases = (("fp64_dfma", 4096, torch.float64, lu.LU_UPDATE_NATIVE),
+             ("fp64_emulated", 8192, torch.float64, lu.LU_UPDATE_F64EMU),
+             ("fp32_split_bf16", 16384, torch.float32, lu.LU_UPDATE_BF16X3))
+    for name, n, tdt, update in cases:
+        A0 = li.uniform_colmajor_torch(n, n, 5, dev, tdt)
+        A = torch.empty_like(A0)
+        ipiv = torch.zeros(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        row = {"case": "early_term", "workload": name, "n": n, "nb": 64, "nb_inner": 16}
+        for et in (0, 1):
+            times = []
+            for rep in range(4):
+                A.copy_(A0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                lu.lu_factor(A, ipiv, info, nb=64, nb_inner=16, update=update, early_term=et)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep > 0:
+                    times.append(e0.elapsed_time(e1))
+            w = lu.lu_last_panel_widths()
+            key = "et_on" if et else "et_off"
+            ms = min(times)
+            row[key] = {"ms": ms, "gflops": flops_lu(n) / (ms / 1e3) / 1e9, "panels": len(w),
+                        "stopped_early": sum(1 for i, x in enumerate(w[:-1]) if x < 64),
+                        "mean_width": sum(w) / len(w), "info": int(info.item())}
+        print(json.dumps(row), flush=True)
+
+
 def run_case(args):
     """Single-kernel cases for profiling (one launch of the kernel of interest)."""
     import torch
@@ -894,6 +933,9 @@ def run_case(args):
         return
     elif args.case == "peaks":
         print(json.dumps(measure_peaks(dev)), flush=True)
+        return
+    elif args.case == "early_term":
+        early_term_case(dev)
         return
     elif args.case == "cholesky":
         print(json.dumps(dict({"case": "cholesky"}, **cholesky_measure(args.n, dev, 3))), flush=True)
@@ -976,7 +1018,7 @@ def make_parser():
                     help="tuning table: loaded (no tuning) if it exists, else written after tuning")
     ap.add_argument("--case", choices=["tc_update", "fp64_factor", "mixed_factor", "batched_f64", "batched_f32",
                                        "fp8_large", "solve_f32", "torch_context", "peaks", "c3_grid", "probe_dfma",
-                                       "emu_update", "cholesky"],
+                                       "emu_update", "cholesky", "early_term"],
                     default=None,
                     help="run one profiling case instead of the benchmark (fp8_large: the order-65536 "
                          "FP8-update solves, one JSON line per kappa)")

@@ -117,6 +117,19 @@ typedef struct {
                           2 = small (32 x 32; 2 sub-tiles).  Changes the schedule, not the
                           arithmetic (results are the same bits); the FP32 tensor-core updates
                           have one shape and ignore it */
+    int early_term;    /* early termination (section 4.2, Figure LU_LA_ET): 0 = off (default);
+                          1 = the panel factorization of step k+1 stops at the end of the
+                          inner panel during which the remainder update of step k finished,
+                          and step k+1 then has the width the panel reached (an adaptive
+                          b_o); 2 = stop at the end of the first inner panel of every panel
+                          (a fixed schedule through the same path, for tests).  Takes effect
+                          when the inner width is below the outer one (nb_inner < nb) and
+                          needs look-ahead of depth 1 (lookahead 0 or 1).  The host learns
+                          each panel's width before enqueueing the next step: lu_factor then
+                          returns after the last panel has run, and a stream under capture
+                          is refused (LU_ERR_UNSUPPORTED).  The pivots follow the unblocked
+                          algorithm as always; the rounding of the factors depends on where
+                          the panels stopped.  lu_last_panel_widths reports the widths. */
 } lu_opts;
 
 /*
@@ -136,6 +149,15 @@ typedef struct {
  */
 int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info,
               const lu_opts *opts, void *stream);
+
+/*
+ * lu_last_panel_widths -- the widths of the panels of the last lu_factor on
+ *   the current device, in order (all b_o but the last unless early
+ *   termination shortened some; section 4.2).  Copies min(count, cap) of them
+ *   to the host array `widths` (may be NULL when cap = 0) and returns count,
+ *   or -1 when no factorization ran on this device yet.
+ */
+int lu_last_panel_widths(int *widths, int cap);
 
 /*
  * lu_solve -- X := A^{-1} B with the factors from lu_factor (no transpose).

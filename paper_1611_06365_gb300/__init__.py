@@ -52,7 +52,8 @@ class LuError(RuntimeError):
 class LuOpts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("nb_inner", ctypes.c_int), ("panel_ctas", ctypes.c_int),
                 ("lookahead", ctypes.c_int), ("update", ctypes.c_int), ("spin_ns", ctypes.c_longlong),
-                ("update_ctas", ctypes.c_int), ("sm_share", ctypes.c_int), ("tile", ctypes.c_int)]
+                ("update_ctas", ctypes.c_int), ("sm_share", ctypes.c_int), ("tile", ctypes.c_int),
+                ("early_term", ctypes.c_int)]
 
 
 class TuneResult(ctypes.Structure):
@@ -117,6 +118,8 @@ def lib():
         L.lu_solve_noalloc.argtypes = [i, i, i, vp, i, ip, vp, i, ip, vp]
         L.lu_solve_noalloc.restype = i
         L.lu_solve_noalloc_capacity.restype = ctypes.c_size_t
+        L.lu_last_panel_widths.argtypes = [ip, i]
+        L.lu_last_panel_widths.restype = i
         L.lu_update_timing.argtypes = [i]
         L.lu_update_timing.restype = i
         L.lu_update_timing_read.argtypes = [ctypes.POINTER(ctypes.c_longlong)] + [ctypes.POINTER(ctypes.c_double)] * 3
@@ -201,12 +204,23 @@ def _cm_dims(A, n=None):
 
 
 def lu_factor(A, ipiv, info, n=None, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0,
-              update=LU_UPDATE_NATIVE, spin_ns=0, update_ctas=0, sm_share=0, tile=0, stream=None):
+              update=LU_UPDATE_NATIVE, spin_ns=0, update_ctas=0, sm_share=0, tile=0, early_term=0, stream=None):
     """P A = L U in place (see include/lu.h).  A: column-major (n, lda) tensor."""
     n, lda = _cm_dims(A, n)
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns, update_ctas, sm_share, tile)
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, spin_ns, update_ctas, sm_share, tile, early_term)
     return _check("lu_factor", lib().lu_factor(_dtype_code(A), n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
                                                 ctypes.byref(o), _stream(stream)))
+
+
+def lu_last_panel_widths():
+    """Widths of the panels of the last factorization on the current device (a list),
+    or None before the first one."""
+    cnt = lib().lu_last_panel_widths(None, 0)
+    if cnt < 0:
+        return None
+    buf = (ctypes.c_int * max(cnt, 1))()
+    lib().lu_last_panel_widths(buf, cnt)
+    return list(buf[:cnt])
 
 
 def lu_cholesky(A, info, n=None, *, nb=0, lookahead=0, update=LU_UPDATE_NATIVE, spin_ns=0, stream=None):
@@ -401,7 +415,7 @@ def from_colmajor(T, m=None):
 
 def _opts_dict(o):
     return {"nb": o.nb, "nb_inner": o.nb_inner, "panel_ctas": o.panel_ctas, "lookahead": o.lookahead, "update": o.update,
-            "update_ctas": o.update_ctas, "sm_share": o.sm_share, "tile": o.tile}
+            "update_ctas": o.update_ctas, "sm_share": o.sm_share, "tile": o.tile, "early_term": o.early_term}
 
 
 def lu_autotune(dtype_code, n, *, update=LU_UPDATE_NATIVE, budget_ms=0.0, stream=None):
@@ -421,10 +435,10 @@ def lu_autotune_batched(dtype_code, ns, max_n, *, stream=None):
 
 
 def lu_plan_info(dtype_code, n, *, nb=0, nb_inner=0, panel_ctas=0, lookahead=0, update=LU_UPDATE_NATIVE, update_ctas=0,
-                 sm_share=0, tile=0):
+                 sm_share=0, tile=0, early_term=0):
     """(status, plan dict) of the plan lu_factor would run for these options (no CUDA call);
     status 0 = every panel fits, LU_ERR_UNSUPPORTED = one does not."""
-    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas, sm_share, tile)
+    o = LuOpts(nb, nb_inner, panel_ctas, lookahead, update, 0, update_ctas, sm_share, tile, early_term)
     p = LuOpts()
     rc = lib().lu_plan_info(dtype_code, n, ctypes.byref(o), ctypes.byref(p))
     if rc < 0 and rc > -100:

@@ -68,8 +68,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout, r.stderr)
         return obj
 
+    # longest units first (the panel unit instantiates its kernel sixteen times), so
+    # the slowest compile starts at once
+    order = sorted(srcs, key=os.path.getsize, reverse=True)
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, srcs))
+        objs = list(ex.map(compile_one, order))
     tmp = OUT + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

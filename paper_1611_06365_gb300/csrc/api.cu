@@ -66,6 +66,9 @@ struct DevState {
     unsigned *share_mask = nullptr;  // [17][kMaskWords]: SMs of one cluster placement of C CTAs
     signed char share_state[17] = {};   // per C: 0 not probed, 1 probed, -1 probe refused
     int sms = 0;
+    int *et = nullptr;               // early termination: [0] flag, [1] width the panel reached
+    std::vector<int> widths;         // panel widths of the last factorization
+    bool widths_valid = false;
 };
 
 DevState g_dev[kMaxDev];
@@ -104,6 +107,8 @@ cudaError_t dev_state(DevState **out) {
         if ((e = cudaMalloc(&st.share_mask, 17 * kMaskWords * sizeof(unsigned))) != cudaSuccess) return e;
         if ((e = cudaMemset(st.share_mask, 0, 17 * kMaskWords * sizeof(unsigned))) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, d)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&st.et, 2 * sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMemset(st.et, 0, 2 * sizeof(int))) != cudaSuccess) return e;
         st.init = true;
     }
     *out = &st;
@@ -250,6 +255,7 @@ struct Plan {
     int update_ctas = 0;   // persistent CTAs of the remainder update (0: one per SM)
     bool share = true;     // worker sharing with the persistent tensor-core update (SmShare)
     int tile = 0;          // update tile shape (lu_opts.tile)
+    int et = 0;            // early termination (lu_opts.early_term; look-ahead of depth 1 only)
     long long bound = 2000000000LL;
 };
 
@@ -292,6 +298,7 @@ Plan make_plan(int n, const lu_opts *o) {
     p.update_ctas = (o && o->update_ctas > 0) ? o->update_ctas : 0;
     p.share = !(o && o->sm_share < 0);
     p.tile = o ? o->tile : 0;
+    p.et = (o && p.depth == 1) ? o->early_term : 0;
     p.bound = lu_spin_bound_ns(o);
     return p;
 }
@@ -405,9 +412,10 @@ int plan_inner_width(const Plan &pl, int n, size_t elem, int kb, int w) {
     return std::min(bi, w);
 }
 
-// Whether every outer panel of the plan fits a cluster.
+// Whether every outer panel of the plan fits a cluster (with early termination
+// a panel may start at any column).
 bool plan_fits(const Plan &pl, int n, size_t elem) {
-    for (int kb = 0; kb < n; kb += pl.bo) {
+    for (int kb = 0; kb < n; kb += pl.et ? 1 : pl.bo) {
         const int w = std::min(pl.bo, n - kb);
         if (!panel_fits(n - kb, elem, w, plan_inner_width(pl, n, elem, kb, w), pl.panel_ctas, kPanelSmemCap)) return false;
     }
@@ -417,13 +425,14 @@ bool plan_fits(const Plan &pl, int n, size_t elem) {
 // Factor outer panel at column kb (width w) on stream s: one cluster launch
 // that also leaves the row map in maps[par], updates perm and stages L21.
 template <typename T>
-cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s, CtaTrace tr, int *yreq = nullptr) {
+cudaError_t factor_outer_panel(FactorCtx<T> &c, int kb, int w, int par, cudaStream_t s, CtaTrace tr, int *yreq = nullptr,
+                               EtArgs et = EtArgs{}) {
     StageDesc sd{nullptr, nullptr, c.kinner, c.kpad, c.pl.fmt, nullptr};
     if (c.pl.tc && kb + w < c.n) { sd.ptr = c.stA[par]; sd.scale = c.scA[par]; sd.dscale = c.dscA[par]; }
     return launch_panel_outer<T>(c.A + kb + (size_t)kb * c.lda, c.lda, c.n - kb, w, plan_inner_width(c.pl, c.n, sizeof(T), kb, w),
                                  c.ipiv + kb, kb,
                                  c.info, c.maps[par], c.perm, sd, c.pl.panel_ctas, kPanelSmemCap, c.st->status,
-                                 c.pl.bound, s, tr, yreq);
+                                 c.pl.bound, s, tr, yreq, et);
 }
 
 // The SMs of one placement of a C-CTA panel cluster (SmShare), found by a probe
@@ -475,12 +484,22 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
     DevState *st = nullptr;
     LU_CUDA_TRY(dev_state(&st));
     std::lock_guard<std::recursive_mutex> lk(g_enqueue_mu);
+    // early termination (section 4.2): the host learns each panel's width before it
+    // enqueues the next step, which a stream under capture cannot give
+    const bool et = pl.et != 0 && pl.depth == 1;
+    if (et) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        LU_CUDA_TRY(cudaStreamIsCapturing(caller, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return LU_ERR_UNSUPPORTED;
+    }
     Workspace ws(caller);
     FactorCtx<T> c;
     c.n = n; c.A = A; c.lda = lda; c.ipiv = ipiv; c.info = info; c.perm = perm; c.pl = pl; c.st = st;
     const int bo = pl.bo;
     // every panel of the plan must fit a cluster before anything is enqueued
     if (!plan_fits(pl, n, sizeof(T))) return LU_ERR_UNSUPPORTED;
+    st->widths.clear();
+    st->widths_valid = false;
     c.ring = std::max(2, pl.depth + 1);
     for (int i = 0; i < c.ring; ++i) LU_CUDA_TRY(ws.get(&c.maps[i], (size_t)(1 + 4 * bo)));
     LU_CUDA_TRY(ws.get(&c.tile_ctr, 2));
@@ -513,19 +532,26 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
         LU_CUDA_TRY(make_stage_map(&c.mapB, c.stB, c.kinner, n, c.kinner, tc_box_cols(), fp8));
     }
     cudaStream_t P = st->P, U = st->U;
+    if (et) LU_CUDA_TRY(cudaMemsetAsync(st->et, 0, 2 * sizeof(int), caller));
     LU_CUDA_TRY(cudaEventRecord(st->evIn, caller));
     LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evIn, 0));
     LU_CUDA_TRY(cudaStreamWaitEvent(U, st->evIn, 0));
 
-    const int nblk = (n + bo - 1) / bo;
     const int depth = pl.depth, R = c.ring;
     // prologue: panel 0
     LU_CUDA_TRY(traced(LU_TRACE_PANEL, 0, 0, P,
                        [&] { return factor_outer_panel<T>(c, 0, std::min(bo, n), 0, P, cta_tag(LU_TRACE_PANEL, 0)); }));
     LU_CUDA_TRY(cudaEventRecord(st->evP[0], P));
-    for (int k = 0; k < nblk; ++k) {
-        const int kb = k * bo, w = std::min(bo, n - kb), sl = k % R, sl1 = (k + 1) % R, slp = (k + R - 1) % R;
+    // panel k starts at column kb with nominal width wnom and factored w columns
+    // (w < wnom only after an early termination)
+    int kb = 0, wnom = std::min(bo, n), w = wnom;
+    for (int k = 0; kb < n; ++k) {
+        const int sl = k % R, sl1 = (k + 1) % R, slp = (k + R - 1) % R;
         const int cn0 = kb + w, wn = std::min(bo, n - cn0);
+        // columns [cn0, kb + wnom) are those an early-terminated panel k left: the panel
+        // already gave them step k (interchanges, U12 rows, update), so strip k+1 takes
+        // step k only from column kb + wnom on
+        const int fresh0 = std::min(std::max(cn0, kb + wnom), cn0 + wn);
         const int *map = c.maps[sl];
         // look-ahead window: strips k+1 .. k+depth on the panel branch, the rest on RU
         const int rest0 = std::min(n, cn0 + depth * bo);
@@ -550,10 +576,13 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
         if (wn > 0 && depth > 0) {
             // strip k+1 was last updated by RU2(k-1) with depth 1, by this branch with depth >= 2
             if (k > 0 && depth == 1) LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[slp], 0));
-            LU_CUDA_TRY(traced(LU_TRACE_PF1, k, 0, P,
-                               [&] { return swap_trsm<T>(c, kb, w, map, cn0, cn0 + wn, 1, P, cta_tag(LU_TRACE_PF1, k)); }));
-            LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P,
-                               [&] { return update<T>(c, sl, kb, w, cn0, cn0 + wn, P, cta_tag(LU_TRACE_PF2, k)); }));
+            if (fresh0 < cn0 + wn) {
+                LU_CUDA_TRY(traced(LU_TRACE_PF1, k, 0, P, [&] {
+                    return swap_trsm<T>(c, kb, w, map, fresh0, cn0 + wn, 1, P, cta_tag(LU_TRACE_PF1, k));
+                }));
+                LU_CUDA_TRY(traced(LU_TRACE_PF2, k, 0, P,
+                                   [&] { return update<T>(c, sl, kb, w, fresh0, cn0 + wn, P, cta_tag(LU_TRACE_PF2, k)); }));
+            }
             // RU2 starts after PF2: when both become ready the panel (higher
             // priority) is dispatched first, and RU2's queued CTAs fill the
             // rest of the GPU and later the SMs the panel cluster frees
@@ -561,9 +590,12 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
             // with a persistent RU2 that may already hold every SM: ask one cluster
             // placement back; the panel withdraws the request once it runs
             if (smask) LU_CUDA_TRY(launch_share_raise(st->share_req, P));
+            // early termination: panel k+1 stops at the end of the inner panel during
+            // which RU2(k) (below, on U) raised the flag to k + 1
+            const EtArgs eta = et ? EtArgs{st->et, k + 1, pl.et == 2 ? 1 : 0, st->et + 1} : EtArgs{};
             LU_CUDA_TRY(traced(LU_TRACE_PANEL, k + 1, 0, P, [&] {
                 return factor_outer_panel<T>(c, cn0, wn, sl1, P, cta_tag(LU_TRACE_PANEL, k + 1),
-                                             smask ? st->share_req : nullptr);
+                                             smask ? st->share_req : nullptr, eta);
             }));
             if (smask) LU_CUDA_TRY(cudaEventRecord(st->evPanelEnd, P));
             // depth >= 2: strips k+2 .. k+depth after the panel, off its chain; the last of
@@ -602,6 +634,7 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
             LU_CUDA_TRY(traced(LU_TRACE_RU2, k, 1, U,
                                [&] { return update<T>(c, sl, kb, w, rest0, n, U, cta_tag(LU_TRACE_RU2, k)); }));
         }
+        if (et) LU_CUDA_TRY(launch_et_signal(st->et, k + 1, U));   // RU2(k) is done
         LU_CUDA_TRY(cudaEventRecord(st->evU[sl], U));
         if (wn > 0 && depth == 0) {
             LU_CUDA_TRY(cudaStreamWaitEvent(P, st->evU[sl], 0));
@@ -609,7 +642,21 @@ int factor_core(int n, T *A, int lda, int *ipiv, int *info, int *perm, const Pla
                                [&] { return factor_outer_panel<T>(c, cn0, wn, sl1, P, cta_tag(LU_TRACE_PANEL, k + 1)); }));
             LU_CUDA_TRY(cudaEventRecord(st->evP[sl1], P));
         }
+        st->widths.push_back(w);
+        // the next step: panel k+1's width, read back once the panel has run
+        int wnext = wn;
+        if (et && wn > 0) {
+            int hw = 0;
+            LU_CUDA_TRY(cudaMemcpyAsync(&hw, st->et + 1, sizeof(int), cudaMemcpyDeviceToHost, P));
+            LU_CUDA_TRY(cudaStreamSynchronize(P));
+            if (hw < 1 || hw > wn) return LU_ERR_CUDA;   // the panel reports a width in [1, wn]
+            wnext = hw;
+        }
+        kb = cn0;
+        wnom = wn;
+        w = wnext;
     }
+    st->widths_valid = true;
     LU_CUDA_TRY(cudaEventRecord(st->evOutP, P));
     LU_CUDA_TRY(cudaEventRecord(st->evOutU, U));
     LU_CUDA_TRY(cudaStreamWaitEvent(caller, st->evOutP, 0));
@@ -650,7 +697,8 @@ extern "C" {
 static bool opts_valid(lu_dtype dt, const lu_opts *opts) {
     if (!opts) return true;
     if (opts->nb < 0 || opts->nb_inner < 0 || opts->panel_ctas < 0 || opts->panel_ctas > 16 || opts->update_ctas < 0 ||
-        opts->sm_share < -1 || opts->sm_share > 1 || opts->tile < 0 || opts->tile > 2 ||
+        opts->sm_share < -1 || opts->sm_share > 1 || opts->tile < 0 || opts->tile > 2 || opts->early_term < 0 ||
+        opts->early_term > 2 || (opts->early_term != 0 && (opts->lookahead < 0 || opts->lookahead > 1)) ||
         (opts->update != LU_UPDATE_NATIVE && opts->update != LU_UPDATE_BF16 && opts->update != LU_UPDATE_BF16X3 &&
          opts->update != LU_UPDATE_FP8 && opts->update != LU_UPDATE_F64EMU))
         return false;
@@ -679,7 +727,19 @@ int lu_plan_info(lu_dtype dt, int n, const lu_opts *opts, lu_opts *plan) {
     plan->update_ctas = p.update_ctas;
     plan->sm_share = p.share ? 1 : -1;
     plan->tile = p.tile;
+    plan->early_term = p.et;
     return plan_fits(p, n, elem) ? LU_OK : LU_ERR_UNSUPPORTED;
+}
+
+int lu_last_panel_widths(int *widths, int cap) {
+    DevState *st = nullptr;
+    if (dev_state(&st) != cudaSuccess) return -1;
+    std::lock_guard<std::recursive_mutex> lk(g_enqueue_mu);
+    if (!st->widths_valid) return -1;
+    const int cnt = (int)st->widths.size();
+    if (widths)
+        for (int i = 0; i < std::min(cnt, cap); ++i) widths[i] = st->widths[i];
+    return cnt;
 }
 
 int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info, const lu_opts *opts, void *stream) {

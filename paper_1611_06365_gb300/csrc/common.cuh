@@ -153,6 +153,17 @@ static inline int lu_ceil_div(long long a, long long b) { return (int)((a + b - 
 //      see lu_f64_slices) with the power-of-two scale of each staged row or
 //      column in dscale[].
 // ptr == NULL: no staging.  lds and kpad count elements of the staged type.
+// Early termination of a panel (section 4.2): the panel kernel reads *flag at
+// the end of each inner panel and stops there when it equals epoch (force:
+// stop at the first inner boundary whatever the flag); the width it factored
+// goes to *w_out.  flag == nullptr and force == 0: the panel runs to its end.
+struct EtArgs {
+    const int *flag;
+    int epoch;
+    int force;
+    int *w_out;
+};
+
 struct StageDesc {
     void *ptr;
     float *scale;

@@ -11,7 +11,8 @@ namespace lu {
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
-                               cudaStream_t s, CtaTrace tr, int *yreq);
+                               cudaStream_t s, CtaTrace tr, int *yreq, EtArgs et = EtArgs{});
+cudaError_t launch_et_signal(int *flag, int epoch, cudaStream_t s);
 int panel_width_that_fits(int m, size_t elem, size_t smem_cap, int cap, int bo);
 int panel_cluster_ctas(int m, size_t elem, int bo, int bi, int max_ctas, size_t smem_cap);
 cudaError_t launch_cluster_sm_probe(int C, unsigned *mask, cudaStream_t s);

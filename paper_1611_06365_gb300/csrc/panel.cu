@@ -38,6 +38,16 @@
 // and, for the tensor-core update, stages L21 in K-major order: BF16,
 // BF16 split into hi/lo, or FP8 e4m3 with a power-of-two scale per row.
 //
+// Early termination (section 4.2): with EtArgs set, the kernel reads a flag at
+// the end of each inner panel, after that inner panel's interchanges, U12 and
+// inner update have reached the panel's other columns (the right-looking inner
+// scheme), and stops there once the step's remainder update has raised it.  The
+// columns it leaves are then exactly trailing columns of a step of the width
+// it factored; that width is written out and every output (pivots, row map,
+// permutation, staging) covers the factored columns only.  CTA 0 reads the flag
+// and the other CTAs take its answer from its shared memory, so the whole
+// cluster stops at the same boundary.
+//
 // Slots, staging rows and barriers are double-buffered by column parity: a CTA
 // pushes column j+2 only after its barrier for column j+1 completed, i.e.
 // after every peer pushed column j+1, which each peer does only after all of
@@ -104,6 +114,8 @@ struct PanelShared {
     int map_cnt;
     int cnt_s;
     int first_zero;                          // first column with a zero pivot (-1: none)
+    int et_stop;                             // CTA 0: stop at this inner boundary
+    int kdone;                               // columns factored (fewer after an early termination)
 };
 
 // Magnitude key of x: the bits of |x| as an unsigned integer, which orders
@@ -331,11 +343,12 @@ __device__ __forceinline__ void rank1_step(T (&a)[RPT][BI], const T *__restrict_
 #define LU_PANEL_CASE4(L) LU_PANEL_CASE(L) LU_PANEL_CASE((L) + 1) LU_PANEL_CASE((L) + 2) LU_PANEL_CASE((L) + 3)
 #define LU_PANEL_CASE16(L) LU_PANEL_CASE4(L) LU_PANEL_CASE4((L) + 4) LU_PANEL_CASE4((L) + 8) LU_PANEL_CASE4((L) + 12)
 
-template <typename T, int RPT>
+template <typename T, int RPT, bool ET>
 __global__ void __launch_bounds__(kPanelThreads, 1)
 panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, int *__restrict__ ipiv, int row_base,
                      int *__restrict__ info, int *__restrict__ map_out, int *__restrict__ perm,
-                     StageDesc sd, int *__restrict__ status, long long bound_ns, CtaTrace tr, int *__restrict__ yreq) {
+                     StageDesc sd, int *__restrict__ status, long long bound_ns, CtaTrace tr, int *__restrict__ yreq,
+                     EtArgs et) {
     const unsigned long long t_start = tr.ring ? lu_globaltimer() : 0ull;
     constexpr int BI = TileWidth<T, RPT>::BI;
     using V = typename Vec16<T>::type;
@@ -363,6 +376,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
     const int kmax = min(m, bo);
     if (tid == 0) {
         S.first_zero = -1;
+        S.kdone = kmax;
         S.abort = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[1])) : "memory");
@@ -591,16 +605,28 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             }
         }
         cl.sync();
+        // early termination: stop here once the step's remainder update is done
+        if (ET && c_right < kmax) {
+            if (rank == 0 && tid == 0) S.et_stop = et.force ? 1 : (lu_ld_acquire(et.flag) == et.epoch ? 1 : 0);
+            cl.sync();
+            if (*cl.map_shared_rank(&S.et_stop, 0)) {
+                if (tid == 0) S.kdone = c_right;
+                break;
+            }
+        }
     }
     cl.sync();   // all of the panel is final in global memory
+    const int kdone = ET ? S.kdone : kmax;
     // pivots and the first zero pivot, written once per panel
     if (rank == 0) {
-        for (int j = tid; j < kmax; j += kPanelThreads) ipiv[j] = row_base + S.piv[j] + 1;
+        for (int j = tid; j < kdone; j += kPanelThreads) ipiv[j] = row_base + S.piv[j] + 1;
         if (tid == 0 && S.first_zero >= 0) atomicCAS(info, 0, row_base + S.first_zero + 1);
+        if (tid == 0 && et.w_out) *et.w_out = kdone;
     }
 
     // row map of all the panel's interchanges, for the rest of the matrix:
-    // [0] count, [1 .. 1+2bo) rows, [1+2bo .. 1+4bo) src (matrix rows)
+    // [0] count, [1 .. 1+2b) rows, [1+2b .. 1+4b) src (matrix rows), b = kdone
+    // (bo unless the panel stopped early)
     if (rank == 0 && map_out) {
         int *rows = reinterpret_cast<int *>(scratch);
         int *src = rows + 2 * kPanelBoMax;
@@ -610,13 +636,13 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
         for (int i = tid; i < 4096; i += kPanelThreads) keys[i] = -1;
         __syncthreads();
         if (tid == 0) {
-            int n = kmax;
-            for (int t = 0; t < kmax; ++t) { rows[t] = t; src[t] = t; }
-            for (int j = 0; j < kmax; ++j) {
+            int n = kdone;
+            for (int t = 0; t < kdone; ++t) { rows[t] = t; src[t] = t; }
+            for (int j = 0; j < kdone; ++j) {
                 const int q = S.piv[j];
                 if (q == j) continue;
                 int iq;
-                if (q < kmax) {
+                if (q < kdone) {
                     iq = q;
                 } else {
                     unsigned h = ((unsigned)q * 2654435761u) & 4095u;
@@ -635,7 +661,7 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
         const int n = S.cnt_s;
         for (int s = tid; s < n; s += kPanelThreads) {
             map_out[1 + s] = row_base + rows[s];
-            map_out[1 + 2 * bo + s] = row_base + src[s];
+            map_out[1 + 2 * kdone + s] = row_base + src[s];
         }
         if (perm) {
             for (int s = tid; s < n; s += kPanelThreads) old[s] = perm[row_base + src[s]];
@@ -643,19 +669,19 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
             for (int s = tid; s < n; s += kPanelThreads) perm[row_base + rows[s]] = old[s];
         }
     }
-    // staging of L21 for the tensor-core update (panel rows kmax.. become stage
+    // staging of L21 for the tensor-core update (panel rows kdone.. become stage
     // rows 0..), K-major, in 32-row chunks through shared memory
     if constexpr (sizeof(T) == 8) {
         if (sd.ptr && sd.fmt == 3) {
-            // FP64 digit slices (emulated FP64 update; kmax <= kpad = 64): one power-of-two
+            // FP64 digit slices (emulated FP64 update; kdone <= kpad = 64): one power-of-two
             // scale per row from the row's largest magnitude, 16 threads per row
             T *tile = reinterpret_cast<T *>(scratch);                 // 32 rows x 64
             int *rexp = reinterpret_cast<int *>(tile + 32 * 64);
             __nv_bfloat16 *st16 = static_cast<__nv_bfloat16 *>(sd.ptr);
-            for (int rb = max(r0, kmax); rb < r0 + myR; rb += 32) {
+            for (int rb = max(r0, kdone); rb < r0 + myR; rb += 32) {
                 const int nrow = min(32, r0 + myR - rb);
                 __syncthreads();
-                for (int e = tid; e < nrow * kmax; e += kPanelThreads) {
+                for (int e = tid; e < nrow * kdone; e += kPanelThreads) {
                     const int r = e % nrow, k = e / nrow;
                     tile[(size_t)r * 64 + k] = P[(size_t)(rb + r) + (size_t)k * lda];
                 }
@@ -664,20 +690,20 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                     const int r = tid >> 4, sub = tid & 15;
                     unsigned long long amax = 0;
                     if (r < nrow)
-                        for (int k = sub; k < kmax; k += 16) amax = max(amax, lu_f64_abs_bits(tile[(size_t)r * 64 + k]));
+                        for (int k = sub; k < kdone; k += 16) amax = max(amax, lu_f64_abs_bits(tile[(size_t)r * 64 + k]));
 #pragma unroll
                     for (int o = 8; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
                     if (sub == 0 && r < nrow) {
                         const int ex = lu_f64_scale_exp_bits(amax);
                         rexp[r] = ex;
-                        sd.dscale[rb + r - kmax] = ldexp(1.0, ex);
+                        sd.dscale[rb + r - kdone] = ldexp(1.0, ex);
                     }
                 }
                 __syncthreads();
                 for (int e = tid; e < nrow * sd.kpad; e += kPanelThreads) {
                     const int r = e / sd.kpad, k = e % sd.kpad;
-                    lu_f64_slices(k < kmax ? tile[(size_t)r * 64 + k] : 0.0, rexp[r],
-                                  st16 + (size_t)(rb + r - kmax) * sd.lds + k, (size_t)sd.kpad);
+                    lu_f64_slices(k < kdone ? tile[(size_t)r * 64 + k] : 0.0, rexp[r],
+                                  st16 + (size_t)(rb + r - kdone) * sd.lds + k, (size_t)sd.kpad);
                 }
             }
         }
@@ -686,10 +712,10 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
         float *tile = reinterpret_cast<float *>(scratch);   // 32 rows x kPanelBoMax, reused
         float *rowmul = tile + 32 * kPanelBoMax;              // FP8: the rows' scale factors
         const int kpad = sd.kpad;
-        for (int rb = max(r0, kmax); rb < r0 + myR; rb += 32) {
+        for (int rb = max(r0, kdone); rb < r0 + myR; rb += 32) {
             const int nrow = min(32, r0 + myR - rb);
             __syncthreads();
-            for (int e = tid; e < nrow * kmax; e += kPanelThreads) {
+            for (int e = tid; e < nrow * kdone; e += kPanelThreads) {
                 const int r = e % nrow, k = e / nrow;
                 tile[(size_t)r * kPanelBoMax + k] = (float)P[(size_t)(rb + r) + (size_t)k * lda];
             }
@@ -699,29 +725,29 @@ panel_factor_cluster(T *__restrict__ P, int lda, int m, int bo, int bi, int R, i
                 const int r = tid >> 4, sub = tid & 15;
                 float amax = 0.f;
                 if (r < nrow)
-                    for (int k = sub; k < kmax; k += 16) amax = fmaxf(amax, fabsf(tile[(size_t)r * kPanelBoMax + k]));
+                    for (int k = sub; k < kdone; k += 16) amax = fmaxf(amax, fabsf(tile[(size_t)r * kPanelBoMax + k]));
 #pragma unroll
                 for (int o = 8; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
                 float inv;
                 const float mul = lu_fp8_scale(amax, &inv);
                 if (sub == 0 && r < nrow) {
                     rowmul[r] = mul;
-                    sd.scale[rb + r - kmax] = inv;
+                    sd.scale[rb + r - kdone] = inv;
                 }
                 __syncthreads();
                 unsigned char *st8 = static_cast<unsigned char *>(sd.ptr);
                 for (int e = tid; e < nrow * kpad; e += kPanelThreads) {
                     const int rr = e / kpad, k = e % kpad;
-                    st8[(size_t)(rb + rr - kmax) * sd.lds + k] =
-                        k < kmax ? lu_to_e4m3(tile[(size_t)rr * kPanelBoMax + k] * rowmul[rr]) : (unsigned char)0;
+                    st8[(size_t)(rb + rr - kdone) * sd.lds + k] =
+                        k < kdone ? lu_to_e4m3(tile[(size_t)rr * kPanelBoMax + k] * rowmul[rr]) : (unsigned char)0;
                 }
             } else {
                 __nv_bfloat16 *st16 = static_cast<__nv_bfloat16 *>(sd.ptr);
                 for (int e = tid; e < nrow * kpad; e += kPanelThreads) {
                     const int r = e / kpad, k = e % kpad;
-                    const float x = k < kmax ? tile[(size_t)r * kPanelBoMax + k] : 0.f;
+                    const float x = k < kdone ? tile[(size_t)r * kPanelBoMax + k] : 0.f;
                     const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-                    __nv_bfloat16 *dst = st16 + (size_t)(rb + r - kmax) * sd.lds;
+                    __nv_bfloat16 *dst = st16 + (size_t)(rb + r - kdone) * sd.lds;
                     dst[k] = hi;
                     if (sd.fmt == 1) dst[kpad + k] = __float2bfloat16_rn(x - __bfloat162float(hi));
                 }
@@ -784,15 +810,16 @@ static bool panel_geometry(int m, int bi, int bo, int max_ctas, size_t smem_cap,
 template <typename T, int RPT>
 static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int bo, int bi, int R, int *ipiv,
                               int row_base, int *info, int *map_out, int *perm, StageDesc sd, int *status, long long bound_ns,
-                              const CtaTrace &tr, int *yreq) {
-    cudaError_t e = cudaFuncSetAttribute(panel_factor_cluster<T, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cfg.dynamicSmemBytes);
+                              const CtaTrace &tr, int *yreq, const EtArgs &et) {
+    // the early-termination check is compiled only into the variant that uses it
+    auto kern = (et.flag || et.force) ? panel_factor_cluster<T, RPT, true> : panel_factor_cluster<T, RPT, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(panel_factor_cluster<T, RPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     lu_count_launch();
-    return cudaLaunchKernelEx(&cfg, panel_factor_cluster<T, RPT>, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out,
-                              perm, sd, status, bound_ns, tr, yreq);
+    return cudaLaunchKernelEx(&cfg, kern, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns,
+                              tr, yreq, et);
 }
 
 // Host launcher: factor the m x bo panel at P with inner width bi; pivots into
@@ -801,11 +828,13 @@ static cudaError_t launch_rpt(cudaLaunchConfig_t &cfg, T *P, int lda, int m, int
 // L21 (stage rows 0.. = panel rows bo.., as described by sd).  A column
 // exchange that waits longer than bound_ns records LU_ERR_TIMEOUT in *status.
 // yreq (may be NULL): the worker-sharing request (SmShare), cleared once the
-// cluster runs.
+// cluster runs.  et: early termination at an inner boundary (EtArgs); the
+// factored width is then written to *et.w_out and the row map is laid out
+// for that width.
 template <typename T>
 cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, int row_base, int *info, int *map_out,
                                int *perm, StageDesc sd, int max_ctas, size_t smem_cap, int *status, long long bound_ns,
-                               cudaStream_t s, CtaTrace tr, int *yreq) {
+                               cudaStream_t s, CtaTrace tr, int *yreq, EtArgs et) {
     if (bi <= 0 || bo <= 0 || bo > kPanelBoMax || m <= 0) return cudaErrorInvalidValue;
     if (bi > bo) bi = bo;
     if (bi > kPanelWMax) return cudaErrorInvalidValue;
@@ -825,10 +854,10 @@ cudaError_t launch_panel_outer(T *P, int lda, int m, int bo, int bi, int *ipiv, 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     switch (rows_per_thread(R)) {
-        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
-        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
-        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
-        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq);
+        case 1: return launch_rpt<T, 1>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq, et);
+        case 2: return launch_rpt<T, 2>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq, et);
+        case 4: return launch_rpt<T, 4>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq, et);
+        case 8: return launch_rpt<T, 8>(cfg, P, lda, m, bo, bi, R, ipiv, row_base, info, map_out, perm, sd, status, bound_ns, tr, yreq, et);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -908,9 +937,22 @@ cudaError_t launch_share_raise(int *req, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---- early termination -------------------------------------------------------
+
+// The remainder update of step k is done: raise the flag panel k+1 reads at its
+// inner boundaries (section 4.2: written only by the update side, read only by
+// the panel side).
+__global__ void et_signal(int *flag, int epoch) { lu_st_release(flag, epoch); }
+
+cudaError_t launch_et_signal(int *flag, int epoch, cudaStream_t s) {
+    et_signal<<<1, 1, 0, s>>>(flag, epoch);
+    lu_count_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_panel_outer<double>(double *, int, int, int, int, int *, int, int *, int *, int *, StageDesc,
-                                                int, size_t, int *, long long, cudaStream_t, CtaTrace, int *);
+                                                int, size_t, int *, long long, cudaStream_t, CtaTrace, int *, EtArgs);
 template cudaError_t launch_panel_outer<float>(float *, int, int, int, int, int *, int, int *, int *, int *, StageDesc, int,
-                                               size_t, int *, long long, cudaStream_t, CtaTrace, int *);
+                                               size_t, int *, long long, cudaStream_t, CtaTrace, int *, EtArgs);
 
 }  // namespace lu

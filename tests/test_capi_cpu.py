@@ -52,6 +52,9 @@ def test_argument_errors_return_minus_i(L):
     assert f(0, 4, dummy, 4, dummy, dummy, ctypes.byref(o), None) == -7
     o = lu.LuOpts(0, 0, 0, 0, lu.LU_UPDATE_BF16, 0)                 # BF16 update needs FP32
     assert f(0, 4, dummy, 4, dummy, dummy, ctypes.byref(o), None) == -7
+    o = lu.LuOpts(0, 0, 0, 2, 0, 0, 0, 0, 0, 1)                     # early termination needs depth 1
+    assert f(0, 4, dummy, 4, dummy, dummy, ctypes.byref(o), None) == -7
+    assert L.lu_last_panel_widths(None, 0) >= -1                    # -1 until a factorization ran
     s = L.lu_solve
     assert s(0, 4, -1, dummy, 4, dummy, dummy, 4, None) == -3
     assert s(0, 4, 1, dummy, 4, dummy, dummy, 2, None) == -8

@@ -25,7 +25,7 @@ def test_put_get_clear(L):
     assert lu.lu_tune_count() == 3
     got = lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F64, 4096)
     assert got == {"nb": 16, "nb_inner": 0, "panel_ctas": 8, "lookahead": 0, "update": 0, "update_ctas": 0, "sm_share": 0,
-                   "tile": 0}
+                   "tile": 0, "early_term": 0}
     # the key includes the update kind and the exact order
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096) is None
     assert lu.lu_tune_get(lu.TUNE_FACTOR, lu.LU_F32, 4096, update=lu.LU_UPDATE_BF16X3)["nb"] == 128
@@ -152,6 +152,21 @@ def test_plan_info_worker_sharing_option(L):
     for bad in (-1, 3):
         with pytest.raises(lu.LuError):
             lu.lu_plan_info(lu.LU_F64, 4096, tile=bad)
+
+
+def test_plan_info_early_termination_option(L):
+    """early_term: 0..2, only with look-ahead of depth 1; the plan reports it, and
+    the fit check then covers panels starting at any column."""
+    for et in (1, 2):
+        rc, p = lu.lu_plan_info(lu.LU_F64, 1000, nb=64, nb_inner=16, early_term=et)
+        assert rc == 0 and p["early_term"] == et and p["lookahead"] == 1 and p["nb_inner"] == 16
+    rc, p = lu.lu_plan_info(lu.LU_F32, 4096, nb=64, nb_inner=16, early_term=1, update=lu.LU_UPDATE_BF16X3)
+    assert rc == 0 and p["early_term"] == 1
+    assert lu.lu_plan_info(lu.LU_F64, 1000)[1]["early_term"] == 0
+    for kw in ({"early_term": -1}, {"early_term": 3}, {"early_term": 1, "lookahead": 2},
+               {"early_term": 1, "lookahead": -1}):
+        with pytest.raises(lu.LuError):
+            lu.lu_plan_info(lu.LU_F64, 1000, **kw)
 
 
 @pytest.mark.parametrize("dt,update,widths", [
