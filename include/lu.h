@@ -151,11 +151,12 @@ int lu_factor(lu_dtype dt, int n, void *dA, int lda, int *d_ipiv, int *d_info,
               const lu_opts *opts, void *stream);
 
 /*
- * lu_last_panel_widths -- the widths of the panels of the last lu_factor on
- *   the current device, in order (all b_o but the last unless early
- *   termination shortened some; section 4.2).  Copies min(count, cap) of them
- *   to the host array `widths` (may be NULL when cap = 0) and returns count,
- *   or -1 when no factorization ran on this device yet.
+ * lu_last_panel_widths -- the widths of the panels of the last LU
+ *   factorization enqueued on the current device (lu_factor, or the one inside
+ *   lu_solve_mixed), in order: all b_o but the last unless early termination
+ *   shortened some (section 4.2).  Copies min(count, cap) of them to the host
+ *   array `widths` (may be NULL when cap = 0) and returns count, or -1 when no
+ *   factorization ran on this device yet.  Host-side bookkeeping: no CUDA work.
  */
 int lu_last_panel_widths(int *widths, int cap);
 
