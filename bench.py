@@ -373,6 +373,13 @@ def run_ours(args):
     if rank == 0 and not args.skip_chol:
         # Cholesky on the same look-ahead schedule (n = 16384: DFMA and emulated updates)
         chol = cholesky_measure(16384, dev, 2)
+    et_rows = None
+    if rank == 0 and not args.skip_et:
+        # early termination (section 4.2) on and off, same plans (b_o = 64, b_i = 16)
+        try:
+            et_rows = early_term_measure(dev)
+        except Exception as exc:   # reported, never fatal to the line
+            et_rows = f"failed: {type(exc).__name__}: {exc}"
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps,
@@ -386,7 +393,7 @@ def run_ours(args):
                    "autotuned": tuned or None},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "fp64_emulated": emu, "time_to_solution": tts, "batched": batched, "latency_n512": small,
-        "cholesky": chol,
+        "cholesky": chol, "early_termination": et_rows,
     }
     if rank == 0 and not args.skip_cpu:
         dt, threads = oracle_sample(args.cpu_n, SEED)
@@ -825,10 +832,11 @@ def measure_peaks(dev):
     return out
 
 
-def early_term_case(dev):
+def early_term_measure(dev):
     """Early termination (section 4.2) against the same plan without it: lu_factor time
     (CUDA events on the caller's stream, so the host's wait for each panel's width is
-    inside), panels, and how many stopped early.  One JSON line per workload."""
+    inside; best of three after a warm-up), panels, and how many stopped early.  One row
+    per workload."""
     import torch
 
     import lu_inputs as li
@@ -837,6 +845,7 @@ def early_term_case(dev):
     cases = (("fp64_dfma", 4096, torch.float64, lu.LU_UPDATE_NATIVE),
              ("fp64_emulated", 8192, torch.float64, lu.LU_UPDATE_F64EMU),
              ("fp32_split_bf16", 16384, torch.float32, lu.LU_UPDATE_BF16X3))
+    rows = []
     for name, n, tdt, update in cases:
         A0 = li.uniform_colmajor_torch(n, n, 5, dev, tdt)
         A = torch.empty_like(A0)
@@ -861,7 +870,10 @@ def early_term_case(dev):
             row[key] = {"ms": ms, "gflops": flops_lu(n) / (ms / 1e3) / 1e9, "panels": len(w),
                         "stopped_early": sum(1 for i, x in enumerate(w[:-1]) if x < 64),
                         "mean_width": sum(w) / len(w), "info": int(info.item())}
-        print(json.dumps(row), flush=True)
+        rows.append(row)
+        del A0, A
+    torch.cuda.empty_cache()
+    return rows
 
 
 def run_case(args):
@@ -935,7 +947,8 @@ def run_case(args):
         print(json.dumps(measure_peaks(dev)), flush=True)
         return
     elif args.case == "early_term":
-        early_term_case(dev)
+        for row in early_term_measure(dev):
+            print(json.dumps(row), flush=True)
         return
     elif args.case == "cholesky":
         print(json.dumps(dict({"case": "cholesky"}, **cholesky_measure(args.n, dev, 3))), flush=True)
@@ -1008,6 +1021,8 @@ def make_parser():
     ap.add_argument("--skip-cpu", dest="skip_cpu", action="store_true")
     ap.add_argument("--skip-batched", dest="skip_batched", action="store_true")
     ap.add_argument("--skip-chol", dest="skip_chol", action="store_true", help="leave out the Cholesky line")
+    ap.add_argument("--skip-et", dest="skip_et", action="store_true",
+                    help="leave out the early-termination comparison")
     ap.add_argument("--skip-small", dest="skip_small", action="store_true",
                     help="skip the n = 512 latency measurement")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
