@@ -23,6 +23,13 @@
 // of width b_i on the cluster, each followed by its interchanges, TRSM and
 // update restricted to the outer panel.
 //
+// Early termination (section 4.2, lu_opts.early_term): after RU2(k) a
+// one-thread kernel raises a flag on U; panel k+1 reads it at the end of
+// each inner panel and stops there, leaving the rest of its strip in the
+// state of trailing columns after a step of the width it reached.  The host
+// reads that width back before it enqueues step k+1, whose strip then takes
+// step k+1 only beyond panel k+1's nominal columns.
+//
 // Plans: b_o, b_i, the panel team and the RU2 grid come from lu_opts, else
 // from the autotuner's table (tune.cu), else from the built-in choice
 // (make_plan); every panel of a plan is checked to fit a cluster before
